@@ -1,0 +1,161 @@
+/*
+ * tor.h -- C ABI of libtor: exact Torontonians on NVIDIA GB300 (sm_103a).
+ *
+ * The Torontonian of a 2n x 2n Hermitian matrix O (paper Sec. 1, Eq. tor) is
+ *
+ *     Tor(O) = sum_{Z subset of {1..n}} (-1)^{n-|Z|} / sqrt(det(I - O_Z)),
+ *
+ * where O_Z keeps, for each mode j in Z, both its a_j and a_j^dag rows and
+ * columns.  For a Gaussian state with complex Husimi covariance Sigma the
+ * input is the sampling matrix O = I - Sigma^{-1} (Sec. 1, Eq. A).
+ *
+ * The library evaluates the sum on the GPU by the paper's recursive subset
+ * tree (Sec. 2, Algorithm 2 and Figs. 1-2): subsets share the Cholesky data of
+ * their common prefix, so adding one mode costs one rank-2 Schur update of the
+ * parent's trailing block instead of a new factorisation.
+ *
+ * Conventions for every call:
+ *   - Every function returns a tor_status; nothing aborts or throws across this
+ *     ABI.  Per-matrix failures are reported in tor_result.status.
+ *   - Matrices are row-major complex128 (tor_c128 == numpy complex128 ==
+ *     torch.cdouble) with leading dimension `ld` >= 2n, in complex elements.
+ *   - Row order is TOR_LAYOUT_BLOCK (a_1..a_n, a_1^dag..a_n^dag) unless the
+ *     context was created with TOR_LAYOUT_PAIRS (a_1, a_1^dag, a_2, ...), the
+ *     order the paper uses (Sec. 2).  Tor is the same in both (rows and columns
+ *     are permuted together).
+ *   - Host inputs are copied before the call returns; the caller keeps
+ *     ownership of every buffer it passes.  With TOR_IN_DEVICE the O pointers
+ *     are device pointers on the context's device; they are read on the
+ *     context's stream and must stay valid until the call returns (tor_eval*)
+ *     or until the ticket has been polled (tor_submit).
+ *   - n = 0 gives Tor = 1 (0 x 0 determinant).  n > 64 gives TOR_ETOOBIG.
+ *   - Input checks (skipped with TOR_NO_CHECK): O Hermitian within
+ *     1e-12 * max|O| (else TOR_ENOTHERM), finite entries (else TOR_EINVAL).
+ *     I - O must be positive definite; a non-positive pivot anywhere in the
+ *     tree gives TOR_ENOTPD for that matrix.
+ */
+#ifndef LIBTOR_TOR_H
+#define LIBTOR_TOR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  TOR_OK = 0,
+  TOR_EINVAL = 1,     /* bad argument or non-finite input */
+  TOR_ENOTHERM = 2,   /* O is not Hermitian within tolerance */
+  TOR_ENOTPD = 3,     /* I - O (or one of its principal blocks) is not positive definite */
+  TOR_ENOMEM = 4,     /* device or pinned-host allocation failed, or over the memory budget */
+  TOR_EAGAIN = 5,     /* result not ready yet (tor_poll) / queue full (tor_submit) */
+  TOR_ETIMEOUT = 6,   /* the evaluation ran past tor_config.timeout_s and was stopped */
+  TOR_ECANCELED = 7,  /* the evaluation was cancelled with tor_cancel */
+  TOR_ECUDA = 8,      /* a CUDA runtime call failed; see tor_last_error */
+  TOR_ETOOBIG = 9     /* n > 64 */
+} tor_status;
+
+typedef struct { double re, im; } tor_c128;
+
+enum { TOR_LAYOUT_BLOCK = 0, TOR_LAYOUT_PAIRS = 1 };
+enum { TOR_IN_DEVICE = 1u, TOR_NO_CHECK = 2u };
+
+typedef struct tor_ctx tor_ctx;
+
+typedef struct {
+  int device;          /* CUDA device ordinal */
+  void* stream;        /* cudaStream_t to run on; NULL = the library creates its own */
+  size_t mem_budget;   /* cap on the library's device memory in bytes; 0 = no cap */
+  int prefix_depth;    /* unit prefix depth p for every n; -1 = built-in plan / autotune table */
+  int layout;          /* TOR_LAYOUT_BLOCK or TOR_LAYOUT_PAIRS */
+  unsigned flags;      /* TOR_IN_DEVICE | TOR_NO_CHECK */
+  double timeout_s;    /* per call; 0 = none.  Past it the kernels stop and return TOR_ETIMEOUT */
+} tor_config;
+
+typedef struct {
+  double hi, lo;       /* Tor as an unevaluated double-double sum hi + lo */
+  double abs_sum;      /* sum over all subsets of |term|: the scale of the rounding error */
+  double err_est;      /* a-priori error estimate 8 n u abs_sum, u = 2^-53 */
+  int n;               /* modes of this matrix */
+  tor_status status;   /* per-matrix status */
+} tor_result;
+
+/* Fills *cfg with defaults: device 0, own stream, no budget, planned prefix
+ * depth, block layout, no flags, no timeout. */
+void tor_config_default(tor_config* cfg);
+
+/* Creates a context on cfg->device (cfg may be NULL for defaults).  Allocates
+ * nothing large until the first evaluation.  *out is NULL on failure. */
+tor_status tor_create(const tor_config* cfg, tor_ctx** out);
+
+/* Frees the context and all its device and pinned memory.  Blocks until the
+ * context's outstanding work has finished.  NULL is ignored. */
+void tor_destroy(tor_ctx* ctx);
+
+/* Tor of one 2n x 2n matrix (Eq. tor).  Blocking.  The call's return value is
+ * the first error of the call; *out carries the per-matrix status too. */
+tor_status tor_eval(tor_ctx* ctx, int n, const tor_c128* O, int ld, tor_result* out);
+
+/* Tor of `count` matrices of mixed sizes in one persistent-kernel launch.
+ * n[i], O[i], ld[i] describe matrix i; out[i] receives its result.  Each
+ * result is bitwise identical to tor_eval of the same matrix on the same
+ * context (the unit decomposition depends on n only).  Blocking. */
+tor_status tor_eval_batch(tor_ctx* ctx, int count, const int* n, const tor_c128* const* O,
+                          const int* ld, tor_result* out);
+
+/* Queues one matrix for evaluation and returns at once with a ticket.  Queued
+ * and running requests are batched by the context's serving loop; a request
+ * that arrives while others run is admitted as device memory frees up.
+ * TOR_EAGAIN if the queue is full. */
+tor_status tor_submit(tor_ctx* ctx, int n, const tor_c128* O, int ld, uint64_t* ticket);
+
+/* Waits up to timeout_s (0 = do not wait, < 0 = forever) for a ticket.
+ * Returns TOR_EAGAIN if it is still pending, TOR_EINVAL for an unknown or
+ * already collected ticket, else the request's status with *out filled. */
+tor_status tor_poll(tor_ctx* ctx, uint64_t ticket, tor_result* out, double timeout_s);
+
+/* Asks the kernels running for this context to stop at their next unit
+ * boundary; the affected results get TOR_ECANCELED.  Thread-safe. */
+tor_status tor_cancel(tor_ctx* ctx);
+
+/* Human-readable name of a status.  Never NULL. */
+const char* tor_strerror(tor_status s);
+
+/* Last CUDA error string seen by this context ("" if none).  Never NULL. */
+const char* tor_last_error(tor_ctx* ctx);
+
+/* ---- inspection and measurement (same kernels, more output) ---- */
+
+/* Prefix depth p the context uses for n modes (2^p equal units, each a subtree
+ * over the last n - p modes).  -1 if n is out of range. */
+int tor_plan_prefix_depth(tor_ctx* ctx, int n);
+
+/* Sets the prefix depth used for n modes from now on (the autotuner's entry
+ * point).  p in [0, n-1].  Changing it changes the summation order, so
+ * results before and after differ in rounding. */
+tor_status tor_set_prefix_depth(tor_ctx* ctx, int n, int p);
+
+/* Like tor_eval, but also copies the 2^p per-unit partial sums to the host:
+ * unit u (bit j of u set <=> mode j is in Z, for j < p) sums the terms of all
+ * Z whose first p decisions are u.  partials must hold 3 * 2^p doubles:
+ * (hi, lo, abs_sum) per unit, in u order.  p = tor_plan_prefix_depth(ctx, n). */
+tor_status tor_eval_units(tor_ctx* ctx, int n, const tor_c128* O, int ld, double* partials,
+                          size_t partials_len, tor_result* out);
+
+/* Device time of the last tor_eval / tor_eval_batch, split by kernel, from CUDA
+ * events on the context's stream: [0] intake, [1] units, [2] reduce, [3] total
+ * (ms).  times must hold 4 doubles. */
+tor_status tor_last_times(tor_ctx* ctx, double* times);
+
+/* Measures the device's FP64 FMA throughput with a saturating kernel (all SMs,
+ * 8 warps each, independent chains) for about `seconds`.  Writes DFMA per
+ * second and FP64 TFLOP/s (2 flops per DFMA). */
+tor_status tor_probe_fp64(int device, double seconds, double* dfma_per_s, double* fp64_tflops);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LIBTOR_TOR_H */

@@ -1,5 +1,279 @@
-"""placeholder"""
-class TorError(Exception): pass
-Context = TorResult = None
-def tor_create(*a, **k): raise NotImplementedError
-tor_destroy = tor_eval = tor_eval_batch = tor_submit = tor_poll = tor_strerror = load_library = library_path = tor_create
+"""Thin ctypes binding of libtor (C ABI in include/tor.h).
+
+Argument marshalling only: every step of the evaluation runs in the CUDA
+library.  If the library has not been built, every call raises TorError --
+there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import build as _build
+
+TOR_OK, TOR_EINVAL, TOR_ENOTHERM, TOR_ENOTPD, TOR_ENOMEM, TOR_EAGAIN, TOR_ETIMEOUT, \
+    TOR_ECANCELED, TOR_ECUDA, TOR_ETOOBIG = range(10)
+STATUS_NAMES = ["TOR_OK", "TOR_EINVAL", "TOR_ENOTHERM", "TOR_ENOTPD", "TOR_ENOMEM", "TOR_EAGAIN",
+                "TOR_ETIMEOUT", "TOR_ECANCELED", "TOR_ECUDA", "TOR_ETOOBIG"]
+TOR_LAYOUT_BLOCK, TOR_LAYOUT_PAIRS = 0, 1
+TOR_IN_DEVICE, TOR_NO_CHECK = 1, 2
+
+# Every symbol include/tor.h declares (the ABI test checks the library exports them).
+EXPORTS = ["tor_config_default", "tor_create", "tor_destroy", "tor_eval", "tor_eval_batch", "tor_submit",
+           "tor_poll", "tor_cancel", "tor_strerror", "tor_last_error", "tor_plan_prefix_depth",
+           "tor_set_prefix_depth", "tor_eval_units", "tor_last_times", "tor_probe_fp64"]
+
+
+class TorError(RuntimeError):
+    def __init__(self, status: int, what: str = ""):
+        self.status = status
+        name = STATUS_NAMES[status] if 0 <= status < len(STATUS_NAMES) else str(status)
+        super().__init__(f"{name}{': ' + what if what else ''}")
+
+
+class tor_config(ctypes.Structure):
+    _fields_ = [("device", ctypes.c_int), ("stream", ctypes.c_void_p), ("mem_budget", ctypes.c_size_t),
+                ("prefix_depth", ctypes.c_int), ("layout", ctypes.c_int), ("flags", ctypes.c_uint),
+                ("timeout_s", ctypes.c_double)]
+
+
+class tor_result(ctypes.Structure):
+    _fields_ = [("hi", ctypes.c_double), ("lo", ctypes.c_double), ("abs_sum", ctypes.c_double),
+                ("err_est", ctypes.c_double), ("n", ctypes.c_int), ("status", ctypes.c_int)]
+
+
+@dataclass
+class TorResult:
+    hi: float
+    lo: float
+    abs_sum: float
+    err_est: float
+    n: int
+    status: int
+
+    @property
+    def tor(self) -> float:
+        return self.hi + self.lo
+
+    @staticmethod
+    def of(r: tor_result) -> "TorResult":
+        return TorResult(r.hi, r.lo, r.abs_sum, r.err_est, r.n, r.status)
+
+
+_LIB = None
+
+
+def library_path() -> str:
+    return _build.library_path()
+
+
+def load_library():
+    """Load the built CUDA library; raises TorError if it is missing."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    path = library_path()
+    if not os.path.exists(path):
+        raise TorError(TOR_ECUDA, f"libtor is not built ({path}); run __graft_entry__.build()")
+    lib = ctypes.CDLL(path)
+    c_int, c_double, c_void_p, c_size_t = ctypes.c_int, ctypes.c_double, ctypes.c_void_p, ctypes.c_size_t
+    P = ctypes.POINTER
+    lib.tor_config_default.argtypes = [P(tor_config)]
+    lib.tor_config_default.restype = None
+    lib.tor_create.argtypes = [P(tor_config), P(c_void_p)]
+    lib.tor_destroy.argtypes = [c_void_p]
+    lib.tor_destroy.restype = None
+    lib.tor_eval.argtypes = [c_void_p, c_int, c_void_p, c_int, P(tor_result)]
+    lib.tor_eval_batch.argtypes = [c_void_p, c_int, P(c_int), P(c_void_p), P(c_int), P(tor_result)]
+    lib.tor_submit.argtypes = [c_void_p, c_int, c_void_p, c_int, P(ctypes.c_uint64)]
+    lib.tor_poll.argtypes = [c_void_p, ctypes.c_uint64, P(tor_result), c_double]
+    lib.tor_cancel.argtypes = [c_void_p]
+    lib.tor_strerror.argtypes = [c_int]
+    lib.tor_strerror.restype = ctypes.c_char_p
+    lib.tor_last_error.argtypes = [c_void_p]
+    lib.tor_last_error.restype = ctypes.c_char_p
+    lib.tor_plan_prefix_depth.argtypes = [c_void_p, c_int]
+    lib.tor_set_prefix_depth.argtypes = [c_void_p, c_int, c_int]
+    lib.tor_eval_units.argtypes = [c_void_p, c_int, c_void_p, c_int, P(c_double), c_size_t, P(tor_result)]
+    lib.tor_last_times.argtypes = [c_void_p, P(c_double)]
+    lib.tor_probe_fp64.argtypes = [c_int, c_double, P(c_double), P(c_double)]
+    _LIB = lib
+    return lib
+
+
+def tor_strerror(status: int) -> str:
+    return load_library().tor_strerror(int(status)).decode()
+
+
+def _host_matrix(O):
+    """complex128 C-contiguous host array -> (array, n, ld)."""
+    a = np.ascontiguousarray(np.asarray(O, dtype=np.complex128))
+    if a.ndim != 2 or a.shape[0] != a.shape[1] or a.shape[0] % 2:
+        raise TorError(TOR_EINVAL, "O must be a square 2n x 2n matrix")
+    return a, a.shape[0] // 2, max(a.shape[1], 1)
+
+
+def _device_matrix(O):
+    """torch.cdouble CUDA tensor with unit column stride -> (tensor, n, ld, pointer)."""
+    if O.dim() != 2 or O.shape[0] != O.shape[1] or O.shape[0] % 2:
+        raise TorError(TOR_EINVAL, "O must be a square 2n x 2n matrix")
+    if O.stride(1) != 1:
+        O = O.contiguous()
+    return O, O.shape[0] // 2, max(O.stride(0), 1), O.data_ptr()
+
+
+class Context:
+    """A libtor context (tor_create / tor_destroy)."""
+
+    def __init__(self, device: int = 0, stream=None, mem_budget: int = 0, prefix_depth: int = -1,
+                 layout: int = TOR_LAYOUT_BLOCK, flags: int = 0, timeout_s: float = 0.0):
+        lib = load_library()
+        cfg = tor_config()
+        lib.tor_config_default(ctypes.byref(cfg))
+        cfg.device = device
+        cfg.stream = ctypes.c_void_p(int(stream)) if stream is not None else None
+        cfg.mem_budget = mem_budget
+        cfg.prefix_depth = prefix_depth
+        cfg.layout = layout
+        cfg.flags = flags
+        cfg.timeout_s = timeout_s
+        h = ctypes.c_void_p()
+        st = lib.tor_create(ctypes.byref(cfg), ctypes.byref(h))
+        if st != TOR_OK:
+            raise TorError(st, "tor_create")
+        self._h = h
+        self._lib = lib
+        self.flags = flags
+        self.device = device
+
+    @property
+    def handle(self):
+        if self._h is None:
+            raise TorError(TOR_EINVAL, "context is closed")
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None) is not None:
+            self._lib.tor_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def last_error(self) -> str:
+        return self._lib.tor_last_error(self.handle).decode()
+
+    def plan_prefix_depth(self, n: int) -> int:
+        return int(self._lib.tor_plan_prefix_depth(self.handle, n))
+
+    def set_prefix_depth(self, n: int, p: int):
+        st = self._lib.tor_set_prefix_depth(self.handle, n, p)
+        if st != TOR_OK:
+            raise TorError(st, "tor_set_prefix_depth")
+
+    def last_times(self):
+        t = (ctypes.c_double * 4)()
+        self._lib.tor_last_times(self.handle, t)
+        return {"intake_ms": t[0], "units_ms": t[1], "reduce_ms": t[2], "total_ms": t[3]}
+
+    def cancel(self):
+        self._lib.tor_cancel(self.handle)
+
+
+def tor_create(**kw) -> Context:
+    return Context(**kw)
+
+
+def tor_destroy(ctx: Context):
+    ctx.close()
+
+
+def _matrix_args(ctx: Context, O):
+    if ctx.flags & TOR_IN_DEVICE:
+        t, n, ld, ptr = _device_matrix(O)
+        return t, n, ld, ptr
+    a, n, ld = _host_matrix(O)
+    return a, n, ld, a.ctypes.data
+
+
+def tor_eval(ctx: Context, O, check: bool = True) -> TorResult:
+    """Tor of one matrix (host numpy array, or torch CUDA tensor with TOR_IN_DEVICE)."""
+    keep, n, ld, ptr = _matrix_args(ctx, O)
+    res = tor_result()
+    st = ctx._lib.tor_eval(ctx.handle, n, ctypes.c_void_p(ptr), ld, ctypes.byref(res))
+    if check and st not in (TOR_OK,):
+        raise TorError(st, ctx.last_error() or "tor_eval")
+    del keep
+    return TorResult.of(res)
+
+
+def tor_eval_batch(ctx: Context, mats, check: bool = True):
+    """Tor of several matrices of mixed sizes in one launch; returns a list of TorResult."""
+    k = len(mats)
+    if k == 0:
+        return []
+    args = [_matrix_args(ctx, O) for O in mats]
+    ns = (ctypes.c_int * k)(*[a[1] for a in args])
+    lds = (ctypes.c_int * k)(*[a[2] for a in args])
+    ptrs = (ctypes.c_void_p * k)(*[a[3] for a in args])
+    res = (tor_result * k)()
+    st = ctx._lib.tor_eval_batch(ctx.handle, k, ns, ptrs, lds, res)
+    if check and st != TOR_OK:
+        raise TorError(st, ctx.last_error() or "tor_eval_batch")
+    del args
+    return [TorResult.of(r) for r in res]
+
+
+def tor_eval_units(ctx: Context, O):
+    """tor_eval plus the per-unit partials: returns (TorResult, p, array of shape (2^p, 3))."""
+    keep, n, ld, ptr = _matrix_args(ctx, O)
+    p = ctx.plan_prefix_depth(n)
+    parts = np.zeros((1 << p, 3), dtype=np.float64)
+    res = tor_result()
+    st = ctx._lib.tor_eval_units(ctx.handle, n, ctypes.c_void_p(ptr), ld,
+                                 parts.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), parts.size,
+                                 ctypes.byref(res))
+    if st != TOR_OK:
+        raise TorError(st, ctx.last_error() or "tor_eval_units")
+    del keep
+    return TorResult.of(res), p, parts
+
+
+def tor_submit(ctx: Context, O) -> int:
+    a, n, ld = _host_matrix(O)
+    t = ctypes.c_uint64()
+    st = ctx._lib.tor_submit(ctx.handle, n, ctypes.c_void_p(a.ctypes.data), ld, ctypes.byref(t))
+    if st != TOR_OK:
+        raise TorError(st, "tor_submit")
+    return int(t.value)
+
+
+def tor_poll(ctx: Context, ticket: int, timeout_s: float = -1.0):
+    """Returns (status, TorResult or None); status TOR_EAGAIN means still pending."""
+    res = tor_result()
+    st = ctx._lib.tor_poll(ctx.handle, ticket, ctypes.byref(res), timeout_s)
+    if st in (TOR_EAGAIN,) or (st == TOR_EINVAL and res.n == 0 and res.status == 0 and res.abs_sum == 0):
+        return st, None
+    return st, TorResult.of(res)
+
+
+def tor_probe_fp64(device: int = 0, seconds: float = 0.5):
+    """(DFMA per second, FP64 TFLOP/s) from the library's saturating FMA kernel."""
+    lib = load_library()
+    d, t = ctypes.c_double(), ctypes.c_double()
+    st = lib.tor_probe_fp64(device, seconds, ctypes.byref(d), ctypes.byref(t))
+    if st != TOR_OK:
+        raise TorError(st, "tor_probe_fp64")
+    return d.value, t.value

@@ -1,0 +1,65 @@
+// tor_internal.h -- structures shared by the host runtime and the kernels.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace tor {
+
+// Partial sum of one unit: Tor contribution as double-double, and sum |term|.
+struct __align__(32) Part {
+  double hi, lo, abs_sum, pad;
+};
+
+// One matrix of a job.
+struct MatDesc {
+  const double2* O;     // input O on the device (row-major, leading dimension ld)
+  double2* B;           // packed lower triangle of B = I - O in pairs order, n(2n+1) entries
+  long long part_off;   // first of this matrix's 2^p unit partials
+  int n, p, ld, layout;
+};
+
+// One warp task.  p >= 5: 32 units of matrix `mat` sharing the decisions on
+// modes 0..p-6 (= bits of `sub`); lane l takes the decisions on modes
+// p-5..p-1 from its 5 bits.  p < 5: units q = 32 sub + lane of the nmat
+// consecutive matrices starting at `mat` (same n and p), q < nmat 2^p.
+struct TaskDesc {
+  int mat, sub, nmat, M;
+};
+
+enum { FLAG_NOTPD = 1, FLAG_NOTHERM = 2, FLAG_NONFINITE = 4 };
+enum { ABORT_TIMEOUT = 1, ABORT_CANCEL = 2 };
+
+struct UnitsParams {
+  const MatDesc* mats;
+  const TaskDesc* tasks;
+  int ntasks;
+  unsigned* ticket;            // zeroed before the launch
+  Part* partials;           // (hi, lo, abs_sum, 0) per unit
+  int* mat_flags;              // FLAG_* per matrix
+  double2* lane_scratch;       // per warp: 32 * lane_elems, lane-interleaved
+  long long lane_elems;
+  double2* warp_scratch;       // per warp: warp_elems, contiguous
+  long long warp_elems;
+  const volatile int* cancel;  // host-mapped; nonzero = stop
+  long long budget_ns;         // 0 = no time limit
+  int* abort_word;             // ABORT_* bits set by the kernel
+};
+
+struct ResultRec {
+  double hi, lo, abs_sum;
+  int flags, pad;
+};
+
+// Element counts of the scratch a task needs (complex128 elements).
+long long lane_elems_for(int n, int p);
+long long warp_elems_for(int n, int p);
+
+cudaError_t launch_intake(const MatDesc* d_mats, int nmats, int check, int* d_flags, cudaStream_t s);
+cudaError_t launch_units(const UnitsParams& prm, int grid, cudaStream_t s);
+cudaError_t launch_reduce(const MatDesc* d_mats, int nmats, const Part* partials, const int* flags,
+                          ResultRec* out, cudaStream_t s);
+int units_block_threads();
+cudaError_t units_blocks_per_sm(int* blocks);
+cudaError_t run_probe_fp64(double seconds, double* dfma_per_s);
+
+}  // namespace tor

@@ -1,0 +1,479 @@
+// tor_kernels.cu -- the GPU path of the subset-tree Torontonian.
+//
+//   k_intake  : B = I - O in pairs order, packed lower triangle (paper Sec. 1
+//               Eq. A and the row order of Sec. 2); Hermitian / finite checks.
+//   k_units   : persistent warps; each warp task evaluates 32 units (prefix
+//               subtrees) of the tree of Algorithm 2, one unit per lane.
+//   k_reduce  : fixed-shape binary tree over each matrix's unit partials, in
+//               double-double.
+//   k_probe   : FP64 FMA throughput probe (the roofline's denominator).
+#include "tor_device.cuh"
+#include "tor_internal.h"
+
+namespace tor {
+
+// ------------------------------------------------------------------ helpers
+
+__host__ __device__ __forceinline__ int tri_size(int m) { return m * (2 * m + 1); }  // packed entries, m modes
+// sum_{k=4}^{m-1} k(2k+1): offset of the lane stack buffer for m modes past the root
+__host__ __device__ __forceinline__ int stack_off(int m) {
+  int s = 0;
+  for (int k = 4; k < m; ++k) s += tri_size(k);
+  return s;
+}
+__host__ __device__ __forceinline__ int arena_off(int m0, int d) {  // BFS arena: level d's include children
+  int s = 0;
+  for (int e = 0; e < d; ++e) s += (1 << e) * tri_size(m0 - e - 1);
+  return s;
+}
+
+long long lane_elems_for(int n, int p) {
+  int M = n - p;
+  long long root = p >= 5 ? tri_size(M) : tri_size(n);
+  return root + stack_off(M) + 4LL * n;
+}
+long long warp_elems_for(int n, int p) {
+  if (p < 5) return 0;
+  int m0 = n - p + 5;
+  return (long long)tri_size(n) + arena_off(m0, 5) + 8LL * n;
+}
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// ------------------------------------------------------------------ includes
+
+__device__ __noinline__ double lane_include_mem(const LaneMem L, int src, int o, int m, int dst, int dst_o,
+                                                int xs, int ys, bool& bad) {
+  Pivot pv = make_pivot(L.ld(src + P(o, o)).x, L.ld(src + P(o + 1, o)), L.ld(src + P(o + 1, o + 1)).x);
+  bad |= !pv.ok;
+  const int R = 2 * (m - 1);
+  for (int r = 0; r < R; ++r) {
+    double2 x = L.ld(src + P(o + 2 + r, o));
+    L.st(xs + r, x);
+    L.st(ys + r, reduce_col(x, L.ld(src + P(o + 2 + r, o + 1)), pv.cl));
+  }
+  for (int i = 0; i < R; ++i) {
+    const double2 xi = L.ld(xs + i), yi = L.ld(ys + i);
+    const double2 xt = cscale(xi, pv.ia), yt = cscale(yi, pv.id2);
+    const int srow = src + P(o + 2 + i, o + 2);
+    const int drow = dst + P(dst_o + i, dst_o);
+#pragma unroll 2
+    for (int k = 0; k < i; ++k) L.st(drow + k, rank2_off(L.ld(srow + k), xt, L.ld(xs + k), yt, L.ld(ys + k)));
+    L.st(drow + i, make_double2(rank2_diag(L.ld(srow + i).x, xt, xi, yt, yi), 0.0));
+  }
+  return pv.rho;
+}
+
+__device__ __noinline__ double coop_include(const double2* src, int o, int m, double2* dst, int dst_o, double2* xs,
+                                            double2* ys, bool& bad) {
+  const int lane = threadIdx.x & (kWarp - 1);
+  Pivot pv = make_pivot(src[P(o, o)].x, src[P(o + 1, o)], src[P(o + 1, o + 1)].x);
+  bad |= !pv.ok;
+  const int R = 2 * (m - 1);
+  // xs[0..R) = x, xs[R..2R) = x / d1; ys[0..R) = y', ys[R..2R) = y' / d2
+  for (int r = lane; r < R; r += kWarp) {
+    double2 x = src[P(o + 2 + r, o)];
+    double2 y = reduce_col(x, src[P(o + 2 + r, o + 1)], pv.cl);
+    xs[r] = x;
+    xs[R + r] = cscale(x, pv.ia);
+    ys[r] = y;
+    ys[R + r] = cscale(y, pv.id2);
+  }
+  __syncwarp();
+  const int tot = (R * (R + 1)) / 2;
+  int i = 0, k = lane;
+  while (k > i) { k -= i + 1; ++i; }
+  for (int e = lane; e < tot; e += kWarp) {
+    const double2 xt = xs[R + i], yt = ys[R + i];
+    const double2 s = src[P(o + 2 + i, o + 2 + k)];
+    double2 out;
+    if (k < i) out = rank2_off(s, xt, xs[k], yt, ys[k]);
+    else out = make_double2(rank2_diag(s.x, xt, xs[i], yt, ys[i]), 0.0);
+    dst[P(dst_o + i, dst_o + k)] = out;
+    k += kWarp;
+    while (k > i) { k -= i + 1; ++i; }
+  }
+  __syncwarp();
+  return pv.rho;
+}
+
+// ------------------------------------------------------------------ lane DFS
+
+// Walks the subtree below a lane's unit root (a view (root, root_o) with M
+// modes, phi_root, incl_root modes included so far out of n - M decided) and
+// adds its 2^M signed terms to acc, their magnitudes to ab.
+//
+// Levels are indexed by the number of modes m of the node.  The binary
+// counter c enumerates the 3-mode nodes in depth-first order: bit t of c is
+// the decision (1 = include) taken at the level with 4 + t modes.  Going
+// from c-1 to c flips bit t = ctz(c) from 0 to 1 and every lower bit back to
+// 0: one include at level 4 + t, then excludes.  Included children are
+// written to the buffer of their own size (buffer m holds an m-mode matrix),
+// excluded children are views of their parent, so a node is never
+// overwritten while a pending include still needs it.  The 3-mode nodes and
+// everything below them live in registers.
+__device__ __noinline__ void lane_dfs(const LaneMem L, int root, int root_o, int M, int n, double phi_root,
+                                      int incl_root, int buf4, int xs, int ys, DD& acc, double& ab, bool& bad) {
+  if (M <= 3) {
+    const int excl_above = (n - M) - incl_root;
+    double v = 0.0, a = 0.0;
+    if (M == 1) {
+      HM<2> R2;
+      lane_load_node<2>(L, root, root_o, R2);
+      Subtree<2>::run(R2, phi_root, v, a, bad);
+    } else if (M == 2) {
+      HM<4> R4;
+      lane_load_node<4>(L, root, root_o, R4);
+      Subtree<4>::run(R4, phi_root, v, a, bad);
+    } else {
+      HM<6> R6;
+      lane_load_node<6>(L, root, root_o, R6);
+      Subtree<6>::run(R6, phi_root, v, a, bad);
+    }
+    if (excl_above & 1) v = -v;
+    acc.add(v);
+    ab += a;
+    return;
+  }
+  int nb[65], nof[65];
+  double ph[65];
+  nb[M] = root;
+  nof[M] = root_o;
+  ph[M] = phi_root;
+  for (int m = M - 1; m >= 4; --m) {
+    nb[m] = nb[m + 1];
+    nof[m] = nof[m + 1] + 2;
+    ph[m] = ph[m + 1];
+  }
+  const unsigned long long count = 1ull << (M - 3);
+  for (unsigned long long c = 0; c < count; ++c) {
+    if (c != 0 && (c & 1ull) == 0) {
+      const int mi = 4 + __ffsll((long long)c) - 1;
+      const int dst = buf4 + stack_off(mi - 1);
+      const double rho = lane_include_mem(L, nb[mi], nof[mi], mi, dst, 0, xs, ys, bad);
+      nb[mi - 1] = dst;
+      nof[mi - 1] = 0;
+      ph[mi - 1] = ph[mi] * rho;
+      for (int m = mi - 2; m >= 4; --m) {
+        nb[m] = nb[m + 1];
+        nof[m] = nof[m + 1] + 2;
+        ph[m] = ph[m + 1];
+      }
+    }
+    HM<6> R3;
+    double phi3;
+    if (c & 1ull) {
+      phi3 = ph[4] * lane_include4(L, nb[4], nof[4], R3, bad);
+    } else {
+      lane_load_trail4(L, nb[4], nof[4], R3);
+      phi3 = ph[4];
+    }
+    double v, a;
+    Subtree<6>::run(R3, phi3, v, a, bad);
+    const int excl_above = (n - 3) - (incl_root + __popcll(c));
+    if (excl_above & 1) v = -v;
+    acc.add(v);
+    ab += a;
+  }
+}
+
+// ------------------------------------------------------------------ kernels
+
+__global__ void k_intake(const MatDesc* __restrict__ mats, int check, int* __restrict__ flags) {
+  const MatDesc D = mats[blockIdx.x];
+  const int n = D.n, R = 2 * n;
+  __shared__ unsigned long long s_max, s_dev;
+  __shared__ int s_bad;
+  if (threadIdx.x == 0) { s_max = 0; s_dev = 0; s_bad = 0; }
+  __syncthreads();
+  double mx = 0.0, dev = 0.0;
+  int bad = 0;
+  for (int r = 0; r < R; ++r) {
+    const int pr = D.layout == 0 ? (r >> 1) + (r & 1) * n : r;
+    for (int s = threadIdx.x; s <= r; s += blockDim.x) {
+      const int ps = D.layout == 0 ? (s >> 1) + (s & 1) * n : s;
+      const double2 a = D.O[(size_t)pr * D.ld + ps];
+      const double2 b = D.O[(size_t)ps * D.ld + pr];
+      if (!isfinite(a.x) || !isfinite(a.y) || !isfinite(b.x) || !isfinite(b.y)) bad = 1;
+      mx = fmax(mx, fmax(hypot(a.x, a.y), hypot(b.x, b.y)));
+      dev = fmax(dev, hypot(a.x - b.x, a.y + b.y));
+      D.B[P(r, s)] = r == s ? make_double2(1.0 - a.x, 0.0) : make_double2(-a.x, -a.y);
+    }
+  }
+  // reduce (values are non-negative, so their bit patterns order like the values)
+  atomicMax(&s_max, (unsigned long long)__double_as_longlong(mx));
+  atomicMax(&s_dev, (unsigned long long)__double_as_longlong(dev));
+  if (bad) atomicOr(&s_bad, 1);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int f = 0;
+    const double gmax = __longlong_as_double((long long)s_max), gdev = __longlong_as_double((long long)s_dev);
+    if (s_bad) f |= FLAG_NONFINITE;
+    if (check && !(gdev <= 1e-12 * gmax)) f |= FLAG_NOTHERM;
+    flags[blockIdx.x] = f;
+  }
+}
+
+__device__ __forceinline__ void write_partial(const UnitsParams& prm, const MatDesc& D, int mat, long long u,
+                                              DD acc, double ab, bool bad) {
+  double hi, lo;
+  fast_two_sum(acc.s, acc.c, hi, lo);
+  prm.partials[D.part_off + u] = Part{hi, lo, ab, 0.0};
+  if (bad) atomicOr(&prm.mat_flags[mat], FLAG_NOTPD);
+}
+
+// p >= 5: the warp builds the task node (depth p - 5) cooperatively, fans it
+// out breadth-first over 5 more levels into 32 unit roots, one per lane, and
+// each lane walks its own subtree.
+__device__ void run_task_shared(const UnitsParams& prm, const TaskDesc T, const LaneMem L, double2* WS, int lane) {
+  const MatDesc D = prm.mats[T.mat];
+  const int n = D.n, p = D.p, M = n - p, m0 = M + 5;
+  double2* SB = WS;
+  double2* arena = WS + tri_size(n);
+  double2* xsw = arena + arena_off(m0, 5);
+  double2* ysw = xsw + 4 * n;
+  bool bad = false;
+  // 1. task node: decisions on modes 0..p-6 are the bits of T.sub (same for all lanes)
+  const double2* src = D.B;
+  int o = 0, incl = 0;
+  double phi = 1.0;
+  bool own = false;
+  for (int j = 0; j < p - 5; ++j) {
+    if ((T.sub >> j) & 1) {
+      double rho;
+      if (!own) {
+        rho = coop_include(src, o, n - j, SB, 0, xsw, ysw, bad);
+        src = SB;
+        o = 0;
+        own = true;
+      } else {
+        rho = coop_include(SB, o, n - j, SB, o + 2, xsw, ysw, bad);
+        o += 2;
+      }
+      phi *= rho;
+      ++incl;
+    } else {
+      o += 2;
+    }
+  }
+  // 2. breadth-first fan-out: lane q holds level-d node q (bit e of q = decision on mode p-5+e)
+  const double2* nptr = src;
+  int no = o, nincl = incl;
+  double nphi = phi;
+  for (int d = 0; d < 5; ++d) {
+    const int nodes = 1 << d, m = m0 - d;
+    for (int q = 0; q < nodes; ++q) {
+      const double2* qp = (const double2*)__shfl_sync(0xffffffffu, (unsigned long long)nptr, q);
+      const int qo = __shfl_sync(0xffffffffu, no, q);
+      const double qphi = __shfl_sync(0xffffffffu, nphi, q);
+      const int qincl = __shfl_sync(0xffffffffu, nincl, q);
+      double2* dst = arena + arena_off(m0, d) + q * tri_size(m - 1);
+      const double rho = coop_include(qp, qo, m, dst, 0, xsw, ysw, bad);
+      if (lane == (q | nodes)) {
+        nptr = dst;
+        no = 0;
+        nphi = qphi * rho;
+        nincl = qincl + 1;
+      }
+    }
+    if (lane < nodes) no += 2;
+  }
+  // 3. copy the lane's unit root into its private stack
+  const int RR = 2 * M;
+  for (int i = 0; i < RR; ++i)
+    for (int k = 0; k <= i; ++k) L.st(P(i, k), nptr[P(i + no, k + no)]);
+  const int root_sz = tri_size(M);
+  const int xs = root_sz + stack_off(M), ys = xs + 2 * n;
+  DD acc{0.0, 0.0};
+  double ab = 0.0;
+  lane_dfs(L, 0, 0, M, n, nphi, nincl, root_sz, xs, ys, acc, ab, bad);
+  const long long u = (long long)T.sub | ((long long)lane << (p - 5));
+  write_partial(prm, D, T.mat, u, acc, ab, bad);
+}
+
+// p < 5: lanes take units of up to 32 small matrices of one size; each lane
+// builds its own root from B by in-place includes.
+__device__ void run_task_lanes(const UnitsParams& prm, const TaskDesc T, const LaneMem L, int lane) {
+  const int p = prm.mats[T.mat].p;
+  const long long q = (long long)T.sub * kWarp + lane;
+  if (q >= ((long long)T.nmat << p)) return;
+  const int mat = T.mat + (int)(q >> p);
+  const MatDesc D = prm.mats[mat];
+  const int n = D.n, M = n - p;
+  const long long u = q & ((1ll << p) - 1);
+  const int RR = 2 * n;
+  for (int i = 0; i < RR; ++i)
+    for (int k = 0; k <= i; ++k) L.st(P(i, k), D.B[P(i, k)]);
+  const int root_sz = tri_size(n);
+  const int xs = root_sz + stack_off(M), ys = xs + 2 * n;
+  bool bad = false;
+  int o = 0, incl = 0;
+  double phi = 1.0;
+  for (int j = 0; j < p; ++j) {
+    if ((u >> j) & 1) {
+      phi *= lane_include_mem(L, 0, o, n - j, 0, o + 2, xs, ys, bad);
+      ++incl;
+    }
+    o += 2;
+  }
+  DD acc{0.0, 0.0};
+  double ab = 0.0;
+  lane_dfs(L, 0, o, M, n, phi, incl, root_sz, xs, ys, acc, ab, bad);
+  write_partial(prm, D, mat, u, acc, ab, bad);
+}
+
+constexpr int kUnitsThreads = 128;
+
+__global__ void __launch_bounds__(kUnitsThreads, 2) k_units(const UnitsParams prm) {
+  const int lane = threadIdx.x & (kWarp - 1);
+  const long long gw = (long long)blockIdx.x * (blockDim.x / kWarp) + threadIdx.x / kWarp;
+  const LaneMem L{prm.lane_scratch + gw * kWarp * prm.lane_elems + lane};
+  double2* WS = prm.warp_scratch + gw * prm.warp_elems;
+  const unsigned long long t0 = global_ns();
+  for (;;) {
+    unsigned t = 0xffffffffu;
+    if (lane == 0) {
+      int ab = 0;
+      if (*prm.cancel) ab = ABORT_CANCEL;
+      else if (prm.budget_ns > 0 && (long long)(global_ns() - t0) > prm.budget_ns) ab = ABORT_TIMEOUT;
+      if (ab) atomicOr(prm.abort_word, ab);
+      else if (*(volatile int*)prm.abort_word == 0) t = atomicAdd(prm.ticket, 1u);
+    }
+    t = __shfl_sync(0xffffffffu, t, 0);
+    if (t >= (unsigned)prm.ntasks) break;
+    const TaskDesc T = prm.tasks[t];
+    if (prm.mats[T.mat].p >= 5) run_task_shared(prm, T, L, WS, lane);
+    else run_task_lanes(prm, T, L, lane);
+    __syncwarp();
+  }
+}
+
+// Binary tree over the 2^p partials of each matrix: thread t reduces an
+// aligned block of 2^k leaves pairwise, then the threads' results are
+// combined pairwise in shared memory.  The shape depends on p only.
+constexpr int kReduceThreads = 256;
+__global__ void __launch_bounds__(kReduceThreads) k_reduce(const MatDesc* __restrict__ mats,
+                                                           const Part* __restrict__ partials,
+                                                           const int* __restrict__ flags, ResultRec* out) {
+  const MatDesc D = mats[blockIdx.x];
+  const long long U = 1ll << D.p;
+  const int T = (int)(U < kReduceThreads ? U : kReduceThreads);
+  const long long chunk = U / T;
+  const Part* x = partials + D.part_off;
+  __shared__ double sh[kReduceThreads], sl[kReduceThreads], sa[kReduceThreads];
+  const int t = threadIdx.x;
+  if (t < T) {
+    double h_st[40], l_st[40], a_st[40];
+    int top = 0;
+    for (long long i = 0; i < chunk; ++i) {
+      const Part v = x[(long long)t * chunk + i];
+      double h = v.hi, l = v.lo, a = v.abs_sum;
+      for (long long k = i; k & 1; k >>= 1) {
+        --top;
+        dd_add(h_st[top], l_st[top], h, l, h, l);
+        a = a_st[top] + a;
+      }
+      h_st[top] = h;
+      l_st[top] = l;
+      a_st[top] = a;
+      ++top;
+    }
+    sh[t] = h_st[0];
+    sl[t] = l_st[0];
+    sa[t] = a_st[0];
+  }
+  __syncthreads();
+  for (int s = 1; s < T; s <<= 1) {
+    if (t < T && (t % (2 * s)) == 0) {
+      double h, l;
+      dd_add(sh[t], sl[t], sh[t + s], sl[t + s], h, l);
+      sh[t] = h;
+      sl[t] = l;
+      sa[t] = sa[t] + sa[t + s];
+    }
+    __syncthreads();
+  }
+  if (t == 0) {
+    ResultRec r;
+    r.hi = sh[0];
+    r.lo = sl[0];
+    r.abs_sum = sa[0];
+    r.flags = flags[blockIdx.x];
+    r.pad = 0;
+    out[blockIdx.x] = r;
+  }
+}
+
+// FP64 throughput probe: independent FMA chains, 8 warps per SM.
+__global__ void __launch_bounds__(256) k_probe(double* out, int iters) {
+  double a0 = 1e-3, a1 = 2e-3, a2 = 3e-3, a3 = 4e-3;
+  const double b = 0.9999999, c = 1e-9 * (threadIdx.x + 1);
+  for (int i = 0; i < iters; ++i) {
+    a0 = fma(a0, b, c);
+    a1 = fma(a1, b, c);
+    a2 = fma(a2, b, c);
+    a3 = fma(a3, b, c);
+  }
+  out[blockIdx.x * blockDim.x + threadIdx.x] = a0 + a1 + a2 + a3;
+}
+
+// ------------------------------------------------------------------ launchers
+
+cudaError_t launch_intake(const MatDesc* d_mats, int nmats, int check, int* d_flags, cudaStream_t s) {
+  if (nmats <= 0) return cudaSuccess;
+  k_intake<<<nmats, 128, 0, s>>>(d_mats, check, d_flags);
+  return cudaGetLastError();
+}
+cudaError_t launch_units(const UnitsParams& prm, int grid, cudaStream_t s) {
+  if (prm.ntasks <= 0) return cudaSuccess;
+  k_units<<<grid, kUnitsThreads, 0, s>>>(prm);
+  return cudaGetLastError();
+}
+cudaError_t launch_reduce(const MatDesc* d_mats, int nmats, const Part* partials, const int* flags,
+                          ResultRec* out, cudaStream_t s) {
+  if (nmats <= 0) return cudaSuccess;
+  k_reduce<<<nmats, kReduceThreads, 0, s>>>(d_mats, partials, flags, out);
+  return cudaGetLastError();
+}
+int units_block_threads() { return kUnitsThreads; }
+cudaError_t units_blocks_per_sm(int* blocks) {
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, k_units, kUnitsThreads, 0);
+}
+
+cudaError_t run_probe_fp64(double seconds, double* dfma_per_s) {
+  int dev = 0, sms = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+  const int blocks = sms, threads = 256;
+  double* d = nullptr;
+  if ((e = cudaMalloc(&d, sizeof(double) * blocks * threads)) != cudaSuccess) return e;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  int iters = 20000;
+  float ms = 0.f;
+  for (int rep = 0; rep < 6; ++rep) {  // grow until the run is long enough
+    cudaEventRecord(e0);
+    k_probe<<<blocks, threads>>>(d, iters);
+    cudaEventRecord(e1);
+    if ((e = cudaEventSynchronize(e1)) != cudaSuccess) break;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (ms > 1000.0 * seconds || rep == 5) break;
+    double scale = (1000.0 * seconds) / (ms > 0.01f ? ms : 0.01f);
+    if (scale > 100) scale = 100;
+    iters = (int)(iters * scale * 1.05) + 1;
+  }
+  if (e == cudaSuccess) e = cudaGetLastError();
+  *dfma_per_s = (double)blocks * threads * iters * 4.0 / (ms * 1e-3);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(d);
+  return e;
+}
+
+}  // namespace tor

@@ -1,0 +1,212 @@
+"""GPU parity: the CUDA path through the C ABI against the binary128 oracle.
+
+Pass criterion (element by element, same seeded inputs):
+    |Tor_gpu - Tor_oracle| <= 1e-10 * sum_Z |term_Z|
+where sum|term| is the oracle's.  Product states are also checked against the
+closed form prod_j (x_j - 1).
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+from paper_2109_04528_gb300 import binding, inputs
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-10
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    from paper_2109_04528_gb300 import build
+    build.build()
+    c = binding.Context(device=0)
+    yield c
+    c.close()
+
+
+def gpu_err(got, ref):
+    return abs((got.hi - ref.hi) + (got.lo - ref.lo))
+
+
+def closed_product(inst):
+    sh, ch = np.sinh(inst.r), np.cosh(inst.r)
+    N = inst.eta * sh * sh
+    M = inst.eta * sh * ch
+    x = np.sqrt((1 + N) ** 2 - M ** 2)
+    return float(np.prod(x - 1)), float(np.prod(x + 1))
+
+
+def test_golden_fixture(ctx):
+    with open(os.path.join(HERE, "golden", "lossy_n8.json")) as f:
+        g = json.load(f)
+    O = np.array(g["O_re"]) + 1j * np.array(g["O_im"])
+    r = binding.tor_eval(ctx, O)
+    assert r.status == 0
+    assert abs((r.hi - g["tor_hi"]) + (r.lo - g["tor_lo"])) <= TOL * g["abs_sum"]
+    assert abs(r.abs_sum - g["abs_sum"]) <= 1e-12 * g["abs_sum"]
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 4, 5, 6, 7, 9, 11, 12, 13, 14, 15, 16])
+def test_random_lossy_vs_oracle(ctx, oracle_mod, n):
+    inst = inputs.lossy_squeezed(n, 500 + n, (0.3, 0.8), (0.3, 0.7))
+    r = binding.tor_eval(ctx, inst.O)
+    ref = oracle_mod.tor_brute(inst.O)
+    assert r.status == 0
+    assert gpu_err(r, ref) <= TOL * ref.abs_sum, (r, ref)
+    assert abs(r.abs_sum - ref.abs_sum) <= 1e-12 * ref.abs_sum
+
+
+@pytest.mark.parametrize("n", [3, 8, 10, 13])
+def test_general_hermitian_vs_oracle(ctx, oracle_mod, n):
+    inst = inputs.random_hermitian_contraction(n, 600 + n, 0.85)
+    r = binding.tor_eval(ctx, inst.O)
+    ref = oracle_mod.tor_brute(inst.O)
+    assert gpu_err(r, ref) <= TOL * ref.abs_sum
+
+
+def test_every_prefix_depth_agrees(ctx, oracle_mod):
+    # p < 5 (lane-built roots) and p >= 5 (shared prefix + fan-out), every M
+    n = 12
+    inst = inputs.lossy_squeezed(n, 77, (0.5, 1.2), 0.4)
+    ref = oracle_mod.tor_brute(inst.O)
+    old = ctx.plan_prefix_depth(n)
+    try:
+        for p in range(0, n):
+            ctx.set_prefix_depth(n, p)
+            r = binding.tor_eval(ctx, inst.O)
+            assert r.status == 0
+            assert gpu_err(r, ref) <= TOL * ref.abs_sum, p
+    finally:
+        ctx.set_prefix_depth(n, old)
+
+
+@pytest.mark.parametrize("n", [6, 13, 20, 24])
+def test_product_state_closed_form(ctx, n):
+    inst = inputs.product_state(n, 700 + n)
+    want, absum = closed_product(inst)
+    r = binding.tor_eval(ctx, inst.O)
+    assert r.status == 0
+    assert abs(r.tor - want) <= TOL * absum
+    assert abs(r.abs_sum - absum) <= 1e-11 * absum
+
+
+def test_high_squeezing_product_relative(ctx):
+    # kappa = sum|term| / |Tor| is moderate here, so the relative error is informative
+    inst = inputs.product_state(16, 91, (1.5, 2.5), (0.8, 1.0))
+    want, absum = closed_product(inst)
+    r = binding.tor_eval(ctx, inst.O)
+    assert abs(r.tor - want) <= 1e-9 * abs(want)
+
+
+def test_vacuum_is_exactly_zero(ctx):
+    for n in (1, 5, 12):
+        r = binding.tor_eval(ctx, inputs.vacuum(n).O)
+        assert r.tor == 0.0 and r.abs_sum == float(2 ** n)
+
+
+def test_n0_and_errors(ctx):
+    r = binding.tor_eval(ctx, np.zeros((0, 0), dtype=np.complex128))
+    assert r.tor == 1.0 and r.status == 0
+    with pytest.raises(binding.TorError) as e:
+        binding.tor_eval(ctx, 2 * np.eye(4, dtype=np.complex128))  # I - O = -I: not PD
+    assert e.value.status == binding.TOR_ENOTPD
+    bad = inputs.lossy_squeezed(3, 1).O.copy()
+    bad[0, 1] += 1e-3
+    with pytest.raises(binding.TorError) as e:
+        binding.tor_eval(ctx, bad)
+    assert e.value.status == binding.TOR_ENOTHERM
+    nan = inputs.lossy_squeezed(3, 1).O.copy()
+    nan[2, 2] = np.nan
+    with pytest.raises(binding.TorError) as e:
+        binding.tor_eval(ctx, nan)
+    assert e.value.status == binding.TOR_EINVAL
+    with pytest.raises(binding.TorError) as e:
+        binding.tor_eval(ctx, np.zeros((130, 130), dtype=np.complex128))
+    assert e.value.status == binding.TOR_ETOOBIG
+    # the context is still usable
+    r = binding.tor_eval(ctx, inputs.config_n8().O)
+    assert r.status == 0
+
+
+def test_layout_pairs_equals_block(oracle_mod):
+    inst = inputs.lossy_squeezed(9, 3, (0.3, 0.8), 0.5)
+    with binding.Context(device=0, layout=binding.TOR_LAYOUT_PAIRS) as c2:
+        r2 = binding.tor_eval(c2, inputs.to_pairs(inst.O))
+    ref = oracle_mod.tor_brute(inst.O)
+    assert gpu_err(r2, ref) <= TOL * ref.abs_sum
+
+
+def test_invariances(ctx):
+    inst = inputs.lossy_squeezed(10, 8, (0.3, 0.8), 0.5)
+    base = binding.tor_eval(ctx, inst.O)
+    rng = np.random.default_rng(4)
+    for O in (inputs.permute_modes(inst.O, rng.permutation(10)),
+              inputs.local_phase(inst.O, rng.uniform(0, 6.3, 10))):
+        r = binding.tor_eval(ctx, O)
+        assert abs(r.tor - base.tor) <= TOL * base.abs_sum
+
+
+def test_batch_bitwise_equals_single(ctx):
+    rng = np.random.default_rng(11)
+    mats = [inputs.lossy_squeezed(int(k), 900 + i, (0.5, 1.2), 0.4).O
+            for i, k in enumerate(rng.integers(1, 19, size=40))]
+    batch = binding.tor_eval_batch(ctx, mats)
+    for O, b in zip(mats, batch):
+        s = binding.tor_eval(ctx, O)
+        assert (s.hi, s.lo, s.abs_sum, s.status) == (b.hi, b.lo, b.abs_sum, b.status)
+
+
+def test_deterministic_repeat(ctx):
+    inst = inputs.config_single(20)
+    a = binding.tor_eval(ctx, inst.O)
+    b = binding.tor_eval(ctx, inst.O)
+    assert (a.hi, a.lo, a.abs_sum) == (b.hi, b.lo, b.abs_sum)
+
+
+def test_units_at_full_size_sampled(ctx, oracle_mod):
+    # n = 24 (the largest single size of the n=16/20/24 workload) in the launch
+    # configuration the benchmark uses: sampled unit partials vs the oracle,
+    # the total vs the sum of the partials.
+    inst = inputs.config_single(24)
+    res, p, parts = binding.tor_eval_units(ctx, inst.O)
+    assert res.status == 0 and p >= 5
+    rng = np.random.default_rng(2)
+    for u in [0, (1 << p) - 1] + list(rng.integers(0, 1 << p, size=4)):
+        ref = oracle_mod.tor_unit(inst.O, p, int(u))
+        got_hi, got_lo, got_abs = parts[int(u)]
+        assert abs((got_hi - ref.hi) + (got_lo - ref.lo)) <= TOL * ref.abs_sum, u
+        assert abs(got_abs - ref.abs_sum) <= 1e-12 * ref.abs_sum
+    assert abs(res.tor - parts[:, 0].sum()) <= 1e-9 * res.abs_sum
+
+
+def test_device_input_equals_host():
+    torch = pytest.importorskip("torch")
+    inst = inputs.lossy_squeezed(11, 12, (0.3, 0.8), 0.5)
+    with binding.Context(device=0) as ch:
+        h = binding.tor_eval(ch, inst.O)
+    t = torch.from_numpy(inst.O).to("cuda:0")
+    with binding.Context(device=0, flags=binding.TOR_IN_DEVICE) as cd:
+        d = binding.tor_eval(cd, t)
+    assert (h.hi, h.lo, h.abs_sum) == (d.hi, d.lo, d.abs_sum)
+
+
+def test_timeout_returns_status_and_context_survives():
+    inst = inputs.config_single(30)
+    with binding.Context(device=0, timeout_s=0.002) as c:
+        r = binding.tor_eval(c, inst.O, check=False)
+        assert r.status == binding.TOR_ETIMEOUT
+    with binding.Context(device=0) as c:
+        assert binding.tor_eval(c, inputs.config_n8().O).status == 0
+
+
+def test_submit_poll(ctx, oracle_mod):
+    mats = [inputs.lossy_squeezed(k, 40 + k, (0.3, 0.9), 0.5).O for k in (3, 7, 10, 12)]
+    tickets = [binding.tor_submit(ctx, O) for O in mats]
+    for O, t in zip(mats, tickets):
+        st, r = binding.tor_poll(ctx, t, 60.0)
+        ref = oracle_mod.tor_brute(O)
+        assert st == 0 and gpu_err(r, ref) <= TOL * ref.abs_sum
