@@ -1,0 +1,337 @@
+"""Benchmark: exact Torontonians through libtor on GB300.
+
+One step = one tor_eval_batch over a workload's matrices (intake, units,
+reduce: every step of the hot path).  Workloads (seeded synthetic inputs):
+
+  single_n16_20_24 (default)  lossy squeezed states n = 16, 20, 24
+                              (r ~ U[0.3,0.8], per-mode eta ~ U[0.3,0.7], Haar U)
+                              plus a product state at n = 24
+  single_n30 / single_n34 / single_n38   one lossy squeezed state of that size
+  batch4096                   4096 click patterns k ~ U{4..24} of one 100-mode state
+
+Metric: subset terms per second (sum of 2^n over the step's matrices / time).
+`value` times the device-resident path (inputs already on the GPU), `e2e` the
+same call with host buffers (H2D of O and D2H of results inside the region).
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
+       python bench.py --impl reference ...   (the CPU oracle, bounded sample)
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+from paper_2109_04528_gb300 import inputs  # noqa: E402
+
+L2_FLUSH_BYTES = 512 << 20  # > 129 MB L2
+
+
+def workload(name: str, rank: int = 0):
+    """(list of O matrices, description)."""
+    off = 7919 * rank
+    if name == "single_n16_20_24":
+        mats = [inputs.config_single(n, seed=inputs.SEED_BASE + 1000 + n + off).O for n in (16, 20, 24)]
+        mats.append(inputs.product_state(24, inputs.SEED_BASE + 2024 + off).O)
+        return mats, "lossy squeezed n=16,20,24 (r~U[0.3,0.8], eta_j~U[0.3,0.7]) + product state n=24"
+    if name.startswith("single_n"):
+        n = int(name[len("single_n"):])
+        return [inputs.config_single(n, seed=inputs.SEED_BASE + 1000 + n + off).O], \
+            f"lossy squeezed n={n} (r~U[0.3,0.8], eta_j~U[0.3,0.7])"
+    if name == "batch4096":
+        _, _, mats = inputs.click_pattern_batch(100, 4096, 4, 24, inputs.SEED_BASE + 3 + off, (0.5, 1.2), 0.4)
+        return mats, "4096 submatrices of a 100-mode lossy squeezed state (r~U[0.5,1.2], eta=0.4), k~U{4..24}"
+    raise SystemExit(f"unknown workload {name}")
+
+
+def csrc_hash() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_2109_04528_gb300", "csrc")
+    for f in sorted(os.listdir(d)):
+        h.update(f.encode())
+        with open(os.path.join(d, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(workload_name: str):
+    """DRAM bytes per k_units launch from the committed ncu capture, if it was
+    taken on this workload and on the kernel sources as they are now."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "k_units_traffic.json")) as f:
+            t = json.load(f)
+    except (OSError, ValueError):
+        return None
+    if t.get("workload") != workload_name or t.get("csrc_hash") != csrc_hash():
+        return None
+    return t.get("dram_bytes_per_launch")
+
+
+def algorithmic_flops(n: int) -> float:
+    """F(n) = sum_j 2^j (32 m_j^2 + 40 m_j + 10) + 10 2^n, m_j = n-1-j:
+    FP64 flops of the rank-2 subset-tree walk (complex MAC = 8 flops,
+    complex x real = 2, sqrt/rsqrt/div = 1)."""
+    f = 10.0 * 2.0 ** n
+    for j in range(n):
+        m = n - 1 - j
+        f += 2.0 ** j * (32 * m * m + 40 * m + 10)
+    return f
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        time.sleep(0.25)
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        time.sleep(0.15)
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx = max(mx, float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx or None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if args.impl != "reference" else "gloo"
+        dist.init_process_group(backend)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(world, x: float, device) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def cpu_baseline(mats, budget_s: float):
+    """The oracle (binary128 brute force) on a bounded sample: the first `count`
+    subsets of the workload's largest matrix, on all host cores."""
+    import oracle
+    oracle.build()
+    O = max(mats, key=lambda a: a.shape[0])
+    n = O.shape[0] // 2
+    cores = os.cpu_count() or 1
+    count = 1 << min(n, 10)
+    t0 = time.perf_counter()
+    oracle.tor_brute(O, threads=cores, count=count)
+    dt = time.perf_counter() - t0
+    while dt < 0.5 and count < (1 << n):  # calibrate
+        count = min(1 << n, count * 4)
+        t0 = time.perf_counter()
+        oracle.tor_brute(O, threads=cores, count=count)
+        dt = time.perf_counter() - t0
+    count = int(min(1 << n, max(count, count * budget_s / max(dt, 1e-3))))
+    t0 = time.perf_counter()
+    oracle.tor_brute(O, threads=cores, count=count)
+    dt = time.perf_counter() - t0
+    return {"value": count / dt, "unit": "subset terms/s", "cores": cores, "kind": "oracle",
+            "sample": f"first {count} of the 2^{n} subsets of the n={n} matrix, binary128 LU per subset, "
+                      f"{dt:.1f} s"}
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return 0
+    mats, desc = workload(args.workload)
+    import oracle
+    oracle.build()
+    cores = os.cpu_count() or 1
+    O = max(mats, key=lambda a: a.shape[0])
+    n = O.shape[0] // 2
+    # size one step to ~2 s of CPU work
+    count = 1 << min(n, 8)
+    t0 = time.perf_counter()
+    oracle.tor_brute(O, threads=cores, count=count)
+    dt = time.perf_counter() - t0
+    count = int(min(1 << n, max(count, count * 2.0 / max(dt, 1e-3))))
+    for _ in range(args.warmup):
+        oracle.tor_brute(O, threads=cores, count=count)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.tor_brute(O, threads=cores, count=count)
+        times.append(time.perf_counter() - t0)
+    tot = sum(times)
+    value = count * args.steps / tot
+    line = {"impl": "reference", "metric": "subset terms/s", "value": value, "unit": "subset terms/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f128",
+            "data": "synthetic", "config": {"workload": args.workload, "desc": desc},
+            "cpu_baseline": {"value": value, "unit": "subset terms/s", "cores": cores, "kind": "oracle",
+                             "sample": f"each step: first {count} of the 2^{n} subsets of the n={n} matrix"},
+            "e2e": {"value": value, "unit": "subset terms/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--workload", default="single_n16_20_24")
+    ap.add_argument("--impl", default="libtor", choices=["libtor", "reference"])
+    ap.add_argument("--cpu-budget", type=float, default=12.0, help="seconds of oracle time for cpu_baseline")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl != "reference":
+        args.warmup = 3
+    world, rank, local = dist_setup(args)
+    if args.impl == "reference":
+        return run_reference(args, world, rank)
+
+    import torch
+
+    from paper_2109_04528_gb300 import binding, build
+    build.build()
+    device = torch.device("cuda", local)
+    torch.cuda.set_device(device)
+    mats, desc = workload(args.workload, rank)
+    ns = [m.shape[0] // 2 for m in mats]
+    terms = float(sum(2.0 ** n for n in ns))
+    flops = float(sum(algorithmic_flops(n) for n in ns))
+    stream = torch.cuda.Stream(device=device)
+    dmats = [torch.from_numpy(m).to(device) for m in mats]
+    ctx_dev = binding.Context(device=local, stream=stream.cuda_stream, flags=binding.TOR_IN_DEVICE)
+    ctx_host = binding.Context(device=local, stream=stream.cuda_stream)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=device)
+    dfma, fp64_tflops = binding.tor_probe_fp64(local, 0.5)
+
+    def timed(ctx, batch, k):
+        ms, units_ms = [], []
+        for _ in range(k):
+            with torch.cuda.stream(stream):
+                flush.fill_(1.0)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            res = binding.tor_eval_batch(ctx, batch)
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+            units_ms.append(ctx.last_times()["units_ms"])
+            for r in res:
+                if r.status != 0:
+                    raise SystemExit(f"evaluation failed: status {r.status}")
+        return ms, units_ms
+
+    timed(ctx_dev, dmats, args.warmup)
+    barrier(world)
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        ms, units_ms = timed(ctx_dev, dmats, args.steps)
+    torch.cuda.synchronize()
+    barrier(world)
+    tot_ms = max_over_ranks(world, sum(ms), device)
+    # end to end: host buffers, H2D + kernels + D2H per step
+    timed(ctx_host, mats, 2)
+    barrier(world)
+    e2e_ms, _ = timed(ctx_host, mats, args.steps)
+    barrier(world)
+    e2e_tot = max_over_ranks(world, sum(e2e_ms), device)
+    value = terms * world * args.steps / (tot_ms * 1e-3)
+    e2e_value = terms * world * args.steps / (e2e_tot * 1e-3)
+    units_avg = sum(units_ms) / len(units_ms)
+    achieved = flops / (units_avg * 1e-3) / 1e12
+    line = {
+        "metric": "subset terms/s", "value": value, "unit": "subset terms/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": tot_ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": args.workload, "desc": desc, "n": ns, "terms_per_step": terms,
+                   "l2": "flushed between steps (512 MB write)",
+                   "prefix_depth": {str(n): ctx_dev.plan_prefix_depth(n) for n in sorted(set(ns))}},
+        "tor_per_s": len(mats) * world * args.steps / (tot_ms * 1e-3),
+        "e2e": {"value": e2e_value, "unit": "subset terms/s",
+                "h2d_bytes_per_step": int(sum(m.size * 16 for m in mats)),
+                "d2h_bytes_per_step": int(32 * len(mats))},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": fp64_tflops, "unit": "TFLOP/s",
+                     "frac": achieved / fp64_tflops, "traffic": profiled_traffic(args.workload),
+                     "kernel": "k_units", "peak_source": "FP64 DFMA probe (tor_probe_fp64), measured in this run",
+                     "flops_per_launch": flops, "units_ms_avg": units_avg},
+        "gpu_launches": 3 * args.steps,
+        "clocks": clk.summary(),
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(mats, args.cpu_budget)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    ctx_dev.close()
+    ctx_host.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())
