@@ -154,6 +154,42 @@ tor_status tor_last_times(tor_ctx* ctx, double* times);
  * second and FP64 TFLOP/s (2 flops per DFMA). */
 tor_status tor_probe_fp64(int device, double seconds, double* dfma_per_s, double* fp64_tflops);
 
+/* ---- evaluation without allocation ---- */
+
+/* Largest n tor_eval_noalloc accepts. */
+#define TOR_NOALLOC_MAX_N 16
+
+/* Tor of one matrix with no memory allocation of any kind, for callers that
+ * must not allocate while they run (a process whose device memory is owned by
+ * a pre-reserved pool, a latency-critical loop in which cudaMalloc/cudaFree
+ * would synchronise the device, a plugin allowed to allocate only at start-up).
+ * The paper has no counterpart; it is a deployment variant of tor_eval.
+ *
+ *   device  CUDA device ordinal; the call makes it current and restores the
+ *           caller's current device before returning.
+ *   n, O, ld, layout
+ *           as for tor_eval, but O is a DEVICE pointer on `device`
+ *           (row-major complex128, leading dimension ld >= 2n).
+ *   stream  cudaStream_t on `device` (NULL = the legacy default stream).
+ *   out     DEVICE pointer to one tor_result, written by the GPU.
+ *
+ * The call only enqueues work on `stream` and returns; synchronise the stream
+ * before reading *out.  Per-matrix failures (not Hermitian, not positive
+ * definite, non-finite input) appear in out->status.  The return value covers
+ * the call itself: TOR_ETOOBIG for n > TOR_NOALLOC_MAX_N, TOR_EINVAL for bad
+ * arguments (n < 1, NULL pointers, ld < 2n, unknown layout or device),
+ * TOR_ECUDA if a launch fails.
+ *
+ * All intermediate data lives in one static device array of 8 MiB compiled
+ * into the library, which every device that loads the library keeps until
+ * the process exits.  Calls share it: calls whose GPU work overlaps (other
+ * streams or threads on the same device) race and must be ordered by the
+ * caller.  The first call on each device looks up the array's device address
+ * (and may load the library's GPU module), so make that first call before
+ * any stream capture starts. */
+tor_status tor_eval_noalloc(int device, int n, const tor_c128* O, int ld, int layout, void* stream,
+                            tor_result* out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -24,7 +24,9 @@ TOR_IN_DEVICE, TOR_NO_CHECK = 1, 2
 # Every symbol include/tor.h declares (the ABI test checks the library exports them).
 EXPORTS = ["tor_config_default", "tor_create", "tor_destroy", "tor_eval", "tor_eval_batch", "tor_submit",
            "tor_poll", "tor_cancel", "tor_strerror", "tor_last_error", "tor_plan_prefix_depth",
-           "tor_set_prefix_depth", "tor_eval_units", "tor_last_times", "tor_probe_fp64"]
+           "tor_set_prefix_depth", "tor_eval_units", "tor_last_times", "tor_probe_fp64",
+           "tor_eval_noalloc"]
+TOR_NOALLOC_MAX_N = 16
 
 
 class TorError(RuntimeError):
@@ -100,6 +102,7 @@ def load_library():
     lib.tor_eval_units.argtypes = [c_void_p, c_int, c_void_p, c_int, P(c_double), c_size_t, P(tor_result)]
     lib.tor_last_times.argtypes = [c_void_p, P(c_double)]
     lib.tor_probe_fp64.argtypes = [c_int, c_double, P(c_double), P(c_double)]
+    lib.tor_eval_noalloc.argtypes = [c_int, c_int, c_void_p, c_int, c_int, c_void_p, c_void_p]
     _LIB = lib
     return lib
 
