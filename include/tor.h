@@ -54,15 +54,24 @@ typedef enum {
   TOR_ETIMEOUT = 6,   /* the evaluation ran past tor_config.timeout_s and was stopped */
   TOR_ECANCELED = 7,  /* the evaluation was cancelled with tor_cancel */
   TOR_ECUDA = 8,      /* a CUDA runtime call failed; see tor_last_error */
-  TOR_ETOOBIG = 9     /* n > 64 */
+  TOR_ETOOBIG = 9     /* n > 64 (or above the limit of the call) */
 } tor_status;
 
 typedef struct { double re, im; } tor_c128;
 
 enum { TOR_LAYOUT_BLOCK = 0, TOR_LAYOUT_PAIRS = 1 };
-enum { TOR_IN_DEVICE = 1u, TOR_NO_CHECK = 2u };
+/* tor_config.flags:
+ *   TOR_IN_DEVICE  O pointers of tor_eval* are device pointers (e.g. torch CUDA tensors)
+ *   TOR_NO_CHECK   skip the Hermitian / finiteness check of the input
+ *   TOR_GRAPHS     capture each evaluation pass into a CUDA graph and replay it for
+ *                  later calls of the same shape (same sizes in the same order) */
+enum { TOR_IN_DEVICE = 1u, TOR_NO_CHECK = 2u, TOR_GRAPHS = 4u };
+
+/* tor_session_create kinds */
+enum { TOR_SESSION_SIGMA = 0, TOR_SESSION_O = 1 };
 
 typedef struct tor_ctx tor_ctx;
+typedef struct tor_session tor_session;
 
 typedef struct {
   int device;          /* CUDA device ordinal */
@@ -116,6 +125,36 @@ tor_status tor_submit(tor_ctx* ctx, int n, const tor_c128* O, int ld, uint64_t* 
  * already collected ticket, else the request's status with *out filled. */
 tor_status tor_poll(tor_ctx* ctx, uint64_t ticket, tor_result* out, double timeout_s);
 
+/* Served requests, completed batches and requests still queued (any may be NULL). */
+tor_status tor_serving_stats(tor_ctx* ctx, long long* served, long long* batches, long long* queued);
+
+/* ---- chain-rule marginals (threshold GBS sampling, paper Sec. 1) ----
+ *
+ * Sampling click patterns mode by mode needs Tor of the sampling matrix of
+ * every prefix of the modes: O^(j) = I - (Sigma_[j])^{-1}, where Sigma_[j] is
+ * the covariance of modes 0..j-1 (Eq. A applied to the marginal state), and
+ * the click probability of a pattern S on those modes is
+ * Tor(O^(j)_S) / sqrt(det Sigma_[j]).
+ *
+ * tor_session_create takes the full n_total-mode covariance Sigma
+ * (kind TOR_SESSION_SIGMA) or sampling matrix O (kind TOR_SESSION_O), 2n x 2n
+ * with leading dimension ld in the context's layout, computes every O^(j)
+ * on the host (extended precision, one rank-2 downdate of Sigma^{-1} per
+ * mode) and keeps them all resident on the device (16 * sum_j 4 j^2 bytes,
+ * ~64 MB for 144 modes).  The caller's buffer may be freed afterwards. */
+tor_status tor_session_create(tor_ctx* ctx, int n_total, const tor_c128* M, int ld, int kind,
+                              tor_session** out);
+void tor_session_destroy(tor_session* s);
+
+/* Tor(O^(j)_S) for S = modes[0..k-1] (distinct, each < j, any order), blocking. */
+tor_status tor_eval_marginal(tor_ctx* ctx, tor_session* s, int j, int k, const int* modes,
+                             tor_result* out);
+
+/* Queues the same evaluation for the serving loop (see tor_submit); poll the
+ * ticket with tor_poll.  The mode list is copied. */
+tor_status tor_submit_marginal(tor_ctx* ctx, tor_session* s, int j, int k, const int* modes,
+                               uint64_t* ticket);
+
 /* Asks the kernels running for this context to stop at their next unit
  * boundary; the affected results get TOR_ECANCELED.  Thread-safe. */
 tor_status tor_cancel(tor_ctx* ctx);
@@ -148,6 +187,21 @@ tor_status tor_eval_units(tor_ctx* ctx, int n, const tor_c128* O, int ld, double
  * events on the context's stream: [0] intake, [1] units, [2] reduce, [3] total
  * (ms).  times must hold 4 doubles. */
 tor_status tor_last_times(tor_ctx* ctx, double* times);
+
+/* Autotuner: for every n in [n_lo, n_hi], times tor_eval at prefix depths
+ * around the built-in plan (control flow depends on n and p only, so a fixed
+ * synthetic matrix serves) and keeps the fastest for this context.  Spends
+ * about budget_s seconds in total.  chosen (may be NULL) receives
+ * n_hi - n_lo + 1 depths.  Not for contexts created with TOR_IN_DEVICE. */
+tor_status tor_autotune(tor_ctx* ctx, int n_lo, int n_hi, double budget_s, int* chosen);
+
+/* Writes / reads the context's prefix-depth table (text: "n p" per line,
+ * plus the resident warp count it was tuned for).  tor_plan_load rejects a
+ * table tuned for a different number of resident warps with TOR_EINVAL.
+ * tor_create loads the table named by the environment variable
+ * TOR_AUTOTUNE_CACHE, if set, unless cfg->prefix_depth >= 0. */
+tor_status tor_plan_save(tor_ctx* ctx, const char* path);
+tor_status tor_plan_load(tor_ctx* ctx, const char* path);
 
 /* Measures the device's FP64 FMA throughput with a saturating kernel (all SMs,
  * 8 warps each, independent chains) for about `seconds`.  Writes DFMA per

@@ -19,13 +19,15 @@ TOR_OK, TOR_EINVAL, TOR_ENOTHERM, TOR_ENOTPD, TOR_ENOMEM, TOR_EAGAIN, TOR_ETIMEO
 STATUS_NAMES = ["TOR_OK", "TOR_EINVAL", "TOR_ENOTHERM", "TOR_ENOTPD", "TOR_ENOMEM", "TOR_EAGAIN",
                 "TOR_ETIMEOUT", "TOR_ECANCELED", "TOR_ECUDA", "TOR_ETOOBIG"]
 TOR_LAYOUT_BLOCK, TOR_LAYOUT_PAIRS = 0, 1
-TOR_IN_DEVICE, TOR_NO_CHECK = 1, 2
+TOR_IN_DEVICE, TOR_NO_CHECK, TOR_GRAPHS = 1, 2, 4
+TOR_SESSION_SIGMA, TOR_SESSION_O = 0, 1
 
 # Every symbol include/tor.h declares (the ABI test checks the library exports them).
 EXPORTS = ["tor_config_default", "tor_create", "tor_destroy", "tor_eval", "tor_eval_batch", "tor_submit",
            "tor_poll", "tor_cancel", "tor_strerror", "tor_last_error", "tor_plan_prefix_depth",
            "tor_set_prefix_depth", "tor_eval_units", "tor_last_times", "tor_probe_fp64",
-           "tor_eval_noalloc"]
+           "tor_eval_noalloc", "tor_autotune", "tor_plan_save", "tor_plan_load", "tor_serving_stats",
+           "tor_session_create", "tor_session_destroy", "tor_eval_marginal", "tor_submit_marginal"]
 TOR_NOALLOC_MAX_N = 16
 
 
@@ -103,6 +105,16 @@ def load_library():
     lib.tor_last_times.argtypes = [c_void_p, P(c_double)]
     lib.tor_probe_fp64.argtypes = [c_int, c_double, P(c_double), P(c_double)]
     lib.tor_eval_noalloc.argtypes = [c_int, c_int, c_void_p, c_int, c_int, c_void_p, c_void_p]
+    lib.tor_autotune.argtypes = [c_void_p, c_int, c_int, c_double, P(c_int)]
+    lib.tor_plan_save.argtypes = [c_void_p, ctypes.c_char_p]
+    lib.tor_plan_load.argtypes = [c_void_p, ctypes.c_char_p]
+    LL = ctypes.c_longlong
+    lib.tor_serving_stats.argtypes = [c_void_p, P(LL), P(LL), P(LL)]
+    lib.tor_session_create.argtypes = [c_void_p, c_int, c_void_p, c_int, c_int, P(c_void_p)]
+    lib.tor_session_destroy.argtypes = [c_void_p]
+    lib.tor_session_destroy.restype = None
+    lib.tor_eval_marginal.argtypes = [c_void_p, c_void_p, c_int, c_int, P(c_int), P(tor_result)]
+    lib.tor_submit_marginal.argtypes = [c_void_p, c_void_p, c_int, c_int, P(c_int), P(ctypes.c_uint64)]
     _LIB = lib
     return lib
 
@@ -194,6 +206,30 @@ class Context:
     def cancel(self):
         self._lib.tor_cancel(self.handle)
 
+    def autotune(self, n_lo: int, n_hi: int, budget_s: float = 5.0):
+        """Tune the prefix depth for n in [n_lo, n_hi]; returns {n: p}."""
+        k = n_hi - n_lo + 1
+        chosen = (ctypes.c_int * k)()
+        st = self._lib.tor_autotune(self.handle, n_lo, n_hi, budget_s, chosen)
+        if st != TOR_OK:
+            raise TorError(st, self.last_error() or "tor_autotune")
+        return {n_lo + i: chosen[i] for i in range(k)}
+
+    def serving_stats(self):
+        s, bt, q = ctypes.c_longlong(), ctypes.c_longlong(), ctypes.c_longlong()
+        self._lib.tor_serving_stats(self.handle, ctypes.byref(s), ctypes.byref(bt), ctypes.byref(q))
+        return {"served": s.value, "batches": bt.value, "queued": q.value}
+
+    def save_plan(self, path: str):
+        st = self._lib.tor_plan_save(self.handle, os.fsencode(path))
+        if st != TOR_OK:
+            raise TorError(st, "tor_plan_save")
+
+    def load_plan(self, path: str):
+        st = self._lib.tor_plan_load(self.handle, os.fsencode(path))
+        if st != TOR_OK:
+            raise TorError(st, "tor_plan_load")
+
 
 def tor_create(**kw) -> Context:
     return Context(**kw)
@@ -280,3 +316,56 @@ def tor_probe_fp64(device: int = 0, seconds: float = 0.5):
     if st != TOR_OK:
         raise TorError(st, "tor_probe_fp64")
     return d.value, t.value
+
+
+class Session:
+    """Resident chain-rule prefix matrices O^(j) of one Gaussian state (tor_session_create)."""
+
+    def __init__(self, ctx: Context, M, kind: int = TOR_SESSION_SIGMA):
+        a, n, ld = _host_matrix(M)
+        h = ctypes.c_void_p()
+        st = ctx._lib.tor_session_create(ctx.handle, n, ctypes.c_void_p(a.ctypes.data), ld, kind, ctypes.byref(h))
+        if st != TOR_OK:
+            raise TorError(st, ctx.last_error() or "tor_session_create")
+        self._h, self.ctx, self.n = h, ctx, n
+
+    def close(self):
+        if getattr(self, "_h", None) is not None:
+            self.ctx._lib.tor_session_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+def _modes_arg(modes):
+    k = len(modes)
+    return k, (ctypes.c_int * max(k, 1))(*[int(x) for x in modes])
+
+
+def tor_eval_marginal(ctx: Context, session: Session, j: int, modes, check: bool = True) -> TorResult:
+    """Tor(O^(j)_S), S = modes (each < j)."""
+    k, arr = _modes_arg(modes)
+    res = tor_result()
+    st = ctx._lib.tor_eval_marginal(ctx.handle, session._h, j, k, arr, ctypes.byref(res))
+    if check and st != TOR_OK:
+        raise TorError(st, ctx.last_error() or "tor_eval_marginal")
+    return TorResult.of(res)
+
+
+def tor_submit_marginal(ctx: Context, session: Session, j: int, modes) -> int:
+    k, arr = _modes_arg(modes)
+    t = ctypes.c_uint64()
+    st = ctx._lib.tor_submit_marginal(ctx.handle, session._h, j, k, arr, ctypes.byref(t))
+    if st != TOR_OK:
+        raise TorError(st, "tor_submit_marginal")
+    return int(t.value)

@@ -1,9 +1,15 @@
 // tor_host.cu -- host runtime and C ABI of libtor (declared in include/tor.h).
 //
-// A call to tor_eval / tor_eval_batch runs, on the context's stream:
-//   H2D copy of the inputs -> k_intake -> k_units (persistent) -> k_reduce -> D2H
-// and then waits for the stream.  tor_submit / tor_poll feed a serving thread
-// that batches queued requests into the same pipeline.
+// A job is a list of matrices evaluated by one pass of the GPU pipeline
+//   H2D (inputs, descriptors) -> k_intake -> k_units (persistent) -> k_reduce -> D2H
+// on one "slot": a stream plus its own device and pinned buffers.  The
+// blocking calls (tor_eval, tor_eval_batch, ...) use the context's main slot.
+// tor_submit / tor_submit_marginal feed a serving thread that keeps several
+// slots in flight on separate streams: requests that arrive while jobs run are
+// admitted into the next free slot as soon as the device-memory budget allows,
+// so a new job starts on SMs that the previous job's tail leaves idle.
+// With TOR_GRAPHS a slot captures its whole pass into a CUDA graph and
+// replays it for every later job of the same shape.
 #include <algorithm>
 #include <atomic>
 #include <chrono>
@@ -14,6 +20,7 @@
 #include <cstring>
 #include <deque>
 #include <map>
+#include <memory>
 #include <mutex>
 #include <string>
 #include <thread>
@@ -29,17 +36,24 @@ namespace {
 struct DevBuf {
   void* p = nullptr;
   size_t cap = 0;
-  cudaError_t ensure(size_t bytes) {
-    if (bytes <= cap) return cudaSuccess;
+  // grows (never shrinks); bumps *gen when the address changes
+  cudaError_t ensure(size_t bytes, uint64_t* gen) {
+    if (bytes <= cap && p) return cudaSuccess;
+    bytes = std::max<size_t>(bytes, 256);
+    size_t want = std::max(bytes, cap + cap / 2);
     if (p) cudaFree(p);
     p = nullptr;
     cap = 0;
-    size_t want = std::max(bytes, cap * 3 / 2);
+    ++*gen;
     cudaError_t e = cudaMalloc(&p, want);
     if (e != cudaSuccess) {
       cudaGetLastError();
       e = cudaMalloc(&p, bytes);
-      if (e != cudaSuccess) { cudaGetLastError(); p = nullptr; return e; }
+      if (e != cudaSuccess) {
+        cudaGetLastError();
+        p = nullptr;
+        return e;
+      }
       want = bytes;
     }
     cap = want;
@@ -55,14 +69,20 @@ struct DevBuf {
 struct HostBuf {
   void* p = nullptr;
   size_t cap = 0;
-  cudaError_t ensure(size_t bytes) {
-    if (bytes <= cap) return cudaSuccess;
+  cudaError_t ensure(size_t bytes, uint64_t* gen) {
+    if (bytes <= cap && p) return cudaSuccess;
+    bytes = std::max<size_t>(bytes, 256);
+    size_t want = std::max(bytes, cap + cap / 2);
     if (p) cudaFreeHost(p);
     p = nullptr;
     cap = 0;
-    size_t want = std::max(bytes, cap * 3 / 2);
+    ++*gen;
     cudaError_t e = cudaMallocHost(&p, want);
-    if (e != cudaSuccess) { cudaGetLastError(); p = nullptr; return e; }
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      p = nullptr;
+      return e;
+    }
     cap = want;
     return cudaSuccess;
   }
@@ -74,31 +94,89 @@ struct HostBuf {
 };
 
 inline int tri(int n) { return n * (2 * n + 1); }
+inline double now_s() {
+  return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+// One matrix of a job, as the caller described it.
+struct MatIn {
+  int n = 0;                    // modes of the matrix to evaluate
+  const tor_c128* O = nullptr;  // source matrix (host, or device if dev)
+  int ld = 0;                   // leading dimension of O (complex elements)
+  int n_src = 0;                // modes of the source matrix
+  int layout = TOR_LAYOUT_BLOCK;
+  bool dev = false;             // O is a device pointer
+  const int* modes = nullptr;   // host list of n source modes (session marginals), or null
+};
+
+struct Slot {
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  DevBuf d_O, d_B, d_mats, d_tasks, d_partials, d_flags, d_results, d_lane, d_warp, d_ctl, d_modes;
+  HostBuf h_O, h_mats, h_tasks, h_results, h_ctl, h_modes;
+  cudaEvent_t ev[5] = {};
+  cudaEvent_t done = nullptr;
+  uint64_t gen = 0;
+  struct Graph {
+    uint64_t key, gen;
+    cudaGraphExec_t exec;
+  };
+  std::vector<Graph> graphs;
+  // the prepared job
+  std::vector<int> act;  // index into the caller's list, job order
+  std::vector<MatDesc> mats;
+  std::vector<TaskDesc> tasks;
+  int J = 0;
+  long long o_elems = 0, b_elems = 0, parts = 0, reds = 0, mode_elems = 0, lane_e = 0, warp_e = 0;
+  bool want_parts = false;
+  size_t bytes = 0;
+  int cancel_epoch = 0;
+  bool busy = false;
+
+  void release() {
+    for (DevBuf* b : {&d_O, &d_B, &d_mats, &d_tasks, &d_partials, &d_flags, &d_results, &d_lane, &d_warp, &d_ctl,
+                      &d_modes})
+      b->release();
+    for (HostBuf* b : {&h_O, &h_mats, &h_tasks, &h_results, &h_ctl, &h_modes}) b->release();
+    for (auto& g : graphs) cudaGraphExecDestroy(g.exec);
+    graphs.clear();
+    for (int i = 0; i < 5; ++i)
+      if (ev[i]) cudaEventDestroy(ev[i]);
+    if (done) cudaEventDestroy(done);
+    if (own_stream && stream) cudaStreamDestroy(stream);
+    stream = nullptr;
+  }
+};
 
 }  // namespace
 
+struct tor_session {
+  tor_ctx* ctx = nullptr;
+  int N = 0;
+  DevBuf d_O;                  // O^(j) for j = 1..N, pairs layout, 2j x 2j row-major each
+  std::vector<long long> off;  // element offset of O^(j)
+  uint64_t gen = 0;
+};
+
 struct Request {
-  uint64_t ticket;
-  int n;
-  std::vector<tor_c128> O;  // 2n x 2n, ld = 2n
-  tor_result res;
+  uint64_t ticket = 0;
+  MatIn in;
+  std::vector<tor_c128> O;  // owned copy of a host matrix
+  std::vector<int> modes;   // owned copy of a marginal's mode list
+  tor_result res{};
   bool done = false;
 };
 
 struct tor_ctx {
   tor_config cfg{};
-  cudaStream_t stream = nullptr;
-  bool own_stream = false;
   int sms = 0, blocks_per_sm = 0, grid = 0, nwarps = 0;
   int plan[65];
-  DevBuf d_O, d_B, d_mats, d_tasks, d_partials, d_flags, d_results, d_lane, d_warp, d_ctl;
-  HostBuf h_O, h_mats, h_tasks, h_results, h_ctl;
-  int* h_cancel = nullptr;  // host-mapped
+  Slot main;
+  int* h_cancel = nullptr;  // host-mapped cancel counter
   int* d_cancel = nullptr;
-  cudaEvent_t ev[5] = {};
   double last_times[4] = {0, 0, 0, 0};
   std::string last_error;
-  std::mutex run_mu;
+  std::mutex run_mu;  // serialises use of the main slot and the plan table
   // serving
   std::mutex q_mu;
   std::condition_variable q_cv, done_cv;
@@ -107,7 +185,11 @@ struct tor_ctx {
   uint64_t next_ticket = 1;
   std::thread server;
   bool server_started = false, stopping = false;
-  size_t queue_limit = 1 << 16;
+  size_t queue_limit = 1 << 20;
+  int n_serve_slots = 2;
+  int max_batch = 4096;
+  std::vector<std::unique_ptr<Slot>> serve;
+  std::atomic<long long> served{0}, batches{0};
 };
 
 static tor_status cuda_fail(tor_ctx* ctx, cudaError_t e, const char* what) {
@@ -120,9 +202,9 @@ static tor_status cuda_fail(tor_ctx* ctx, cudaError_t e, const char* what) {
   return e == cudaErrorMemoryAllocation ? TOR_ENOMEM : TOR_ECUDA;
 }
 
-#define CK(call, what)                                   \
-  do {                                                   \
-    cudaError_t e_ = (call);                             \
+#define CK(call, what)                                      \
+  do {                                                      \
+    cudaError_t e_ = (call);                                \
     if (e_ != cudaSuccess) return cuda_fail(ctx, e_, what); \
   } while (0)
 
@@ -137,6 +219,552 @@ static int default_prefix_depth(int n, int nwarps) {
   M = std::min(M, n - 1);
   return n - M;
 }
+
+static int plan_p(tor_ctx* ctx, int n) {
+  int p;
+  if (ctx->plan[n] >= 0) p = ctx->plan[n];
+  else if (ctx->cfg.prefix_depth >= 0) p = ctx->cfg.prefix_depth;
+  else p = default_prefix_depth(n, ctx->nwarps);
+  return std::max(0, std::min(p, n - 1));
+}
+
+static cudaError_t slot_init(Slot& s, cudaStream_t stream) {
+  cudaError_t e;
+  if (stream) {
+    s.stream = stream;
+    s.own_stream = false;
+  } else {
+    if ((e = cudaStreamCreateWithFlags(&s.stream, cudaStreamNonBlocking)) != cudaSuccess) return e;
+    s.own_stream = true;
+  }
+  for (int i = 0; i < 5; ++i)
+    if ((e = cudaEventCreate(&s.ev[i])) != cudaSuccess) return e;
+  return cudaEventCreateWithFlags(&s.done, cudaEventDisableTiming);
+}
+
+// Device bytes a job of these matrices needs (what admission checks).
+static size_t job_bytes(tor_ctx* ctx, const std::vector<MatIn>& ins, size_t count) {
+  long long o = 0, b = 0, parts = 0, md = 0, lane_e = 0, warp_e = 0, ntask = 0;
+  for (size_t i = 0; i < count; ++i) {
+    const MatIn& m = ins[i];
+    if (m.n < 1 || m.n > 64) continue;
+    const int p = plan_p(ctx, m.n);
+    if (!m.dev && !m.modes) o += 4ll * m.n * m.n;
+    if (m.modes) md += m.n;
+    b += tri(m.n);
+    parts += 2ll << p;
+    ntask += p >= 5 ? (1ll << (p - 5)) : 1;
+    lane_e = std::max(lane_e, lane_elems_for(m.n, p));
+    warp_e = std::max(warp_e, warp_elems_for(m.n, p));
+  }
+  return (size_t)(o * 16 + b * 16 + parts * 32 + md * 4 + ntask * (long long)sizeof(TaskDesc) +
+                  (long long)count * (long long)(sizeof(MatDesc) + sizeof(ResultRec) + 4)) +
+         (size_t)ctx->nwarps * 32 * lane_e * 16 + (size_t)ctx->nwarps * warp_e * 16 + 4096;
+}
+
+// Validates the inputs, fills trivial results, plans the job and fills the
+// slot's pinned staging buffers.  Returns the first error; *any = job has work.
+static tor_status slot_prepare(tor_ctx* ctx, Slot& S, const std::vector<MatIn>& ins, tor_result* out,
+                               bool want_parts, bool* any) {
+  *any = false;
+  tor_status first = TOR_OK;
+  auto note = [&](tor_status s) {
+    if (first == TOR_OK && s != TOR_OK) first = s;
+  };
+  const int count = (int)ins.size();
+  S.act.clear();
+  S.J = 0;
+  for (int i = 0; i < count; ++i) {
+    const MatIn& m = ins[i];
+    tor_result& r = out[i];
+    memset(&r, 0, sizeof r);
+    r.n = m.n;
+    if (m.n < 0) r.status = TOR_EINVAL;
+    else if (m.n > 64) r.status = TOR_ETOOBIG;
+    else if (m.n == 0) {
+      r.hi = 1.0;
+      r.abs_sum = 1.0;
+      r.status = TOR_OK;
+    } else if (!m.O || (!m.modes && m.ld < 2 * m.n) || (m.modes && m.ld < 2 * m.n_src)) r.status = TOR_EINVAL;
+    else {
+      S.act.push_back(i);
+      continue;
+    }
+    note(r.status);
+  }
+  if (S.act.empty()) return first;
+  // job order: by n descending so equal sizes are adjacent (stable: same n keeps caller order)
+  std::stable_sort(S.act.begin(), S.act.end(), [&](int a, int b) { return ins[a].n > ins[b].n; });
+  const int J = (int)S.act.size();
+  S.mats.assign(J, MatDesc{});
+  S.tasks.clear();
+  S.o_elems = S.b_elems = S.parts = S.reds = S.mode_elems = S.lane_e = S.warp_e = 0;
+  for (int j = 0; j < J; ++j) {
+    const MatIn& m = ins[S.act[j]];
+    const int p = plan_p(ctx, m.n);
+    MatDesc& D = S.mats[j];
+    D.n = m.n;
+    D.p = p;
+    D.layout = m.layout;
+    D.n_src = m.modes ? m.n_src : m.n;
+    D.part_off = S.parts;
+    S.parts += 1ll << p;
+    D.red_log2 = p >= 5 ? p - 5 : p;
+    D.red_off = S.reds;
+    S.reds += 1ll << D.red_log2;
+    S.b_elems += tri(m.n);
+    if (!m.dev && !m.modes) S.o_elems += 4ll * m.n * m.n;
+    if (m.modes) S.mode_elems += m.n;
+    S.lane_e = std::max(S.lane_e, lane_elems_for(m.n, p));
+    S.warp_e = std::max(S.warp_e, warp_elems_for(m.n, p));
+  }
+  // warp tasks, largest subtrees first
+  for (int j = 0; j < J;) {
+    int k = j;
+    while (k < J && S.mats[k].n == S.mats[j].n) ++k;
+    const int p = S.mats[j].p, M = S.mats[j].n - p;
+    if (p >= 5) {
+      for (int a = j; a < k; ++a)
+        for (int t = 0; t < (1 << (p - 5)); ++t) S.tasks.push_back({a, t, 1, M});
+    } else {
+      const long long units = (long long)(k - j) << p;
+      for (long long t = 0; t * 32 < units; ++t) S.tasks.push_back({j, (int)t, k - j, M});
+    }
+    j = k;
+  }
+  std::stable_sort(S.tasks.begin(), S.tasks.end(), [](const TaskDesc& a, const TaskDesc& b) { return a.M > b.M; });
+  S.want_parts = want_parts;
+  // buffers
+  const size_t lane_bytes = (size_t)ctx->nwarps * 32 * S.lane_e * sizeof(double2);
+  const size_t warp_bytes = (size_t)ctx->nwarps * S.warp_e * sizeof(double2);
+  S.bytes = job_bytes(ctx, ins, ins.size());
+  if (ctx->cfg.mem_budget && S.bytes > ctx->cfg.mem_budget) {
+    for (int j = 0; j < J; ++j) out[S.act[j]].status = TOR_ENOMEM;
+    S.act.clear();
+    S.J = 0;
+    return TOR_ENOMEM;
+  }
+  uint64_t* g = &S.gen;
+  CK(S.d_O.ensure(S.o_elems * 16, g), "alloc O");
+  CK(S.d_B.ensure(S.b_elems * 16, g), "alloc B");
+  CK(S.d_partials.ensure((S.parts + S.reds) * 32, g), "alloc partials");
+  CK(S.d_mats.ensure(J * sizeof(MatDesc), g), "alloc mats");
+  CK(S.d_tasks.ensure(S.tasks.size() * sizeof(TaskDesc), g), "alloc tasks");
+  CK(S.d_flags.ensure(J * sizeof(int), g), "alloc flags");
+  CK(S.d_results.ensure(J * sizeof(ResultRec), g), "alloc results");
+  CK(S.d_lane.ensure(lane_bytes, g), "alloc lane scratch");
+  CK(S.d_warp.ensure(warp_bytes, g), "alloc warp scratch");
+  CK(S.d_ctl.ensure(64, g), "alloc control");
+  CK(S.d_modes.ensure(S.mode_elems * sizeof(int), g), "alloc modes");
+  CK(S.h_O.ensure(S.o_elems * 16, g), "pinned O");
+  CK(S.h_mats.ensure(J * sizeof(MatDesc), g), "pinned mats");
+  CK(S.h_tasks.ensure(S.tasks.size() * sizeof(TaskDesc), g), "pinned tasks");
+  CK(S.h_results.ensure(J * sizeof(ResultRec) + (want_parts ? S.parts * 32 : 0), g), "pinned results");
+  CK(S.h_ctl.ensure(64, g), "pinned control");
+  CK(S.h_modes.ensure(S.mode_elems * sizeof(int), g), "pinned modes");
+  // staging
+  long long oo = 0, bo = 0, mo = 0;
+  double2* dO = (double2*)S.d_O.p;
+  double2* dB = (double2*)S.d_B.p;
+  tor_c128* hO = (tor_c128*)S.h_O.p;
+  int* hm = (int*)S.h_modes.p;
+  for (int j = 0; j < J; ++j) {
+    const MatIn& m = ins[S.act[j]];
+    MatDesc& D = S.mats[j];
+    const int mm = 2 * m.n;
+    if (m.modes) {
+      D.O = (const double2*)m.O;  // resident session matrix
+      D.ld = m.ld;
+      memcpy(hm + mo, m.modes, sizeof(int) * m.n);
+      D.modes = (const int*)S.d_modes.p + mo;
+      mo += m.n;
+    } else if (m.dev) {
+      D.O = (const double2*)m.O;
+      D.ld = m.ld;
+      D.modes = nullptr;
+    } else {
+      for (int r = 0; r < mm; ++r)
+        memcpy(hO + oo + (long long)r * mm, m.O + (long long)r * m.ld, sizeof(tor_c128) * mm);
+      D.O = dO + oo;
+      D.ld = mm;
+      D.modes = nullptr;
+      oo += (long long)mm * mm;
+    }
+    D.B = dB + bo;
+    bo += tri(m.n);
+  }
+  memcpy(S.h_mats.p, S.mats.data(), J * sizeof(MatDesc));
+  memcpy(S.h_tasks.p, S.tasks.data(), S.tasks.size() * sizeof(TaskDesc));
+  S.J = J;
+  *any = true;
+  return first;
+}
+
+static uint64_t mix(uint64_t h, uint64_t v) {
+  h ^= v + 0x9E3779B97F4A7C15ull + (h << 6) + (h >> 2);
+  return h;
+}
+
+// The stream operations of one pass (what a graph captures).
+static tor_status slot_record(tor_ctx* ctx, Slot& S) {
+  cudaStream_t s = S.stream;
+  const int J = S.J;
+  CK(cudaEventRecord(S.ev[0], s), "event");
+  if (S.o_elems) CK(cudaMemcpyAsync(S.d_O.p, S.h_O.p, S.o_elems * 16, cudaMemcpyHostToDevice, s), "H2D O");
+  if (S.mode_elems)
+    CK(cudaMemcpyAsync(S.d_modes.p, S.h_modes.p, S.mode_elems * sizeof(int), cudaMemcpyHostToDevice, s), "H2D modes");
+  CK(cudaMemcpyAsync(S.d_mats.p, S.h_mats.p, J * sizeof(MatDesc), cudaMemcpyHostToDevice, s), "H2D mats");
+  CK(cudaMemcpyAsync(S.d_tasks.p, S.h_tasks.p, S.tasks.size() * sizeof(TaskDesc), cudaMemcpyHostToDevice, s),
+     "H2D tasks");
+  CK(cudaMemsetAsync(S.d_ctl.p, 0, 64, s), "memset control");
+  CK(cudaEventRecord(S.ev[1], s), "event");
+  const bool check = !(ctx->cfg.flags & TOR_NO_CHECK);
+  CK(launch_intake((const MatDesc*)S.d_mats.p, J, check ? 1 : 0, (int*)S.d_flags.p, s), "k_intake");
+  CK(cudaEventRecord(S.ev[2], s), "event");
+  UnitsParams prm;
+  prm.mats = (const MatDesc*)S.d_mats.p;
+  prm.tasks = (const TaskDesc*)S.d_tasks.p;
+  prm.ntasks = (int)S.tasks.size();
+  prm.ticket = (unsigned*)S.d_ctl.p;
+  prm.abort_word = (int*)S.d_ctl.p + 1;
+  prm.partials = (Part*)S.d_partials.p;
+  prm.red_leaves = (Part*)S.d_partials.p + S.parts;
+  prm.mat_flags = (int*)S.d_flags.p;
+  prm.lane_scratch = (double2*)S.d_lane.p;
+  prm.lane_elems = S.lane_e;
+  prm.warp_scratch = (double2*)S.d_warp.p;
+  prm.warp_elems = S.warp_e;
+  prm.cancel = ctx->d_cancel;
+  prm.cancel_epoch = S.cancel_epoch;
+  prm.budget_ns = ctx->cfg.timeout_s > 0 ? (long long)(ctx->cfg.timeout_s * 1e9) : 0;
+  CK(launch_units(prm, ctx->grid, s), "k_units");
+  CK(cudaEventRecord(S.ev[3], s), "event");
+  CK(launch_reduce((const MatDesc*)S.d_mats.p, J, (const Part*)S.d_partials.p + S.parts, (const int*)S.d_flags.p,
+                   (ResultRec*)S.d_results.p, s),
+     "k_reduce");
+  CK(cudaEventRecord(S.ev[4], s), "event");
+  CK(cudaMemcpyAsync(S.h_results.p, S.d_results.p, J * sizeof(ResultRec), cudaMemcpyDeviceToHost, s), "D2H results");
+  if (S.want_parts)
+    CK(cudaMemcpyAsync((char*)S.h_results.p + J * sizeof(ResultRec), S.d_partials.p, S.parts * 32,
+                       cudaMemcpyDeviceToHost, s),
+       "D2H partials");
+  CK(cudaMemcpyAsync(S.h_ctl.p, (int*)S.d_ctl.p + 1, sizeof(int), cudaMemcpyDeviceToHost, s), "D2H abort");
+  return TOR_OK;
+}
+
+// Enqueues the prepared job (graph replay when enabled and the shape repeats).
+static tor_status slot_launch(tor_ctx* ctx, Slot& S) {
+  S.cancel_epoch = __atomic_load_n(ctx->h_cancel, __ATOMIC_SEQ_CST);
+  if (!(ctx->cfg.flags & TOR_GRAPHS)) {
+    tor_status st = slot_record(ctx, S);
+    if (st != TOR_OK) return st;
+    CK(cudaEventRecord(S.done, S.stream), "event");
+    return TOR_OK;
+  }
+  uint64_t key = mix(0, (uint64_t)S.J);
+  for (const MatDesc& D : S.mats)
+    key = mix(key, (uint64_t)D.n | (uint64_t)D.p << 8 | (uint64_t)D.n_src << 16 | (uint64_t)D.layout << 28 |
+                       (uint64_t)(D.modes != nullptr) << 29);
+  key = mix(key, (uint64_t)S.o_elems);
+  key = mix(key, (uint64_t)S.mode_elems);
+  key = mix(key, (uint64_t)S.tasks.size());
+  key = mix(key, (uint64_t)S.want_parts);
+  key = mix(key, (uint64_t)S.lane_e << 1 ^ (uint64_t)S.warp_e << 33);
+  key = mix(key, (uint64_t)(uint32_t)S.cancel_epoch);
+  cudaGraphExec_t exec = nullptr;
+  for (auto& g : S.graphs)
+    if (g.key == key && g.gen == S.gen) exec = g.exec;
+  if (!exec) {
+    CK(cudaStreamBeginCapture(S.stream, cudaStreamCaptureModeThreadLocal), "begin capture");
+    tor_status st = slot_record(ctx, S);
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamEndCapture(S.stream, &graph);
+    if (st != TOR_OK) {
+      if (graph) cudaGraphDestroy(graph);
+      return st;
+    }
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "end capture");
+    e = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "graph instantiate");
+    // keep a small cache; entries of older buffer generations can never match again
+    std::vector<Slot::Graph> keep;
+    for (auto& g : S.graphs) {
+      if (g.gen != S.gen) cudaGraphExecDestroy(g.exec);
+      else keep.push_back(g);
+    }
+    S.graphs.swap(keep);
+    if (S.graphs.size() >= 16) {
+      cudaGraphExecDestroy(S.graphs.front().exec);
+      S.graphs.erase(S.graphs.begin());
+    }
+    S.graphs.push_back({key, S.gen, exec});
+  }
+  CK(cudaGraphLaunch(exec, S.stream), "graph launch");
+  CK(cudaEventRecord(S.done, S.stream), "event");
+  return TOR_OK;
+}
+
+// Reads back a finished job into out[] (indexed like the prepared inputs).
+static tor_status slot_finish(Slot& S, tor_result* out, double* unit_partials, double* times) {
+  tor_status first = TOR_OK;
+  const ResultRec* hr = (const ResultRec*)S.h_results.p;
+  const int abort_word = *(const int*)S.h_ctl.p;
+  for (int j = 0; j < S.J; ++j) {
+    tor_result& r = out[S.act[j]];
+    const ResultRec& q = hr[j];
+    r.hi = q.hi;
+    r.lo = q.lo;
+    r.abs_sum = q.abs_sum;
+    r.err_est = 8.0 * r.n * std::ldexp(1.0, -53) * q.abs_sum;
+    if (q.flags & FLAG_NONFINITE) r.status = TOR_EINVAL;
+    else if (q.flags & FLAG_NOTHERM) r.status = TOR_ENOTHERM;
+    else if (abort_word & ABORT_CANCEL) r.status = TOR_ECANCELED;
+    else if (abort_word & ABORT_TIMEOUT) r.status = TOR_ETIMEOUT;
+    else if (q.flags & FLAG_NOTPD) r.status = TOR_ENOTPD;
+    else r.status = TOR_OK;
+    if (first == TOR_OK && r.status != TOR_OK) first = r.status;
+  }
+  if (unit_partials && S.J == 1) {
+    const Part* hp = (const Part*)((const char*)S.h_results.p + S.J * sizeof(ResultRec));
+    const long long U = 1ll << S.mats[0].p;
+    for (long long u = 0; u < U; ++u) {
+      unit_partials[3 * u] = hp[u].hi;
+      unit_partials[3 * u + 1] = hp[u].lo;
+      unit_partials[3 * u + 2] = hp[u].abs_sum;
+    }
+  }
+  if (times) {
+    float ms[4] = {0, 0, 0, 0};
+    cudaEventElapsedTime(&ms[0], S.ev[1], S.ev[2]);
+    cudaEventElapsedTime(&ms[1], S.ev[2], S.ev[3]);
+    cudaEventElapsedTime(&ms[2], S.ev[3], S.ev[4]);
+    cudaEventElapsedTime(&ms[3], S.ev[0], S.ev[4]);
+    cudaGetLastError();
+    for (int i = 0; i < 4; ++i) times[i] = ms[i];
+  }
+  return first;
+}
+
+// Blocking evaluation on the main slot (caller holds run_mu).
+static tor_status run_blocking(tor_ctx* ctx, const std::vector<MatIn>& ins, tor_result* out, double* unit_partials,
+                               size_t unit_len) {
+  CK(cudaSetDevice(ctx->cfg.device), "cudaSetDevice");
+  for (int i = 0; i < 4; ++i) ctx->last_times[i] = 0;
+  Slot& S = ctx->main;
+  bool any = false;
+  tor_status first = slot_prepare(ctx, S, ins, out, unit_partials != nullptr, &any);
+  if (!any) return first;
+  if (unit_partials && (S.J != 1 || unit_len < 3ull * (1ull << S.mats[0].p))) return TOR_EINVAL;
+  tor_status st = slot_launch(ctx, S);
+  if (st != TOR_OK) return st;
+  CK(cudaStreamSynchronize(S.stream), "kernel execution");
+  tor_status fin = slot_finish(S, out, unit_partials, ctx->last_times);
+  return first != TOR_OK ? first : fin;
+}
+
+// ---------------------------------------------------------------------------
+// Serving thread: continuous batching over several slots.
+// ---------------------------------------------------------------------------
+static void complete(tor_ctx* ctx, std::vector<Request*>& reqs) {  // caller holds q_mu
+  for (Request* r : reqs) r->done = true;
+  ctx->done_cv.notify_all();
+}
+
+static void server_loop(tor_ctx* ctx) {
+  cudaSetDevice(ctx->cfg.device);
+  struct InFlight {
+    std::vector<Request*> reqs;
+    std::vector<tor_result> res;
+  };
+  std::vector<InFlight> fl(ctx->serve.size());
+  size_t reserved = 0;
+  for (;;) {
+    bool progressed = false;
+    // 1. completions
+    for (size_t i = 0; i < ctx->serve.size(); ++i) {
+      Slot& S = *ctx->serve[i];
+      if (!S.busy) continue;
+      const cudaError_t q = cudaEventQuery(S.done);
+      if (q == cudaErrorNotReady) continue;
+      if (q == cudaSuccess) {
+        slot_finish(S, fl[i].res.data(), nullptr, nullptr);
+      } else {
+        cudaGetLastError();
+        for (int a : S.act) fl[i].res[a].status = TOR_ECUDA;
+      }
+      {
+        std::lock_guard<std::mutex> lk(ctx->q_mu);
+        for (size_t k = 0; k < fl[i].reqs.size(); ++k) fl[i].reqs[k]->res = fl[i].res[k];
+        complete(ctx, fl[i].reqs);
+      }
+      ctx->served += (long long)fl[i].reqs.size();
+      ctx->batches += 1;
+      reserved -= S.bytes;
+      S.busy = false;
+      fl[i].reqs.clear();
+      fl[i].res.clear();
+      progressed = true;
+    }
+    // 2. admission into free slots
+    for (size_t i = 0; i < ctx->serve.size(); ++i) {
+      Slot& S = *ctx->serve[i];
+      if (S.busy) continue;
+      std::vector<Request*> batch;
+      {
+        std::lock_guard<std::mutex> lk(ctx->q_mu);
+        while (!ctx->queue.empty() && (int)batch.size() < ctx->max_batch) {
+          batch.push_back(ctx->queue.front());
+          ctx->queue.pop_front();
+        }
+      }
+      if (batch.empty()) break;
+      std::vector<MatIn> ins;
+      for (Request* r : batch) ins.push_back(r->in);
+      // device-memory budget: shrink the batch until it fits beside the jobs in flight
+      if (ctx->cfg.mem_budget) {
+        size_t need = job_bytes(ctx, ins, ins.size());
+        while (batch.size() > 1 && reserved + need > ctx->cfg.mem_budget) {
+          std::lock_guard<std::mutex> lk(ctx->q_mu);
+          ctx->queue.push_front(batch.back());
+          batch.pop_back();
+          ins.pop_back();
+          need = job_bytes(ctx, ins, ins.size());
+        }
+        if (reserved + need > ctx->cfg.mem_budget) {
+          std::lock_guard<std::mutex> lk(ctx->q_mu);
+          if (reserved == 0) {  // cannot fit even alone
+            batch[0]->res = tor_result{};
+            batch[0]->res.n = batch[0]->in.n;
+            batch[0]->res.status = TOR_ENOMEM;
+            complete(ctx, batch);
+          } else {  // wait for a job in flight to finish
+            ctx->queue.push_front(batch[0]);
+          }
+          break;
+        }
+      }
+      std::vector<tor_result> res(ins.size());
+      bool any = false;
+      tor_status st = slot_prepare(ctx, S, ins, res.data(), false, &any);
+      if (any) st = slot_launch(ctx, S);
+      if (!any || st == TOR_ECUDA || st == TOR_ENOMEM) {
+        // nothing to run, or the launch failed: complete now
+        std::lock_guard<std::mutex> lk(ctx->q_mu);
+        for (size_t k = 0; k < batch.size(); ++k) {
+          batch[k]->res = res[k];
+          if (any && std::find(S.act.begin(), S.act.end(), (int)k) != S.act.end()) batch[k]->res.status = st;
+        }
+        complete(ctx, batch);
+        continue;
+      }
+      S.busy = true;
+      reserved += S.bytes;
+      fl[i].reqs = std::move(batch);
+      fl[i].res = std::move(res);
+      progressed = true;
+    }
+    // 3. idle / stop
+    bool busy = false;
+    for (auto& s : ctx->serve) busy |= s->busy;
+    std::unique_lock<std::mutex> lk(ctx->q_mu);
+    if (ctx->stopping && !busy && ctx->queue.empty()) return;
+    if (!progressed) {
+      if (!busy && ctx->queue.empty()) ctx->q_cv.wait(lk, [&] { return ctx->stopping || !ctx->queue.empty(); });
+      else ctx->q_cv.wait_for(lk, std::chrono::microseconds(50));
+    }
+  }
+}
+
+static tor_status start_server(tor_ctx* ctx) {  // caller holds q_mu
+  if (ctx->server_started) return TOR_OK;
+  cudaSetDevice(ctx->cfg.device);
+  for (int i = 0; i < ctx->n_serve_slots; ++i) {
+    std::unique_ptr<Slot> s(new Slot());
+    cudaError_t e = slot_init(*s, nullptr);
+    if (e != cudaSuccess) {
+      s->release();
+      return cuda_fail(ctx, e, "serving slot");
+    }
+    ctx->serve.push_back(std::move(s));
+  }
+  ctx->server = std::thread(server_loop, ctx);
+  ctx->server_started = true;
+  return TOR_OK;
+}
+
+static tor_status enqueue_request(tor_ctx* ctx, Request* r, uint64_t* ticket) {
+  {
+    std::lock_guard<std::mutex> lk(ctx->q_mu);
+    if (ctx->queue.size() >= ctx->queue_limit) {
+      delete r;
+      return TOR_EAGAIN;
+    }
+    tor_status st = start_server(ctx);
+    if (st != TOR_OK) {
+      delete r;
+      return st;
+    }
+    r->ticket = ctx->next_ticket++;
+    ctx->reqs[r->ticket] = r;
+    ctx->queue.push_back(r);
+    *ticket = r->ticket;
+  }
+  ctx->q_cv.notify_one();
+  return TOR_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Sessions: resident chain-rule prefix matrices O^(j) = I - (Sigma_[j])^{-1}.
+// Computed on the host in long double: K = Sigma^{-1} (or I - O), then one
+// rank-2 downdate per removed mode, K_[j-1] = K_aa - K_ab K_bb^{-1} K_ba,
+// which is the inverse of the leading block Sigma_[j-1].
+// ---------------------------------------------------------------------------
+namespace {
+struct CL {
+  long double re, im;
+};
+inline CL cadd(CL a, CL b) { return {a.re + b.re, a.im + b.im}; }
+inline CL csub(CL a, CL b) { return {a.re - b.re, a.im - b.im}; }
+inline CL cmul(CL a, CL b) { return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re}; }
+inline CL cconj(CL a) { return {a.re, -a.im}; }
+
+// In-place inverse of an HPD matrix (m x m, row-major) via A = L L^H; false if not PD.
+bool hpd_inverse(std::vector<CL>& A, int m) {
+  std::vector<CL> L((size_t)m * m, CL{0, 0});
+  for (int i = 0; i < m; ++i) {
+    for (int j = 0; j <= i; ++j) {
+      CL s = A[(size_t)i * m + j];
+      for (int k = 0; k < j; ++k) s = csub(s, cmul(L[(size_t)i * m + k], cconj(L[(size_t)j * m + k])));
+      if (i == j) {
+        if (!(s.re > 0)) return false;
+        L[(size_t)i * m + i] = {sqrtl(s.re), 0};
+      } else {
+        const long double d = L[(size_t)j * m + j].re;
+        L[(size_t)i * m + j] = {s.re / d, s.im / d};
+      }
+    }
+  }
+  // W = L^{-1} (lower triangular), A^{-1} = W^H W
+  std::vector<CL> W((size_t)m * m, CL{0, 0});
+  for (int i = 0; i < m; ++i) {
+    W[(size_t)i * m + i] = {1.0L / L[(size_t)i * m + i].re, 0};
+    for (int j = 0; j < i; ++j) {
+      CL s{0, 0};
+      for (int k = j; k < i; ++k) s = csub(s, cmul(L[(size_t)i * m + k], W[(size_t)k * m + j]));
+      const long double d = L[(size_t)i * m + i].re;
+      W[(size_t)i * m + j] = {s.re / d, s.im / d};
+    }
+  }
+  for (int i = 0; i < m; ++i)
+    for (int j = 0; j < m; ++j) {
+      CL s{0, 0};
+      for (int k = std::max(i, j); k < m; ++k) s = cadd(s, cmul(cconj(W[(size_t)k * m + i]), W[(size_t)k * m + j]));
+      A[(size_t)i * m + j] = s;
+    }
+  return true;
+}
+}  // namespace
 
 extern "C" {
 
@@ -163,12 +791,14 @@ const char* tor_strerror(tor_status s) {
     case TOR_ETIMEOUT: return "timed out";
     case TOR_ECANCELED: return "cancelled";
     case TOR_ECUDA: return "CUDA error";
-    case TOR_ETOOBIG: return "too many modes (n > 64)";
+    case TOR_ETOOBIG: return "too many modes for this call";
   }
   return "unknown status";
 }
 
 const char* tor_last_error(tor_ctx* ctx) { return ctx ? ctx->last_error.c_str() : ""; }
+
+tor_status tor_plan_load(tor_ctx* ctx, const char* path);
 
 tor_status tor_create(const tor_config* cfg, tor_ctx** out) {
   if (!out) return TOR_EINVAL;
@@ -180,7 +810,10 @@ tor_status tor_create(const tor_config* cfg, tor_ctx** out) {
   if (c.timeout_s < 0) return TOR_EINVAL;
   int ndev = 0;
   cudaError_t e = cudaGetDeviceCount(&ndev);
-  if (e != cudaSuccess) { cudaGetLastError(); return TOR_ECUDA; }
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return TOR_ECUDA;
+  }
   if (c.device < 0 || c.device >= ndev) return TOR_EINVAL;
   tor_ctx* ctx = new tor_ctx();
   ctx->cfg = c;
@@ -197,20 +830,16 @@ tor_status tor_create(const tor_config* cfg, tor_ctx** out) {
   ctx->blocks_per_sm = std::max(1, ctx->blocks_per_sm);
   ctx->grid = ctx->sms * ctx->blocks_per_sm;
   ctx->nwarps = ctx->grid * (units_block_threads() / 32);
-  if (c.stream) {
-    ctx->stream = (cudaStream_t)c.stream;
-  } else {
-    if ((e = cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking)) != cudaSuccess)
-      return fail(e, "stream");
-    ctx->own_stream = true;
-  }
-  for (int i = 0; i < 5; ++i)
-    if ((e = cudaEventCreate(&ctx->ev[i])) != cudaSuccess) return fail(e, "event");
+  if ((e = slot_init(ctx->main, (cudaStream_t)c.stream)) != cudaSuccess) return fail(e, "stream/events");
   if ((e = cudaHostAlloc((void**)&ctx->h_cancel, sizeof(int), cudaHostAllocMapped)) != cudaSuccess)
     return fail(e, "cancel flag");
   *ctx->h_cancel = 0;
   if ((e = cudaHostGetDevicePointer((void**)&ctx->d_cancel, ctx->h_cancel, 0)) != cudaSuccess)
     return fail(e, "cancel flag map");
+  if (c.prefix_depth < 0) {
+    const char* cache = getenv("TOR_AUTOTUNE_CACHE");
+    if (cache && *cache) tor_plan_load(ctx, cache);  // a missing or foreign table is ignored
+  }
   *out = ctx;
   return TOR_OK;
 }
@@ -226,15 +855,11 @@ void tor_destroy(tor_ctx* ctx) {
   for (auto& kv : ctx->reqs) delete kv.second;
   ctx->reqs.clear();
   cudaSetDevice(ctx->cfg.device);
-  if (ctx->stream) cudaStreamSynchronize(ctx->stream);
-  for (DevBuf* b : {&ctx->d_O, &ctx->d_B, &ctx->d_mats, &ctx->d_tasks, &ctx->d_partials, &ctx->d_flags,
-                    &ctx->d_results, &ctx->d_lane, &ctx->d_warp, &ctx->d_ctl})
-    b->release();
-  for (HostBuf* b : {&ctx->h_O, &ctx->h_mats, &ctx->h_tasks, &ctx->h_results, &ctx->h_ctl}) b->release();
+  if (ctx->main.stream) cudaStreamSynchronize(ctx->main.stream);
+  ctx->main.release();
+  for (auto& s : ctx->serve) s->release();
+  ctx->serve.clear();
   if (ctx->h_cancel) cudaFreeHost(ctx->h_cancel);
-  for (int i = 0; i < 5; ++i)
-    if (ctx->ev[i]) cudaEventDestroy(ctx->ev[i]);
-  if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
   cudaGetLastError();
   delete ctx;
 }
@@ -242,11 +867,7 @@ void tor_destroy(tor_ctx* ctx) {
 int tor_plan_prefix_depth(tor_ctx* ctx, int n) {
   if (!ctx || n < 0 || n > 64) return -1;
   if (n == 0) return 0;
-  int p;
-  if (ctx->plan[n] >= 0) p = ctx->plan[n];
-  else if (ctx->cfg.prefix_depth >= 0) p = ctx->cfg.prefix_depth;
-  else p = default_prefix_depth(n, ctx->nwarps);
-  return std::max(0, std::min(p, n - 1));
+  return plan_p(ctx, n);
 }
 
 tor_status tor_set_prefix_depth(tor_ctx* ctx, int n, int p) {
@@ -258,7 +879,7 @@ tor_status tor_set_prefix_depth(tor_ctx* ctx, int n, int p) {
 
 tor_status tor_cancel(tor_ctx* ctx) {
   if (!ctx) return TOR_EINVAL;
-  __atomic_store_n(ctx->h_cancel, 1, __ATOMIC_SEQ_CST);
+  __atomic_add_fetch(ctx->h_cancel, 1, __ATOMIC_SEQ_CST);
   return TOR_OK;
 }
 
@@ -270,241 +891,36 @@ tor_status tor_last_times(tor_ctx* ctx, double* times) {
 
 tor_status tor_probe_fp64(int device, double seconds, double* dfma_per_s, double* fp64_tflops) {
   if (!dfma_per_s || !fp64_tflops || seconds <= 0) return TOR_EINVAL;
-  if (cudaSetDevice(device) != cudaSuccess) { cudaGetLastError(); return TOR_ECUDA; }
+  if (cudaSetDevice(device) != cudaSuccess) {
+    cudaGetLastError();
+    return TOR_ECUDA;
+  }
   double r = 0;
   cudaError_t e = run_probe_fp64(seconds, &r);
-  if (e != cudaSuccess) { cudaGetLastError(); return TOR_ECUDA; }
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return TOR_ECUDA;
+  }
   *dfma_per_s = r;
   *fp64_tflops = 2.0 * r / 1e12;
   return TOR_OK;
 }
 
-}  // extern "C"
-
-// ----------------------------------------------------------------------------
-// The evaluation pipeline for a set of matrices.
-// ----------------------------------------------------------------------------
-static tor_status run_job(tor_ctx* ctx, int count, const int* ns, const tor_c128* const* Os, const int* lds,
-                          tor_result* out, bool device_inputs, double* unit_partials, size_t unit_len) {
-  CK(cudaSetDevice(ctx->cfg.device), "cudaSetDevice");
-  const int layout = ctx->cfg.layout;
-  const bool check = !(ctx->cfg.flags & TOR_NO_CHECK);
-  tor_status first = TOR_OK;
-  auto note = [&](tor_status s) {
-    if (first == TOR_OK && s != TOR_OK) first = s;
-  };
-  // argument checks and trivial cases
-  std::vector<int> act;
-  act.reserve(count);
-  for (int i = 0; i < count; ++i) {
-    tor_result& r = out[i];
-    memset(&r, 0, sizeof r);
-    r.n = ns[i];
-    if (ns[i] < 0) r.status = TOR_EINVAL;
-    else if (ns[i] > 64) r.status = TOR_ETOOBIG;
-    else if (ns[i] == 0) { r.hi = 1.0; r.abs_sum = 1.0; r.status = TOR_OK; }
-    else if (!Os[i] || (lds && lds[i] < 2 * ns[i])) r.status = TOR_EINVAL;
-    else { act.push_back(i); continue; }
-    note(r.status);
-  }
-  for (int i = 0; i < 4; ++i) ctx->last_times[i] = 0;
-  if (act.empty()) return first;
-  // job order: by n descending so equal sizes are adjacent
-  std::stable_sort(act.begin(), act.end(), [&](int a, int b) { return ns[a] > ns[b]; });
-  const int J = (int)act.size();
-  std::vector<MatDesc> mats(J);
-  std::vector<TaskDesc> tasks;
-  long long o_elems = 0, b_elems = 0, parts = 0, lane_e = 0, warp_e = 0;
-  for (int j = 0; j < J; ++j) {
-    const int n = ns[act[j]];
-    const int p = tor_plan_prefix_depth(ctx, n);
-    mats[j].n = n;
-    mats[j].p = p;
-    mats[j].layout = layout;
-    mats[j].part_off = parts;
-    parts += 1ll << p;
-    b_elems += tri(n);
-    if (!device_inputs) o_elems += 4ll * n * n;
-    lane_e = std::max(lane_e, lane_elems_for(n, p));
-    warp_e = std::max(warp_e, warp_elems_for(n, p));
-  }
-  // tasks, largest subtrees first
-  for (int j = 0; j < J;) {
-    int k = j;
-    while (k < J && mats[k].n == mats[j].n) ++k;
-    const int p = mats[j].p, M = mats[j].n - p;
-    if (p >= 5) {
-      for (int a = j; a < k; ++a)
-        for (int t = 0; t < (1 << (p - 5)); ++t) tasks.push_back({a, t, 1, M});
-    } else {
-      const long long units = (long long)(k - j) << p;
-      for (long long t = 0; t * 32 < units; ++t) tasks.push_back({j, (int)t, k - j, M});
-    }
-    j = k;
-  }
-  std::stable_sort(tasks.begin(), tasks.end(), [](const TaskDesc& a, const TaskDesc& b) { return a.M > b.M; });
-  if (unit_partials && (J != 1 || unit_len < 3ull * (1ull << mats[0].p))) return TOR_EINVAL;
-  // device memory
-  const size_t lane_bytes = (size_t)ctx->nwarps * 32 * lane_e * sizeof(double2);
-  const size_t warp_bytes = (size_t)ctx->nwarps * warp_e * sizeof(double2);
-  const size_t need = o_elems * 16 + b_elems * 16 + parts * 32 + J * sizeof(MatDesc) +
-                      tasks.size() * sizeof(TaskDesc) + J * (4 + sizeof(ResultRec)) + lane_bytes + warp_bytes + 64;
-  if (ctx->cfg.mem_budget && need > ctx->cfg.mem_budget) {
-    for (int j = 0; j < J; ++j) out[act[j]].status = TOR_ENOMEM;
-    return TOR_ENOMEM;
-  }
-  CK(ctx->d_O.ensure(std::max<long long>(o_elems, 1) * 16), "alloc O");
-  CK(ctx->d_B.ensure(b_elems * 16), "alloc B");
-  CK(ctx->d_partials.ensure(parts * 32), "alloc partials");
-  CK(ctx->d_mats.ensure(J * sizeof(MatDesc)), "alloc mats");
-  CK(ctx->d_tasks.ensure(std::max<size_t>(tasks.size(), 1) * sizeof(TaskDesc)), "alloc tasks");
-  CK(ctx->d_flags.ensure(J * sizeof(int)), "alloc flags");
-  CK(ctx->d_results.ensure(J * sizeof(ResultRec)), "alloc results");
-  CK(ctx->d_lane.ensure(std::max<size_t>(lane_bytes, 16)), "alloc lane scratch");
-  CK(ctx->d_warp.ensure(std::max<size_t>(warp_bytes, 16)), "alloc warp scratch");
-  CK(ctx->d_ctl.ensure(64), "alloc control");
-  CK(ctx->h_O.ensure(std::max<long long>(o_elems, 1) * 16), "pinned O");
-  CK(ctx->h_mats.ensure(J * sizeof(MatDesc)), "pinned mats");
-  CK(ctx->h_tasks.ensure(std::max<size_t>(tasks.size(), 1) * sizeof(TaskDesc)), "pinned tasks");
-  CK(ctx->h_results.ensure(J * sizeof(ResultRec) + (unit_partials ? parts * 32 : 0)), "pinned results");
-  // inputs
-  long long oo = 0, bo = 0;
-  double2* dO = (double2*)ctx->d_O.p;
-  double2* dB = (double2*)ctx->d_B.p;
-  tor_c128* hO = (tor_c128*)ctx->h_O.p;
-  for (int j = 0; j < J; ++j) {
-    const int i = act[j], n = ns[i], m = 2 * n;
-    const int ld = lds ? lds[i] : m;
-    if (device_inputs) {
-      mats[j].O = (const double2*)Os[i];
-      mats[j].ld = ld;
-    } else {
-      for (int r = 0; r < m; ++r) memcpy(hO + oo + (long long)r * m, Os[i] + (long long)r * ld, sizeof(tor_c128) * m);
-      mats[j].O = dO + oo;
-      mats[j].ld = m;
-      oo += (long long)m * m;
-    }
-    mats[j].B = dB + bo;
-    bo += tri(n);
-  }
-  memcpy(ctx->h_mats.p, mats.data(), J * sizeof(MatDesc));
-  memcpy(ctx->h_tasks.p, tasks.data(), tasks.size() * sizeof(TaskDesc));
-  cudaStream_t s = ctx->stream;
-  __atomic_store_n(ctx->h_cancel, 0, __ATOMIC_SEQ_CST);
-  CK(cudaEventRecord(ctx->ev[0], s), "event");
-  if (!device_inputs) CK(cudaMemcpyAsync(dO, hO, o_elems * 16, cudaMemcpyHostToDevice, s), "H2D O");
-  CK(cudaMemcpyAsync(ctx->d_mats.p, ctx->h_mats.p, J * sizeof(MatDesc), cudaMemcpyHostToDevice, s), "H2D mats");
-  CK(cudaMemcpyAsync(ctx->d_tasks.p, ctx->h_tasks.p, tasks.size() * sizeof(TaskDesc), cudaMemcpyHostToDevice, s),
-     "H2D tasks");
-  CK(cudaMemsetAsync(ctx->d_ctl.p, 0, 64, s), "memset control");
-  CK(cudaEventRecord(ctx->ev[1], s), "event");
-  CK(launch_intake((const MatDesc*)ctx->d_mats.p, J, check ? 1 : 0, (int*)ctx->d_flags.p, s), "k_intake");
-  CK(cudaEventRecord(ctx->ev[2], s), "event");
-  UnitsParams prm;
-  prm.mats = (const MatDesc*)ctx->d_mats.p;
-  prm.tasks = (const TaskDesc*)ctx->d_tasks.p;
-  prm.ntasks = (int)tasks.size();
-  prm.ticket = (unsigned*)ctx->d_ctl.p;
-  prm.abort_word = (int*)ctx->d_ctl.p + 1;
-  prm.partials = (Part*)ctx->d_partials.p;
-  prm.mat_flags = (int*)ctx->d_flags.p;
-  prm.lane_scratch = (double2*)ctx->d_lane.p;
-  prm.lane_elems = lane_e;
-  prm.warp_scratch = (double2*)ctx->d_warp.p;
-  prm.warp_elems = warp_e;
-  prm.cancel = ctx->d_cancel;
-  prm.budget_ns = ctx->cfg.timeout_s > 0 ? (long long)(ctx->cfg.timeout_s * 1e9) : 0;
-  CK(launch_units(prm, ctx->grid, s), "k_units");
-  CK(cudaEventRecord(ctx->ev[3], s), "event");
-  CK(launch_reduce((const MatDesc*)ctx->d_mats.p, J, (const Part*)ctx->d_partials.p, (const int*)ctx->d_flags.p,
-                   (ResultRec*)ctx->d_results.p, s),
-     "k_reduce");
-  CK(cudaEventRecord(ctx->ev[4], s), "event");
-  ResultRec* hr = (ResultRec*)ctx->h_results.p;
-  CK(cudaMemcpyAsync(hr, ctx->d_results.p, J * sizeof(ResultRec), cudaMemcpyDeviceToHost, s), "D2H results");
-  Part* hparts = (Part*)((char*)ctx->h_results.p + J * sizeof(ResultRec));
-  if (unit_partials)
-    CK(cudaMemcpyAsync(hparts, ctx->d_partials.p, parts * 32, cudaMemcpyDeviceToHost, s), "D2H partials");
-  int abort_word = 0;
-  CK(cudaMemcpyAsync(&abort_word, (int*)ctx->d_ctl.p + 1, sizeof(int), cudaMemcpyDeviceToHost, s), "D2H abort");
-  CK(cudaStreamSynchronize(s), "kernel execution");
-  float ms[4];
-  cudaEventElapsedTime(&ms[0], ctx->ev[1], ctx->ev[2]);
-  cudaEventElapsedTime(&ms[1], ctx->ev[2], ctx->ev[3]);
-  cudaEventElapsedTime(&ms[2], ctx->ev[3], ctx->ev[4]);
-  cudaEventElapsedTime(&ms[3], ctx->ev[0], ctx->ev[4]);
-  for (int i = 0; i < 4; ++i) ctx->last_times[i] = ms[i];
-  for (int j = 0; j < J; ++j) {
-    tor_result& r = out[act[j]];
-    const ResultRec& q = hr[j];
-    r.hi = q.hi;
-    r.lo = q.lo;
-    r.abs_sum = q.abs_sum;
-    r.err_est = 8.0 * r.n * std::ldexp(1.0, -53) * q.abs_sum;
-    if (q.flags & FLAG_NONFINITE) r.status = TOR_EINVAL;
-    else if (q.flags & FLAG_NOTHERM) r.status = TOR_ENOTHERM;
-    else if (abort_word & ABORT_CANCEL) r.status = TOR_ECANCELED;
-    else if (abort_word & ABORT_TIMEOUT) r.status = TOR_ETIMEOUT;
-    else if (q.flags & FLAG_NOTPD) r.status = TOR_ENOTPD;
-    else r.status = TOR_OK;
-    note(r.status);
-  }
-  if (unit_partials) {
-    const long long U = 1ll << mats[0].p;
-    for (long long u = 0; u < U; ++u) {
-      unit_partials[3 * u] = hparts[u].hi;
-      unit_partials[3 * u + 1] = hparts[u].lo;
-      unit_partials[3 * u + 2] = hparts[u].abs_sum;
-    }
-  }
-  return first;
-}
-
-// ----------------------------------------------------------------------------
-// Serving thread: drains the submit queue in batches.
-// ----------------------------------------------------------------------------
-static void server_loop(tor_ctx* ctx) {
-  for (;;) {
-    std::vector<Request*> batch;
-    {
-      std::unique_lock<std::mutex> lk(ctx->q_mu);
-      ctx->q_cv.wait(lk, [&] { return ctx->stopping || !ctx->queue.empty(); });
-      if (ctx->stopping && ctx->queue.empty()) return;
-      while (!ctx->queue.empty()) {
-        batch.push_back(ctx->queue.front());
-        ctx->queue.pop_front();
-      }
-    }
-    std::vector<int> ns(batch.size()), lds(batch.size());
-    std::vector<const tor_c128*> Os(batch.size());
-    std::vector<tor_result> res(batch.size());
-    for (size_t i = 0; i < batch.size(); ++i) {
-      ns[i] = batch[i]->n;
-      lds[i] = 2 * batch[i]->n;
-      Os[i] = batch[i]->O.data();
-    }
-    {
-      std::lock_guard<std::mutex> lk(ctx->run_mu);
-      run_job(ctx, (int)batch.size(), ns.data(), Os.data(), lds.data(), res.data(), false, nullptr, 0);
-    }
-    {
-      std::lock_guard<std::mutex> lk(ctx->q_mu);
-      for (size_t i = 0; i < batch.size(); ++i) {
-        batch[i]->res = res[i];
-        batch[i]->done = true;
-      }
-    }
-    ctx->done_cv.notify_all();
-  }
-}
-
-extern "C" {
-
 tor_status tor_eval_batch(tor_ctx* ctx, int count, const int* n, const tor_c128* const* O, const int* ld,
                           tor_result* out) {
   if (!ctx || count < 0 || (count > 0 && (!n || !O || !out))) return TOR_EINVAL;
+  std::vector<MatIn> ins(count);
+  const bool dev = (ctx->cfg.flags & TOR_IN_DEVICE) != 0;
+  for (int i = 0; i < count; ++i) {
+    ins[i].n = n[i];
+    ins[i].O = O[i];
+    ins[i].ld = ld ? ld[i] : 2 * n[i];
+    ins[i].n_src = n[i];
+    ins[i].layout = ctx->cfg.layout;
+    ins[i].dev = dev;
+  }
   std::lock_guard<std::mutex> lk(ctx->run_mu);
-  return run_job(ctx, count, n, O, ld, out, (ctx->cfg.flags & TOR_IN_DEVICE) != 0, nullptr, 0);
+  return run_blocking(ctx, ins, out, nullptr, 0);
 }
 
 tor_status tor_eval(tor_ctx* ctx, int n, const tor_c128* O, int ld, tor_result* out) {
@@ -517,10 +933,15 @@ tor_status tor_eval(tor_ctx* ctx, int n, const tor_c128* O, int ld, tor_result* 
 tor_status tor_eval_units(tor_ctx* ctx, int n, const tor_c128* O, int ld, double* partials, size_t partials_len,
                           tor_result* out) {
   if (!ctx || !out || !partials || n < 1 || n > 64) return TOR_EINVAL;
-  const tor_c128* Op[1] = {O};
-  int lds[1] = {ld};
+  std::vector<MatIn> ins(1);
+  ins[0].n = n;
+  ins[0].O = O;
+  ins[0].ld = ld;
+  ins[0].n_src = n;
+  ins[0].layout = ctx->cfg.layout;
+  ins[0].dev = (ctx->cfg.flags & TOR_IN_DEVICE) != 0;
   std::lock_guard<std::mutex> lk(ctx->run_mu);
-  return run_job(ctx, 1, &n, Op, lds, out, (ctx->cfg.flags & TOR_IN_DEVICE) != 0, partials, partials_len);
+  return run_blocking(ctx, ins, out, partials, partials_len);
 }
 
 tor_status tor_submit(tor_ctx* ctx, int n, const tor_c128* O, int ld, uint64_t* ticket) {
@@ -528,26 +949,15 @@ tor_status tor_submit(tor_ctx* ctx, int n, const tor_c128* O, int ld, uint64_t* 
   if (n > 64) return TOR_ETOOBIG;
   if (ctx->cfg.flags & TOR_IN_DEVICE) return TOR_EINVAL;  // the queue copies host inputs only
   Request* r = new Request();
-  r->n = n;
   r->O.resize((size_t)4 * n * n);
-  for (int i = 0; i < 2 * n; ++i) memcpy(r->O.data() + (size_t)i * 2 * n, O + (size_t)i * ld, sizeof(tor_c128) * 2 * n);
-  {
-    std::lock_guard<std::mutex> lk(ctx->q_mu);
-    if (ctx->queue.size() >= ctx->queue_limit) {
-      delete r;
-      return TOR_EAGAIN;
-    }
-    r->ticket = ctx->next_ticket++;
-    ctx->reqs[r->ticket] = r;
-    ctx->queue.push_back(r);
-    if (!ctx->server_started) {
-      ctx->server = std::thread(server_loop, ctx);
-      ctx->server_started = true;
-    }
-    *ticket = r->ticket;
-  }
-  ctx->q_cv.notify_one();
-  return TOR_OK;
+  for (int i = 0; i < 2 * n; ++i)
+    memcpy(r->O.data() + (size_t)i * 2 * n, O + (size_t)i * ld, sizeof(tor_c128) * 2 * n);
+  r->in.n = n;
+  r->in.O = r->O.data();
+  r->in.ld = 2 * n;
+  r->in.n_src = n;
+  r->in.layout = ctx->cfg.layout;
+  return enqueue_request(ctx, r, ticket);
 }
 
 tor_status tor_poll(tor_ctx* ctx, uint64_t ticket, tor_result* out, double timeout_s) {
@@ -566,6 +976,264 @@ tor_status tor_poll(tor_ctx* ctx, uint64_t ticket, tor_result* out, double timeo
   ctx->reqs.erase(it);
   delete r;
   return out->status;
+}
+
+tor_status tor_serving_stats(tor_ctx* ctx, long long* served, long long* batches, long long* queued) {
+  if (!ctx) return TOR_EINVAL;
+  std::lock_guard<std::mutex> lk(ctx->q_mu);
+  if (served) *served = ctx->served.load();
+  if (batches) *batches = ctx->batches.load();
+  if (queued) *queued = (long long)ctx->queue.size();
+  return TOR_OK;
+}
+
+tor_status tor_session_create(tor_ctx* ctx, int n_total, const tor_c128* M, int ld, int kind,
+                              tor_session** out) {
+  if (!ctx || !out || !M || n_total < 1 || n_total > 1024 || ld < 2 * n_total) return TOR_EINVAL;
+  if (kind != TOR_SESSION_SIGMA && kind != TOR_SESSION_O) return TOR_EINVAL;
+  *out = nullptr;
+  const int N = n_total, m = 2 * N;
+  const bool block = ctx->cfg.layout == TOR_LAYOUT_BLOCK;
+  auto src = [&](int r) { return block ? (r >> 1) + (r & 1) * N : r; };  // pairs row -> input row
+  // K = (Sigma_[N])^{-1} in pairs order
+  std::vector<CL> K((size_t)m * m);
+  for (int a = 0; a < m; ++a)
+    for (int b = 0; b < m; ++b) {
+      const tor_c128 v = M[(size_t)src(a) * ld + src(b)];
+      K[(size_t)a * m + b] = kind == TOR_SESSION_O ? CL{(a == b ? 1.0L : 0.0L) - v.re, -(long double)v.im}
+                                                   : CL{(long double)v.re, (long double)v.im};
+    }
+  if (kind == TOR_SESSION_SIGMA && !hpd_inverse(K, m)) return TOR_ENOTPD;
+  tor_session* s = new tor_session();
+  s->ctx = ctx;
+  s->N = N;
+  s->off.assign(N + 1, 0);
+  long long tot = 0;
+  for (int j = 1; j <= N; ++j) {
+    s->off[j] = tot;
+    tot += 4ll * j * j;
+  }
+  std::vector<tor_c128> host((size_t)tot);
+  for (int j = N; j >= 1; --j) {
+    const int mj = 2 * j;
+    tor_c128* Oj = host.data() + s->off[j];
+    for (int a = 0; a < mj; ++a)
+      for (int b = 0; b < mj; ++b) {
+        const CL k = K[(size_t)a * m + b];
+        Oj[(size_t)a * mj + b] = tor_c128{(double)((a == b ? 1.0L : 0.0L) - k.re), (double)(-k.im)};
+      }
+    if (j == 1) break;
+    // remove mode j-1 (rows/cols b0, b0+1): K <- K_aa - K_ab K_bb^{-1} K_ba
+    const int b0 = mj - 2;
+    const CL p = K[(size_t)b0 * m + b0], q = K[(size_t)b0 * m + b0 + 1], r = K[(size_t)(b0 + 1) * m + b0],
+             t = K[(size_t)(b0 + 1) * m + b0 + 1];
+    const CL det = csub(cmul(p, t), cmul(q, r));
+    const long double dd = det.re * det.re + det.im * det.im;
+    if (!(dd > 0)) {
+      delete s;
+      return TOR_ENOTPD;
+    }
+    const CL idet{det.re / dd, -det.im / dd};
+    const CL i00 = cmul(t, idet), i01 = cmul(CL{-q.re, -q.im}, idet), i10 = cmul(CL{-r.re, -r.im}, idet),
+             i11 = cmul(p, idet);
+    for (int a = 0; a < b0; ++a) {
+      const CL ka0 = K[(size_t)a * m + b0], ka1 = K[(size_t)a * m + b0 + 1];
+      const CL u0 = cadd(cmul(ka0, i00), cmul(ka1, i10)), u1 = cadd(cmul(ka0, i01), cmul(ka1, i11));
+      for (int b = 0; b < b0; ++b) {
+        const CL d = cadd(cmul(u0, K[(size_t)b0 * m + b]), cmul(u1, K[(size_t)(b0 + 1) * m + b]));
+        K[(size_t)a * m + b] = csub(K[(size_t)a * m + b], d);
+      }
+    }
+  }
+  cudaSetDevice(ctx->cfg.device);
+  cudaError_t e = s->d_O.ensure((size_t)tot * 16, &s->gen);
+  if (e == cudaSuccess) e = cudaMemcpy(s->d_O.p, host.data(), (size_t)tot * 16, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    tor_status st = cuda_fail(ctx, e, "session upload");
+    s->d_O.release();
+    delete s;
+    return st;
+  }
+  *out = s;
+  return TOR_OK;
+}
+
+void tor_session_destroy(tor_session* s) {
+  if (!s) return;
+  if (s->ctx) cudaSetDevice(s->ctx->cfg.device);
+  s->d_O.release();
+  delete s;
+}
+
+}  // extern "C"
+
+static tor_status marginal_in(tor_session* s, int j, int k, const int* modes, MatIn& in, std::vector<int>& own) {
+  if (!s || j < 1 || j > s->N || k < 0 || k > j || (k > 0 && !modes)) return TOR_EINVAL;
+  if (k > 64) return TOR_ETOOBIG;
+  own.assign(modes, modes + k);
+  std::sort(own.begin(), own.end());
+  for (int i = 0; i < k; ++i)
+    if (own[i] < 0 || own[i] >= j || (i && own[i] == own[i - 1])) return TOR_EINVAL;
+  in.n = k;
+  in.O = (const tor_c128*)((const double2*)s->d_O.p + s->off[j]);
+  in.ld = 2 * j;
+  in.n_src = j;
+  in.layout = TOR_LAYOUT_PAIRS;
+  in.dev = true;
+  in.modes = k ? own.data() : nullptr;
+  return TOR_OK;
+}
+
+extern "C" {
+
+tor_status tor_eval_marginal(tor_ctx* ctx, tor_session* s, int j, int k, const int* modes, tor_result* out) {
+  if (!ctx || !out || !s || s->ctx != ctx) return TOR_EINVAL;
+  std::vector<MatIn> ins(1);
+  std::vector<int> own;
+  tor_status st = marginal_in(s, j, k, modes, ins[0], own);
+  if (st != TOR_OK) return st;
+  std::lock_guard<std::mutex> lk(ctx->run_mu);
+  return run_blocking(ctx, ins, out, nullptr, 0);
+}
+
+tor_status tor_submit_marginal(tor_ctx* ctx, tor_session* s, int j, int k, const int* modes, uint64_t* ticket) {
+  if (!ctx || !ticket || !s || s->ctx != ctx) return TOR_EINVAL;
+  Request* r = new Request();
+  tor_status st = marginal_in(s, j, k, modes, r->in, r->modes);
+  if (st != TOR_OK) {
+    delete r;
+    return st;
+  }
+  r->in.modes = k ? r->modes.data() : nullptr;
+  return enqueue_request(ctx, r, ticket);
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Autotuner: for each n, time tor_eval at prefix depths around the built-in
+// plan and keep the fastest.  The kernels' control flow depends on n and p
+// only, so a fixed synthetic matrix (0.3 I plus a small seeded Hermitian
+// perturbation, I - O positive definite) times every input of that size.
+// ---------------------------------------------------------------------------
+static void synthetic_matrix(int n, std::vector<tor_c128>& O) {
+  const int m = 2 * n;
+  O.assign((size_t)m * m, tor_c128{0.0, 0.0});
+  uint64_t x = 0x9E3779B97F4A7C15ull ^ (uint64_t)n;
+  auto next = [&]() {  // splitmix64 -> uniform in [-1, 1)
+    x += 0x9E3779B97F4A7C15ull;
+    uint64_t z = x;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    return (double)(z >> 11) * 0x1.0p-52 - 1.0;
+  };
+  const double eps = 0.2 / m;
+  for (int r = 0; r < m; ++r) {
+    O[(size_t)r * m + r] = tor_c128{0.3, 0.0};
+    for (int c = 0; c < r; ++c) {
+      const double a = eps * next(), b = eps * next();
+      O[(size_t)r * m + c] = tor_c128{a, b};
+      O[(size_t)c * m + r] = tor_c128{a, -b};
+    }
+  }
+}
+
+extern "C" {
+
+tor_status tor_autotune(tor_ctx* ctx, int n_lo, int n_hi, double budget_s, int* chosen) {
+  if (!ctx || n_lo < 1 || n_hi > 64 || n_lo > n_hi || budget_s <= 0) return TOR_EINVAL;
+  if (ctx->cfg.flags & TOR_IN_DEVICE) return TOR_EINVAL;  // times host inputs
+  const double per_n = budget_s / (n_hi - n_lo + 1);
+  std::vector<tor_c128> O;
+  for (int n = n_lo; n <= n_hi; ++n) {
+    synthetic_matrix(n, O);
+    int base;
+    {
+      std::lock_guard<std::mutex> lk(ctx->run_mu);
+      ctx->plan[n] = -1;
+      base = plan_p(ctx, n);
+    }
+    std::vector<int> cands;
+    for (int d = -4; d <= 4; ++d) {
+      const int p = base + d, M = n - p;
+      if (p < 0 || M < 1 || M > 22) continue;
+      cands.push_back(p);
+    }
+    double best_t = 1e300;
+    int best_p = base;
+    const double t_start = now_s();
+    for (int p : cands) {
+      {
+        std::lock_guard<std::mutex> lk(ctx->run_mu);
+        ctx->plan[n] = p;
+      }
+      tor_result r;
+      tor_status st = tor_eval(ctx, n, O.data(), 2 * n, &r);  // warm-up (and buffer growth)
+      if (st != TOR_OK) return st;
+      double tmin = 1e300;
+      for (int rep = 0; rep < 3; ++rep) {
+        st = tor_eval(ctx, n, O.data(), 2 * n, &r);
+        if (st != TOR_OK) return st;
+        tmin = std::min(tmin, ctx->last_times[3]);
+        if (now_s() - t_start > per_n) break;
+      }
+      if (tmin < best_t) {
+        best_t = tmin;
+        best_p = p;
+      }
+      if (now_s() - t_start > per_n) break;
+    }
+    {
+      std::lock_guard<std::mutex> lk(ctx->run_mu);
+      ctx->plan[n] = best_p;
+    }
+    if (chosen) chosen[n - n_lo] = best_p;
+  }
+  return TOR_OK;
+}
+
+tor_status tor_plan_save(tor_ctx* ctx, const char* path) {
+  if (!ctx || !path) return TOR_EINVAL;
+  FILE* f = fopen(path, "w");
+  if (!f) return TOR_EINVAL;
+  cudaDeviceProp prop;
+  if (cudaGetDeviceProperties(&prop, ctx->cfg.device) != cudaSuccess) {
+    cudaGetLastError();
+    snprintf(prop.name, sizeof prop.name, "unknown");
+  }
+  fprintf(f, "# libtor prefix-depth plan: device %s, %d SMs, %d resident warps\n", prop.name, ctx->sms, ctx->nwarps);
+  fprintf(f, "warps %d\n", ctx->nwarps);
+  {
+    std::lock_guard<std::mutex> lk(ctx->run_mu);
+    for (int n = 1; n <= 64; ++n)
+      if (ctx->plan[n] >= 0) fprintf(f, "%d %d\n", n, ctx->plan[n]);
+  }
+  fclose(f);
+  return TOR_OK;
+}
+
+tor_status tor_plan_load(tor_ctx* ctx, const char* path) {
+  if (!ctx || !path) return TOR_EINVAL;
+  FILE* f = fopen(path, "r");
+  if (!f) return TOR_EINVAL;
+  char line[256];
+  int warps = -1;
+  std::vector<std::pair<int, int>> rows;
+  while (fgets(line, sizeof line, f)) {
+    if (line[0] == '#') continue;
+    int a, b;
+    if (sscanf(line, "warps %d", &a) == 1) {
+      warps = a;
+      continue;
+    }
+    if (sscanf(line, "%d %d", &a, &b) == 2 && a >= 1 && a <= 64 && b >= 0 && b < a) rows.push_back({a, b});
+  }
+  fclose(f);
+  if (warps != ctx->nwarps) return TOR_EINVAL;  // tuned for another device shape
+  std::lock_guard<std::mutex> lk(ctx->run_mu);
+  for (auto& r : rows) ctx->plan[r.first] = r.second;
+  return TOR_OK;
 }
 
 }  // extern "C"

@@ -12,10 +12,15 @@ struct __align__(32) Part {
 
 // One matrix of a job.
 struct MatDesc {
-  const double2* O;     // input O on the device (row-major, leading dimension ld)
+  const double2* O;     // source matrix on the device (row-major, leading dimension ld)
+  const int* modes;     // device list of the n source modes to keep, or null (modes 0..n-1)
   double2* B;           // packed lower triangle of B = I - O in pairs order, n(2n+1) entries
   long long part_off;   // first of this matrix's 2^p unit partials
+  long long red_off;    // first of this matrix's reduction leaves (task partials if p >= 5, else unit partials)
+  int red_log2;         // log2 of the number of reduction leaves: p - 5 if p >= 5, else p
   int n, p, ld, layout;
+  int n_src;            // modes of the source matrix (n unless `modes` selects a submatrix)
+  int pad;
 };
 
 // One warp task.  p >= 5: 32 units of matrix `mat` sharing the decisions on
@@ -34,13 +39,15 @@ struct UnitsParams {
   const TaskDesc* tasks;
   int ntasks;
   unsigned* ticket;            // zeroed before the launch
-  Part* partials;           // (hi, lo, abs_sum, 0) per unit
+  Part* partials;              // (hi, lo, abs_sum, 0) per unit
+  Part* red_leaves;            // per warp task (p >= 5: its 32 units summed by a fixed lane tree) or per unit
   int* mat_flags;              // FLAG_* per matrix
   double2* lane_scratch;       // per warp: 32 * lane_elems, lane-interleaved
   long long lane_elems;
   double2* warp_scratch;       // per warp: warp_elems, contiguous
   long long warp_elems;
-  const volatile int* cancel;  // host-mapped; nonzero = stop
+  const volatile int* cancel;  // host-mapped cancel counter
+  int cancel_epoch;            // its value when the job started; a change = stop
   long long budget_ns;         // 0 = no time limit
   int* abort_word;             // ABORT_* bits set by the kernel
 };

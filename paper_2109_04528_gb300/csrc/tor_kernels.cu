@@ -4,8 +4,8 @@
 //               Eq. A and the row order of Sec. 2); Hermitian / finite checks.
 //   k_units   : persistent warps; each warp task evaluates 32 units (prefix
 //               subtrees) of the tree of Algorithm 2, one unit per lane.
-//   k_reduce  : fixed-shape binary tree over each matrix's unit partials, in
-//               double-double.
+//   k_reduce  : fixed-shape binary tree over each matrix's task partials (each
+//               already a fixed lane tree over 32 units), in double-double.
 //   k_probe   : FP64 FMA throughput probe (the roofline's denominator).
 #include "tor_device.cuh"
 #include "tor_internal.h"
@@ -183,28 +183,34 @@ __device__ __noinline__ void lane_dfs(const LaneMem L, int root, int root_o, int
 
 // ------------------------------------------------------------------ kernels
 
-__global__ void k_intake(const MatDesc* __restrict__ mats, int check, int* __restrict__ flags) {
+// One block per matrix; threads over the packed lower triangle of B.  Checks:
+// finite entries, and max |O_rs - conj(O_sr)| <= 1e-12 max |O| in the
+// max(|Re|, |Im|) norm of each entry.
+__global__ void __launch_bounds__(256) k_intake(const MatDesc* __restrict__ mats, int check, int* __restrict__ flags) {
   const MatDesc D = mats[blockIdx.x];
-  const int n = D.n, R = 2 * n;
+  const int n = D.n, tot = n * (2 * n + 1);
   __shared__ unsigned long long s_max, s_dev;
   __shared__ int s_bad;
   if (threadIdx.x == 0) { s_max = 0; s_dev = 0; s_bad = 0; }
   __syncthreads();
   double mx = 0.0, dev = 0.0;
   int bad = 0;
-  for (int r = 0; r < R; ++r) {
-    const int pr = D.layout == 0 ? (r >> 1) + (r & 1) * n : r;
-    for (int s = threadIdx.x; s <= r; s += blockDim.x) {
-      const int ps = D.layout == 0 ? (s >> 1) + (s & 1) * n : s;
-      const double2 a = D.O[(size_t)pr * D.ld + ps];
-      const double2 b = D.O[(size_t)ps * D.ld + pr];
-      if (!isfinite(a.x) || !isfinite(a.y) || !isfinite(b.x) || !isfinite(b.y)) bad = 1;
-      mx = fmax(mx, fmax(hypot(a.x, a.y), hypot(b.x, b.y)));
-      dev = fmax(dev, hypot(a.x - b.x, a.y + b.y));
-      D.B[P(r, s)] = r == s ? make_double2(1.0 - a.x, 0.0) : make_double2(-a.x, -a.y);
-    }
+  for (int e = threadIdx.x; e < tot; e += blockDim.x) {
+    int r = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f);
+    while (P(r, 0) > e) --r;
+    while (P(r + 1, 0) <= e) ++r;
+    const int s = e - P(r, 0);
+    const int mr = D.modes ? D.modes[r >> 1] : (r >> 1), ms = D.modes ? D.modes[s >> 1] : (s >> 1);
+    const int pr = D.layout == 0 ? mr + (r & 1) * D.n_src : 2 * mr + (r & 1);
+    const int ps = D.layout == 0 ? ms + (s & 1) * D.n_src : 2 * ms + (s & 1);
+    const double2 a = D.O[(size_t)pr * D.ld + ps];
+    const double2 b = D.O[(size_t)ps * D.ld + pr];
+    if (!isfinite(a.x) || !isfinite(a.y) || !isfinite(b.x) || !isfinite(b.y)) bad = 1;
+    mx = fmax(mx, fmax(fmax(fabs(a.x), fabs(a.y)), fmax(fabs(b.x), fabs(b.y))));
+    dev = fmax(dev, fmax(fabs(a.x - b.x), fabs(a.y + b.y)));
+    D.B[e] = r == s ? make_double2(1.0 - a.x, 0.0) : make_double2(-a.x, -a.y);
   }
-  // reduce (values are non-negative, so their bit patterns order like the values)
+  // non-negative doubles order like their bit patterns
   atomicMax(&s_max, (unsigned long long)__double_as_longlong(mx));
   atomicMax(&s_dev, (unsigned long long)__double_as_longlong(dev));
   if (bad) atomicOr(&s_bad, 1);
@@ -218,12 +224,33 @@ __global__ void k_intake(const MatDesc* __restrict__ mats, int check, int* __res
   }
 }
 
-__device__ __forceinline__ void write_partial(const UnitsParams& prm, const MatDesc& D, int mat, long long u,
+// Unit partial (hi, lo, abs).  For p < 5 the unit partials are the reduction leaves.
+__device__ __forceinline__ Part write_partial(const UnitsParams& prm, const MatDesc& D, int mat, long long u,
                                               DD acc, double ab, bool bad) {
   double hi, lo;
   fast_two_sum(acc.s, acc.c, hi, lo);
-  prm.partials[D.part_off + u] = Part{hi, lo, ab, 0.0};
+  const Part v{hi, lo, ab, 0.0};
+  prm.partials[D.part_off + u] = v;
+  if (D.p < 5) prm.red_leaves[D.red_off + u] = v;
   if (bad) atomicOr(&prm.mat_flags[mat], FLAG_NOTPD);
+  return v;
+}
+
+// Sum of the 32 lanes' unit partials of a task by a fixed binary tree over lane index.
+__device__ __forceinline__ void write_task_partial(const UnitsParams& prm, const MatDesc& D, int sub, Part v,
+                                                   int lane) {
+  double h = v.hi, l = v.lo, a = v.abs_sum;
+#pragma unroll
+  for (int off = 1; off < kWarp; off <<= 1) {
+    const double h2 = __shfl_down_sync(0xffffffffu, h, off);
+    const double l2 = __shfl_down_sync(0xffffffffu, l, off);
+    const double a2 = __shfl_down_sync(0xffffffffu, a, off);
+    if ((lane & (2 * off - 1)) == 0) {
+      dd_add(h, l, h2, l2, h, l);
+      a = a + a2;
+    }
+  }
+  if (lane == 0) prm.red_leaves[D.red_off + sub] = Part{h, l, a, 0.0};
 }
 
 // p >= 5: the warp builds the task node (depth p - 5) cooperatively, fans it
@@ -292,7 +319,8 @@ __device__ void run_task_shared(const UnitsParams& prm, const TaskDesc T, const 
   double ab = 0.0;
   lane_dfs(L, 0, 0, M, n, nphi, nincl, root_sz, xs, ys, acc, ab, bad);
   const long long u = (long long)T.sub | ((long long)lane << (p - 5));
-  write_partial(prm, D, T.mat, u, acc, ab, bad);
+  const Part v = write_partial(prm, D, T.mat, u, acc, ab, bad);
+  write_task_partial(prm, D, T.sub, v, lane);
 }
 
 // p < 5: lanes take units of up to 32 small matrices of one size; each lane
@@ -338,7 +366,7 @@ __global__ void __launch_bounds__(kUnitsThreads, 2) k_units(const UnitsParams pr
     unsigned t = 0xffffffffu;
     if (lane == 0) {
       int ab = 0;
-      if (*prm.cancel) ab = ABORT_CANCEL;
+      if (*prm.cancel != prm.cancel_epoch) ab = ABORT_CANCEL;
       else if (prm.budget_ns > 0 && (long long)(global_ns() - t0) > prm.budget_ns) ab = ABORT_TIMEOUT;
       if (ab) atomicOr(prm.abort_word, ab);
       else if (*(volatile int*)prm.abort_word == 0) t = atomicAdd(prm.ticket, 1u);
@@ -360,10 +388,10 @@ __global__ void __launch_bounds__(kReduceThreads) k_reduce(const MatDesc* __rest
                                                            const Part* __restrict__ partials,
                                                            const int* __restrict__ flags, ResultRec* out) {
   const MatDesc D = mats[blockIdx.x];
-  const long long U = 1ll << D.p;
+  const long long U = 1ll << D.red_log2;
   const int T = (int)(U < kReduceThreads ? U : kReduceThreads);
   const long long chunk = U / T;
-  const Part* x = partials + D.part_off;
+  const Part* x = partials + D.red_off;
   __shared__ double sh[kReduceThreads], sl[kReduceThreads], sa[kReduceThreads];
   const int t = threadIdx.x;
   if (t < T) {
@@ -425,7 +453,7 @@ __global__ void __launch_bounds__(256) k_probe(double* out, int iters) {
 
 cudaError_t launch_intake(const MatDesc* d_mats, int nmats, int check, int* d_flags, cudaStream_t s) {
   if (nmats <= 0) return cudaSuccess;
-  k_intake<<<nmats, 128, 0, s>>>(d_mats, check, d_flags);
+  k_intake<<<nmats, 256, 0, s>>>(d_mats, check, d_flags);
   return cudaGetLastError();
 }
 cudaError_t launch_units(const UnitsParams& prm, int grid, cudaStream_t s) {

@@ -83,7 +83,8 @@ constexpr size_t OFF_TASKS = align256(OFF_MATS + sizeof(MatDesc));      // <= 32
 constexpr size_t OFF_RES = align256(OFF_TASKS + 64 * sizeof(TaskDesc));  // one ResultRec
 constexpr size_t OFF_B = align256(OFF_RES + sizeof(ResultRec));
 constexpr size_t OFF_PARTS = align256(OFF_B + sizeof(double2) * tri_c(kNoallocMaxN));
-constexpr size_t OFF_LANE = align256(OFF_PARTS + sizeof(Part) * kMaxUnits);
+constexpr size_t OFF_REDS = align256(OFF_PARTS + sizeof(Part) * kMaxUnits);
+constexpr size_t OFF_LANE = align256(OFF_REDS + sizeof(Part) * kMaxUnits);
 constexpr size_t OFF_WARP = align256(OFF_LANE + sizeof(double2) * kLanes * max_lane_elems() * kWarps);
 constexpr size_t END = align256(OFF_WARP + sizeof(double2) * max_warp_elems() * kWarps);
 static_assert(END <= kNoallocBytes, "no-alloc scratch layout does not fit the static array");
@@ -98,8 +99,13 @@ __global__ void k_noalloc_setup(const double2* O, int n, int ld, int layout) {
     *(int*)(base + OFF_FLAGS) = 0;
     MatDesc* D = (MatDesc*)(base + OFF_MATS);
     D->O = O;
+    D->modes = nullptr;
+    D->n_src = n;
+    D->pad = 0;
     D->B = (double2*)(base + OFF_B);
     D->part_off = 0;
+    D->red_off = 0;
+    D->red_log2 = p >= 5 ? p - 5 : p;
     D->n = n;
     D->p = p;
     D->ld = ld;
@@ -176,8 +182,10 @@ extern "C" tor_status tor_eval_noalloc(int device, int n, const tor_c128* O, int
       prm.ticket = (unsigned*)(base + OFF_CTL);
       prm.abort_word = (int*)(base + OFF_CTL) + 1;
       prm.cancel = (const volatile int*)(base + OFF_CTL) + 2;
+      prm.cancel_epoch = 0;
       prm.budget_ns = 0;
       prm.partials = (Part*)(base + OFF_PARTS);
+      prm.red_leaves = (Part*)(base + OFF_REDS);
       prm.mat_flags = (int*)(base + OFF_FLAGS);
       prm.lane_scratch = (double2*)(base + OFF_LANE);
       prm.lane_elems = max_lane_elems();
@@ -186,7 +194,7 @@ extern "C" tor_status tor_eval_noalloc(int device, int n, const tor_c128* O, int
       e = launch_units(prm, kNoallocBlocks, s);
     }
     if (e == cudaSuccess)
-      e = launch_reduce((const MatDesc*)(base + OFF_MATS), 1, (const Part*)(base + OFF_PARTS),
+      e = launch_reduce((const MatDesc*)(base + OFF_MATS), 1, (const Part*)(base + OFF_REDS),
                         (const int*)(base + OFF_FLAGS), (ResultRec*)(base + OFF_RES), s);
     if (e == cudaSuccess) {
       k_noalloc_finish<<<1, 1, 0, s>>>(out, n);

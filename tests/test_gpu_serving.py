@@ -1,0 +1,176 @@
+"""GPU tests of the batched and served paths: CUDA-graph replay, the
+autotuner, chain-rule sessions, continuous batching, admission by memory
+budget and cancellation.  Every numeric check is against the binary128
+oracle or an identity of Eq. (tor); 'same alone and in the mix' is bitwise."""
+import threading
+import time
+
+import numpy as np
+import pytest
+
+from paper_2109_04528_gb300 import binding, inputs
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-10
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    from paper_2109_04528_gb300 import build
+    build.build()
+    c = binding.Context(device=0)
+    yield c
+    c.close()
+
+
+def same(a, b):
+    return (a.hi, a.lo, a.abs_sum, a.status) == (b.hi, b.lo, b.abs_sum, b.status)
+
+
+def test_graph_replay_bitwise_and_fresh_data(ctx):
+    rng = np.random.default_rng(5)
+    sizes = [int(k) for k in rng.integers(3, 17, size=12)]
+    with binding.Context(device=0, flags=binding.TOR_GRAPHS) as g:
+        for rep in range(3):  # same shape, new data every time: the graph must read the new inputs
+            mats = [inputs.lossy_squeezed(k, 100 * rep + i, (0.5, 1.2), 0.4).O for i, k in enumerate(sizes)]
+            a = binding.tor_eval_batch(g, mats)
+            b = binding.tor_eval_batch(ctx, mats)
+            assert all(same(x, y) for x, y in zip(a, b))
+
+
+def test_graph_replay_device_inputs():
+    torch = pytest.importorskip("torch")
+    with binding.Context(device=0, flags=binding.TOR_GRAPHS | binding.TOR_IN_DEVICE) as g, \
+            binding.Context(device=0) as h:
+        for rep in range(3):
+            mats = [inputs.lossy_squeezed(n, 50 + rep, (0.3, 0.8), 0.5).O for n in (6, 12, 14)]
+            d = [torch.from_numpy(m).to("cuda:0") for m in mats]
+            a = binding.tor_eval_batch(g, d)
+            b = binding.tor_eval_batch(h, mats)
+            assert all(same(x, y) for x, y in zip(a, b))
+
+
+def test_autotune_and_plan_roundtrip(ctx, oracle_mod, tmp_path):
+    with binding.Context(device=0) as c:
+        chosen = c.autotune(10, 13, budget_s=3.0)
+        assert set(chosen) == {10, 11, 12, 13}
+        for n, p in chosen.items():
+            assert 0 <= p < n and c.plan_prefix_depth(n) == p
+        inst = inputs.lossy_squeezed(13, 3, (0.3, 0.8), 0.5)
+        r = binding.tor_eval(c, inst.O)
+        ref = oracle_mod.tor_brute(inst.O)
+        assert abs(r.tor - ref.tor) <= TOL * ref.abs_sum
+        path = str(tmp_path / "plan.txt")
+        c.save_plan(path)
+        with binding.Context(device=0) as c2:
+            c2.load_plan(path)
+            assert all(c2.plan_prefix_depth(n) == p for n, p in chosen.items())
+        bad = tmp_path / "foreign.txt"
+        bad.write_text("warps 7\n10 3\n")
+        with pytest.raises(binding.TorError):
+            c.load_plan(str(bad))
+
+
+def marginal_O(sigma, j):
+    n = sigma.shape[0] // 2
+    idx = np.concatenate([np.arange(j), n + np.arange(j)])
+    sj = sigma[np.ix_(idx, idx)]
+    return inputs.sampling_matrix(sj)
+
+
+def test_session_marginals_vs_oracle(ctx, oracle_mod):
+    inst = inputs.lossy_squeezed(10, 77, (0.5, 1.2), 0.3)
+    rng = np.random.default_rng(1)
+    with binding.Session(ctx, inst.sigma, binding.TOR_SESSION_SIGMA) as s_sig, \
+            binding.Session(ctx, inst.O, binding.TOR_SESSION_O) as s_o:
+        for _ in range(12):
+            j = int(rng.integers(1, 11))
+            k = int(rng.integers(0, j + 1))
+            S = sorted(rng.choice(j, size=k, replace=False).tolist())
+            Oj = marginal_O(inst.sigma, j)
+            ref = oracle_mod.tor_brute(inputs.submatrix(Oj, S)) if k else None
+            for sess in (s_sig, s_o):
+                r = binding.tor_eval_marginal(ctx, sess, j, list(reversed(S)))
+                if k == 0:
+                    assert r.tor == 1.0
+                else:
+                    assert abs(r.tor - ref.tor) <= 1e-9 * ref.abs_sum, (j, S)
+
+
+def test_served_marginals_sum_to_one(ctx):
+    # chain rule at full size: sum over all 2^j click patterns of the first j
+    # modes of Tor(O^(j)_S) equals sqrt(det Sigma_[j]) (probabilities sum to 1)
+    inst = inputs.lossy_squeezed(16, 9, (0.5, 1.2), 0.3)
+    j = 12
+    with binding.Session(ctx, inst.sigma) as sess:
+        tickets = [binding.tor_submit_marginal(ctx, sess, j, [m for m in range(j) if mask >> m & 1])
+                   for mask in range(1 << j)]
+        tot, absum = 0.0, 0.0
+        for t in tickets:
+            st, r = binding.tor_poll(ctx, t, 120.0)
+            assert st == 0
+            tot += r.tor
+            absum += r.abs_sum
+    n = inst.n
+    idx = np.concatenate([np.arange(j), n + np.arange(j)])
+    want = np.sqrt(np.linalg.det(inst.sigma[np.ix_(idx, idx)]).real)
+    assert abs(tot - want) <= 1e-10 * absum
+
+
+def test_same_alone_and_in_the_mix(ctx):
+    rng = np.random.default_rng(8)
+    mats = [inputs.lossy_squeezed(int(k), 1000 + i, (0.5, 1.2), 0.4).O for i, k in enumerate(rng.integers(1, 23, 60))]
+    alone = [binding.tor_eval(ctx, O) for O in mats]
+    got = [None] * len(mats)
+
+    def client(ids):
+        for i in ids:
+            t = binding.tor_submit(ctx, mats[i])
+            time.sleep(0.0005 * (i % 3))
+            got[i] = t
+
+    threads = [threading.Thread(target=client, args=(list(range(w, len(mats), 4)),)) for w in range(4)]
+    for th in threads:
+        th.start()
+    for th in threads:
+        th.join()
+    for i, t in enumerate(got):
+        st, r = binding.tor_poll(ctx, t, 120.0)
+        assert st == 0 and same(r, alone[i]), i
+    stats = ctx.serving_stats()
+    assert stats["served"] >= len(mats) and stats["queued"] == 0
+
+
+def test_admission_by_memory_budget():
+    mats = [inputs.lossy_squeezed(n, 5 + n, (0.3, 0.8), 0.5).O for n in (10, 11, 12, 13, 14)]
+    with binding.Context(device=0) as free:
+        alone = [binding.tor_eval(free, O) for O in mats]
+    # a budget that holds roughly one job at a time: requests wait for memory, none is lost
+    with binding.Context(device=0, mem_budget=1_500_000_000) as c:
+        tickets = [binding.tor_submit(c, O) for O in mats]
+        for t, a in zip(tickets, alone):
+            st, r = binding.tor_poll(c, t, 120.0)
+            assert st == 0 and abs(r.tor - a.tor) <= TOL * a.abs_sum
+    # a budget too small for any job: the request fails cleanly
+    with binding.Context(device=0, mem_budget=1_000_000) as c:
+        t = binding.tor_submit(c, mats[0])
+        st, r = binding.tor_poll(c, t, 60.0)
+        assert st == binding.TOR_ENOMEM
+
+
+def test_cancel_stops_a_running_evaluation():
+    inst = inputs.config_single(32)
+    with binding.Context(device=0) as c:
+        out = {}
+
+        def run():
+            out["r"] = binding.tor_eval(c, inst.O, check=False)
+
+        th = threading.Thread(target=run)
+        th.start()
+        time.sleep(0.3)
+        c.cancel()
+        th.join(timeout=60)
+        assert not th.is_alive()
+        assert out["r"].status == binding.TOR_ECANCELED
+        assert binding.tor_eval(c, inputs.config_n8().O).status == 0
