@@ -233,6 +233,112 @@ def run_reference(args, world, rank):
     return 0
 
 
+def serve_requests(rate: float, window: float, seed: int, N: int = 144):
+    """Seeded Poisson arrivals of chain-rule marginal requests on an N-mode state:
+    k ~ U{2..30}, j ~ U{max(k,1)..N}, S = a k-subset of modes 0..j-1 that
+    contains mode j-1 (the mode the chain rule is adding)."""
+    rng = np.random.default_rng(seed)
+    t, reqs = 0.0, []
+    while True:
+        t += rng.exponential(1.0 / rate)
+        if t > window:
+            break
+        k = int(rng.integers(2, 31))
+        j = int(rng.integers(max(k, 1), N + 1))
+        rest = rng.choice(j - 1, size=k - 1, replace=False) if k > 1 else np.zeros(0, dtype=int)
+        S = sorted([j - 1] + [int(x) for x in rest])
+        reqs.append((t, j, S))
+    return reqs
+
+
+def replay(ctx, sess, reqs, mode: str, drain_s: float):
+    """Submits reqs at their scheduled times; returns latencies (s) of the
+    requests completed by window end + drain_s, and counts.  mode 'served' =
+    tor_submit_marginal + polling; 'plain' = one blocking tor_eval_marginal at a
+    time in arrival order."""
+    from paper_2109_04528_gb300 import binding
+    window = reqs[-1][0] if reqs else 0.0
+    deadline = window + drain_s
+    lat, terms_done = [], 0.0
+    t0 = time.perf_counter()
+    if mode == "plain":
+        for (ta, j, S) in reqs:
+            now = time.perf_counter() - t0
+            if now > deadline:
+                break
+            if now < ta:
+                time.sleep(ta - now)
+            binding.tor_eval_marginal(ctx, sess, j, S)
+            lat.append(time.perf_counter() - t0 - ta)
+            terms_done += 2.0 ** len(S)
+        return lat, len(lat), terms_done
+    pending = {}
+    i = 0
+    while True:
+        now = time.perf_counter() - t0
+        while i < len(reqs) and reqs[i][0] <= now:
+            ta, j, S = reqs[i]
+            pending[binding.tor_submit_marginal(ctx, sess, j, S)] = (ta, len(S))
+            i += 1
+        for t in list(pending):
+            st, r = binding.tor_poll(ctx, t, 0.0)
+            if st != binding.TOR_EAGAIN:
+                ta, k = pending.pop(t)
+                if st == 0:
+                    lat.append(time.perf_counter() - t0 - ta)
+                    terms_done += 2.0 ** k
+        if (i >= len(reqs) and not pending) or now > deadline:
+            break
+        time.sleep(0.0002)
+    return lat, len(lat), terms_done
+
+
+def run_serve(args, world, rank, local):
+    """Serving benchmark on a 144-mode lossy squeezed state (r ~ U[0.5,1.2], eta = 0.3)."""
+    if rank != 0:
+        return 0
+    import torch
+
+    from paper_2109_04528_gb300 import binding, build
+    build.build()
+    torch.cuda.set_device(local)
+    inst = inputs.lossy_squeezed(144, inputs.SEED_BASE + 5, (0.5, 1.2), 0.3)
+
+    def pct(x, q):
+        if not x:
+            return None
+        x = sorted(x)
+        return x[min(len(x) - 1, int(q * len(x)))]
+
+    out = {"metric": "requests/s", "unit": "requests/s", "n_gpus": 1, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": "serve", "state": "144-mode lossy squeezed, r~U[0.5,1.2], eta=0.3",
+                      "request": "k~U{2..30}, j~U{max(k,1)..144}, S a k-subset of [j] containing j-1",
+                      "latency": "completion minus scheduled arrival"}}
+    runs = {}
+    for name, rate, window in (("overload", args.serve_rate, args.serve_window),
+                               ("sustained", args.serve_sustain_rate, args.serve_sustain_window)):
+        reqs = serve_requests(rate, window, inputs.SEED_BASE + 17)
+        for mode in ("served", "plain"):
+            with binding.Context(device=local) as ctx, binding.Session(ctx, inst.sigma) as sess:
+                binding.tor_eval_marginal(ctx, sess, 10, [0, 3, 9])  # warm-up
+                t0 = time.perf_counter()
+                lat, done, terms = replay(ctx, sess, reqs, mode, drain_s=2.0 if name == "overload" else 30.0)
+                el = time.perf_counter() - t0
+                stats = ctx.serving_stats()
+            runs[f"{name}_{mode}"] = {
+                "offered_rate": rate, "window_s": window, "offered": len(reqs), "completed": done,
+                "requests_per_s": done / el, "terms_per_s": terms / el,
+                "p50_ms": None if not lat else 1e3 * pct(lat, 0.5), "p99_ms": None if not lat else 1e3 * pct(lat, 0.99),
+                "backlog_at_end": len(reqs) - done, "batches": stats["batches"]}
+    out["runs"] = runs
+    s = runs["sustained_served"]
+    out["value"] = s["requests_per_s"]
+    out["p50_ms"], out["p99_ms"] = s["p50_ms"], s["p99_ms"]
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -242,12 +348,20 @@ def main():
     ap.add_argument("--impl", default="libtor", choices=["libtor", "reference"])
     ap.add_argument("--cpu-budget", type=float, default=12.0, help="seconds of oracle time for cpu_baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--autotune", type=float, default=0.0,
+                    help="seconds for the prefix-depth autotuner before timing (0 = built-in plan)")
+    ap.add_argument("--serve-window", type=float, default=2.0, help="serve: seconds of the overload window")
+    ap.add_argument("--serve-rate", type=float, default=2000.0, help="serve: offered requests/s")
+    ap.add_argument("--serve-sustain-rate", type=float, default=40.0, help="serve: sustainable requests/s")
+    ap.add_argument("--serve-sustain-window", type=float, default=8.0)
     args = ap.parse_args()
     if args.warmup < 3 and args.impl != "reference":
         args.warmup = 3
     world, rank, local = dist_setup(args)
     if args.impl == "reference":
         return run_reference(args, world, rank)
+    if args.workload == "serve":
+        return run_serve(args, world, rank, local)
 
     import torch
 
@@ -261,8 +375,19 @@ def main():
     flops = float(sum(algorithmic_flops(n) for n in ns))
     stream = torch.cuda.Stream(device=device)
     dmats = [torch.from_numpy(m).to(device) for m in mats]
-    ctx_dev = binding.Context(device=local, stream=stream.cuda_stream, flags=binding.TOR_IN_DEVICE)
-    ctx_host = binding.Context(device=local, stream=stream.cuda_stream)
+    ctx_dev = binding.Context(device=local, stream=stream.cuda_stream,
+                              flags=binding.TOR_IN_DEVICE | binding.TOR_GRAPHS)
+    ctx_host = binding.Context(device=local, stream=stream.cuda_stream, flags=binding.TOR_GRAPHS)
+    tuned = None
+    if args.autotune > 0:
+        sizes = sorted(set(ns))
+        plan_file = os.path.join(ROOT, "gpurun_out", f"plan_{args.workload}.txt")
+        os.makedirs(os.path.dirname(plan_file), exist_ok=True)
+        tuned = {}
+        for n in sizes:
+            tuned.update(ctx_host.autotune(n, n, args.autotune / len(sizes)))
+        ctx_host.save_plan(plan_file)
+        ctx_dev.load_plan(plan_file)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=device)
     dfma, fp64_tflops = binding.tor_probe_fp64(local, 0.5)
 
@@ -300,6 +425,27 @@ def main():
     e2e_tot = max_over_ranks(world, sum(e2e_ms), device)
     value = terms * world * args.steps / (tot_ms * 1e-3)
     e2e_value = terms * world * args.steps / (e2e_tot * 1e-3)
+    plain = None
+    if len(mats) > 8:
+        # the plain GPU path: one tor_eval (launch + sync) per matrix, same kernels and plan
+        with binding.Context(device=local, stream=stream.cuda_stream, flags=binding.TOR_IN_DEVICE) as ctx_plain:
+            if tuned:
+                ctx_plain.load_plan(plan_file)
+            for m in dmats[:64]:
+                binding.tor_eval(ctx_plain, m)
+            torch.cuda.synchronize()
+            lat = []
+            t0 = time.perf_counter()
+            for m in dmats:
+                a = time.perf_counter()
+                binding.tor_eval(ctx_plain, m)
+                lat.append(time.perf_counter() - a)
+            plain_s = time.perf_counter() - t0
+        lat.sort()
+        plain = {"value": terms / plain_s, "unit": "subset terms/s", "tor_per_s": len(mats) / plain_s,
+                 "ms_per_batch": 1e3 * plain_s, "per_matrix_ms_p50": 1e3 * lat[len(lat) // 2],
+                 "per_matrix_ms_p99": 1e3 * lat[min(len(lat) - 1, int(0.99 * len(lat)))],
+                 "what": "one blocking tor_eval per matrix (H2D descriptors, 3 kernels, D2H, sync), host-timed"}
     units_avg = sum(units_ms) / len(units_ms)
     achieved = flops / (units_avg * 1e-3) / 1e12
     line = {
@@ -321,6 +467,11 @@ def main():
         "gpu_launches": 3 * args.steps,
         "clocks": clk.summary(),
     }
+    if tuned:
+        line["config"]["autotuned"] = True
+    if plain:
+        line["plain_per_matrix"] = plain
+        line["batched_over_plain"] = value / plain["value"]
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(mats, args.cpu_budget)
     if rank == 0:

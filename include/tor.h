@@ -99,8 +99,10 @@ void tor_config_default(tor_config* cfg);
  * nothing large until the first evaluation.  *out is NULL on failure. */
 tor_status tor_create(const tor_config* cfg, tor_ctx** out);
 
-/* Frees the context and all its device and pinned memory.  Blocks until the
- * context's outstanding work has finished.  NULL is ignored. */
+/* Frees the context and all its device and pinned memory.  Requests still
+ * queued for the serving loop are dropped, running kernels are asked to stop
+ * (as tor_cancel), and the call blocks until the GPU work has ended.  Tickets
+ * of the context are invalid afterwards.  NULL is ignored. */
 void tor_destroy(tor_ctx* ctx);
 
 /* Tor of one 2n x 2n matrix (Eq. tor).  Blocking.  The call's return value is

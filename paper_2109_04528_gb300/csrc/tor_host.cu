@@ -188,6 +188,7 @@ struct tor_ctx {
   size_t queue_limit = 1 << 20;
   int n_serve_slots = 2;
   int max_batch = 4096;
+  double max_batch_terms = 268435456.0;  // ~45 ms of GPU work per served batch (2^28 subset terms)
   std::vector<std::unique_ptr<Slot>> serve;
   std::atomic<long long> served{0}, batches{0};
 };
@@ -613,7 +614,12 @@ static void server_loop(tor_ctx* ctx) {
       std::vector<Request*> batch;
       {
         std::lock_guard<std::mutex> lk(ctx->q_mu);
+        double terms = 0;
         while (!ctx->queue.empty() && (int)batch.size() < ctx->max_batch) {
+          const int n = ctx->queue.front()->in.n;
+          const double t = std::ldexp(1.0, std::max(0, std::min(n, 64)));
+          if (!batch.empty() && terms + t > ctx->max_batch_terms) break;
+          terms += t;
           batch.push_back(ctx->queue.front());
           ctx->queue.pop_front();
         }
@@ -847,9 +853,19 @@ tor_status tor_create(const tor_config* cfg, tor_ctx** out) {
 void tor_destroy(tor_ctx* ctx) {
   if (!ctx) return;
   {
+    // requests still queued are dropped (TOR_ECANCELED); jobs on the GPU are asked to stop
     std::lock_guard<std::mutex> lk(ctx->q_mu);
     ctx->stopping = true;
+    for (Request* r : ctx->queue) {
+      r->res = tor_result{};
+      r->res.n = r->in.n;
+      r->res.status = TOR_ECANCELED;
+      r->done = true;
+    }
+    ctx->queue.clear();
+    if (ctx->h_cancel) __atomic_add_fetch(ctx->h_cancel, 1, __ATOMIC_SEQ_CST);
   }
+  ctx->done_cv.notify_all();
   ctx->q_cv.notify_all();
   if (ctx->server.joinable()) ctx->server.join();
   for (auto& kv : ctx->reqs) delete kv.second;
