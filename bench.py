@@ -297,11 +297,8 @@ def run_serve(args, world, rank, local):
     """Serving benchmark on a 144-mode lossy squeezed state (r ~ U[0.5,1.2], eta = 0.3)."""
     if rank != 0:
         return 0
-    import torch
-
     from paper_2109_04528_gb300 import binding, build
     build.build()
-    torch.cuda.set_device(local)
     inst = inputs.lossy_squeezed(144, inputs.SEED_BASE + 5, (0.5, 1.2), 0.3)
 
     def pct(x, q):
@@ -320,12 +317,15 @@ def run_serve(args, world, rank, local):
                                ("sustained", args.serve_sustain_rate, args.serve_sustain_window)):
         reqs = serve_requests(rate, window, inputs.SEED_BASE + 17)
         for mode in ("served", "plain"):
-            with binding.Context(device=local) as ctx, binding.Session(ctx, inst.sigma) as sess:
-                binding.tor_eval_marginal(ctx, sess, 10, [0, 3, 9])  # warm-up
-                t0 = time.perf_counter()
-                lat, done, terms = replay(ctx, sess, reqs, mode, drain_s=2.0 if name == "overload" else 30.0)
-                el = time.perf_counter() - t0
-                stats = ctx.serving_stats()
+            ctx = binding.Context(device=local)
+            sess = binding.Session(ctx, inst.sigma)
+            binding.tor_eval_marginal(ctx, sess, 10, [0, 3, 9])  # warm-up
+            t0 = time.perf_counter()
+            lat, done, terms = replay(ctx, sess, reqs, mode, drain_s=2.0 if name == "overload" else 30.0)
+            el = time.perf_counter() - t0
+            stats = ctx.serving_stats()
+            ctx.close()  # drops the backlog, stops running jobs, waits for the GPU
+            sess.close()
             runs[f"{name}_{mode}"] = {
                 "offered_rate": rate, "window_s": window, "offered": len(reqs), "completed": done,
                 "requests_per_s": done / el, "terms_per_s": terms / el,
@@ -375,8 +375,9 @@ def main():
     flops = float(sum(algorithmic_flops(n) for n in ns))
     stream = torch.cuda.Stream(device=device)
     dmats = [torch.from_numpy(m).to(device) for m in mats]
-    ctx_dev = binding.Context(device=local, stream=stream.cuda_stream,
-                              flags=binding.TOR_IN_DEVICE | binding.TOR_GRAPHS)
+    # device-resident inputs, plain launches (per-kernel CUDA-event times for the roofline)
+    ctx_dev = binding.Context(device=local, stream=stream.cuda_stream, flags=binding.TOR_IN_DEVICE)
+    # host inputs through the C ABI, replayed as a CUDA graph
     ctx_host = binding.Context(device=local, stream=stream.cuda_stream, flags=binding.TOR_GRAPHS)
     tuned = None
     if args.autotune > 0:
@@ -425,6 +426,15 @@ def main():
     e2e_tot = max_over_ranks(world, sum(e2e_ms), device)
     value = terms * world * args.steps / (tot_ms * 1e-3)
     e2e_value = terms * world * args.steps / (e2e_tot * 1e-3)
+    # the same device-resident step replayed as a CUDA graph
+    graph_ms = None
+    with binding.Context(device=local, stream=stream.cuda_stream,
+                         flags=binding.TOR_IN_DEVICE | binding.TOR_GRAPHS) as ctx_g:
+        if tuned:
+            ctx_g.load_plan(plan_file)
+        timed(ctx_g, dmats, 2)
+        gms, _ = timed(ctx_g, dmats, args.steps)
+        graph_ms = sum(gms) / len(gms)
     plain = None
     if len(mats) > 8:
         # the plain GPU path: one tor_eval (launch + sync) per matrix, same kernels and plan
@@ -467,6 +477,7 @@ def main():
         "gpu_launches": 3 * args.steps,
         "clocks": clk.summary(),
     }
+    line["graph_replay"] = {"ms_per_step": graph_ms, "value": terms / (graph_ms * 1e-3), "unit": "subset terms/s"}
     if tuned:
         line["config"]["autotuned"] = True
     if plain:
@@ -478,6 +489,7 @@ def main():
         print(json.dumps(line), flush=True)
     ctx_dev.close()
     ctx_host.close()
+    torch.cuda.synchronize()  # surface any late device error in this process
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()

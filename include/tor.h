@@ -146,6 +146,12 @@ tor_status tor_serving_stats(tor_ctx* ctx, long long* served, long long* batches
  * ~64 MB for 144 modes).  The caller's buffer may be freed afterwards. */
 tor_status tor_session_create(tor_ctx* ctx, int n_total, const tor_c128* M, int ld, int kind,
                               tor_session** out);
+
+/* Frees a session's device matrices.  Requests of this session still queued
+ * are completed with TOR_ECANCELED, and the call blocks until every request
+ * of the session that is already running on the GPU has finished, so no
+ * kernel reads the matrices after they are freed.  A session may outlive its
+ * context (destroying the context detaches it).  NULL is ignored. */
 void tor_session_destroy(tor_session* s);
 
 /* Tor(O^(j)_S) for S = modes[0..k-1] (distinct, each < j, any order), blocking. */
@@ -164,7 +170,8 @@ tor_status tor_cancel(tor_ctx* ctx);
 /* Human-readable name of a status.  Never NULL. */
 const char* tor_strerror(tor_status s);
 
-/* Last CUDA error string seen by this context ("" if none).  Never NULL. */
+/* Last CUDA error string seen by this context ("" if none); with ctx == NULL,
+ * the last error of a failed tor_create on this thread.  Never NULL. */
 const char* tor_last_error(tor_ctx* ctx);
 
 /* ---- inspection and measurement (same kernels, more output) ---- */
@@ -187,7 +194,8 @@ tor_status tor_eval_units(tor_ctx* ctx, int n, const tor_c128* O, int ld, double
 
 /* Device time of the last tor_eval / tor_eval_batch, split by kernel, from CUDA
  * events on the context's stream: [0] intake, [1] units, [2] reduce, [3] total
- * (ms).  times must hold 4 doubles. */
+ * (ms).  With TOR_GRAPHS only the total is measured; [0..2] are -1.  times
+ * must hold 4 doubles. */
 tor_status tor_last_times(tor_ctx* ctx, double* times);
 
 /* Autotuner: for every n in [n_lo, n_hi], times tor_eval at prefix depths

@@ -158,7 +158,7 @@ class Context:
         h = ctypes.c_void_p()
         st = lib.tor_create(ctypes.byref(cfg), ctypes.byref(h))
         if st != TOR_OK:
-            raise TorError(st, "tor_create")
+            raise TorError(st, "tor_create: " + lib.tor_last_error(None).decode())
         self._h = h
         self._lib = lib
         self.flags = flags

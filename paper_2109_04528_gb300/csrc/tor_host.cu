@@ -132,6 +132,7 @@ struct Slot {
   size_t bytes = 0;
   int cancel_epoch = 0;
   bool busy = false;
+  bool graphed = false;  // the last pass was a graph replay
 
   void release() {
     for (DevBuf* b : {&d_O, &d_B, &d_mats, &d_tasks, &d_partials, &d_flags, &d_results, &d_lane, &d_warp, &d_ctl,
@@ -151,8 +152,12 @@ struct Slot {
 }  // namespace
 
 struct tor_session {
-  tor_ctx* ctx = nullptr;
+  tor_ctx* ctx = nullptr;  // null once the context has been destroyed
+  int device = 0;
   int N = 0;
+  int inflight = 0;        // requests taken by the serving loop and not completed (guarded by ctx->q_mu)
+  int blocking = 0;        // tor_eval_marginal calls in progress (guarded by ctx->q_mu)
+  bool closing = false;
   DevBuf d_O;                  // O^(j) for j = 1..N, pairs layout, 2j x 2j row-major each
   std::vector<long long> off;  // element offset of O^(j)
   uint64_t gen = 0;
@@ -160,6 +165,7 @@ struct tor_session {
 
 struct Request {
   uint64_t ticket = 0;
+  tor_session* sess = nullptr;  // the session a marginal request reads, or null
   MatIn in;
   std::vector<tor_c128> O;  // owned copy of a host matrix
   std::vector<int> modes;   // owned copy of a marginal's mode list
@@ -191,14 +197,17 @@ struct tor_ctx {
   double max_batch_terms = 268435456.0;  // ~45 ms of GPU work per served batch (2^28 subset terms)
   std::vector<std::unique_ptr<Slot>> serve;
   std::atomic<long long> served{0}, batches{0};
+  std::vector<tor_session*> sessions;  // live sessions of this context (guarded by q_mu)
 };
 
+// Last error of a call that had no context to record it in (tor_create).
+static thread_local std::string g_create_error;
+
 static tor_status cuda_fail(tor_ctx* ctx, cudaError_t e, const char* what) {
-  if (ctx) {
-    char buf[256];
-    snprintf(buf, sizeof buf, "%s: %s", what, cudaGetErrorString(e));
-    ctx->last_error = buf;
-  }
+  char buf[256];
+  snprintf(buf, sizeof buf, "%s: %s", what, cudaGetErrorString(e));
+  if (ctx) ctx->last_error = buf;
+  g_create_error = buf;
   cudaGetLastError();
   return e == cudaErrorMemoryAllocation ? TOR_ENOMEM : TOR_ECUDA;
 }
@@ -406,11 +415,12 @@ static uint64_t mix(uint64_t h, uint64_t v) {
   return h;
 }
 
-// The stream operations of one pass (what a graph captures).
-static tor_status slot_record(tor_ctx* ctx, Slot& S) {
+// The stream operations of one pass (what a graph captures; the timing
+// events stay outside graphs).
+static tor_status slot_record(tor_ctx* ctx, Slot& S, bool timed) {
   cudaStream_t s = S.stream;
   const int J = S.J;
-  CK(cudaEventRecord(S.ev[0], s), "event");
+  if (timed) CK(cudaEventRecord(S.ev[0], s), "event");
   if (S.o_elems) CK(cudaMemcpyAsync(S.d_O.p, S.h_O.p, S.o_elems * 16, cudaMemcpyHostToDevice, s), "H2D O");
   if (S.mode_elems)
     CK(cudaMemcpyAsync(S.d_modes.p, S.h_modes.p, S.mode_elems * sizeof(int), cudaMemcpyHostToDevice, s), "H2D modes");
@@ -418,10 +428,10 @@ static tor_status slot_record(tor_ctx* ctx, Slot& S) {
   CK(cudaMemcpyAsync(S.d_tasks.p, S.h_tasks.p, S.tasks.size() * sizeof(TaskDesc), cudaMemcpyHostToDevice, s),
      "H2D tasks");
   CK(cudaMemsetAsync(S.d_ctl.p, 0, 64, s), "memset control");
-  CK(cudaEventRecord(S.ev[1], s), "event");
+  if (timed) CK(cudaEventRecord(S.ev[1], s), "event");
   const bool check = !(ctx->cfg.flags & TOR_NO_CHECK);
   CK(launch_intake((const MatDesc*)S.d_mats.p, J, check ? 1 : 0, (int*)S.d_flags.p, s), "k_intake");
-  CK(cudaEventRecord(S.ev[2], s), "event");
+  if (timed) CK(cudaEventRecord(S.ev[2], s), "event");
   UnitsParams prm;
   prm.mats = (const MatDesc*)S.d_mats.p;
   prm.tasks = (const TaskDesc*)S.d_tasks.p;
@@ -439,11 +449,11 @@ static tor_status slot_record(tor_ctx* ctx, Slot& S) {
   prm.cancel_epoch = S.cancel_epoch;
   prm.budget_ns = ctx->cfg.timeout_s > 0 ? (long long)(ctx->cfg.timeout_s * 1e9) : 0;
   CK(launch_units(prm, ctx->grid, s), "k_units");
-  CK(cudaEventRecord(S.ev[3], s), "event");
+  if (timed) CK(cudaEventRecord(S.ev[3], s), "event");
   CK(launch_reduce((const MatDesc*)S.d_mats.p, J, (const Part*)S.d_partials.p + S.parts, (const int*)S.d_flags.p,
                    (ResultRec*)S.d_results.p, s),
      "k_reduce");
-  CK(cudaEventRecord(S.ev[4], s), "event");
+  if (timed) CK(cudaEventRecord(S.ev[4], s), "event");
   CK(cudaMemcpyAsync(S.h_results.p, S.d_results.p, J * sizeof(ResultRec), cudaMemcpyDeviceToHost, s), "D2H results");
   if (S.want_parts)
     CK(cudaMemcpyAsync((char*)S.h_results.p + J * sizeof(ResultRec), S.d_partials.p, S.parts * 32,
@@ -456,8 +466,9 @@ static tor_status slot_record(tor_ctx* ctx, Slot& S) {
 // Enqueues the prepared job (graph replay when enabled and the shape repeats).
 static tor_status slot_launch(tor_ctx* ctx, Slot& S) {
   S.cancel_epoch = __atomic_load_n(ctx->h_cancel, __ATOMIC_SEQ_CST);
-  if (!(ctx->cfg.flags & TOR_GRAPHS)) {
-    tor_status st = slot_record(ctx, S);
+  S.graphed = (ctx->cfg.flags & TOR_GRAPHS) != 0;
+  if (!S.graphed) {
+    tor_status st = slot_record(ctx, S, true);
     if (st != TOR_OK) return st;
     CK(cudaEventRecord(S.done, S.stream), "event");
     return TOR_OK;
@@ -477,7 +488,7 @@ static tor_status slot_launch(tor_ctx* ctx, Slot& S) {
     if (g.key == key && g.gen == S.gen) exec = g.exec;
   if (!exec) {
     CK(cudaStreamBeginCapture(S.stream, cudaStreamCaptureModeThreadLocal), "begin capture");
-    tor_status st = slot_record(ctx, S);
+    tor_status st = slot_record(ctx, S, false);
     cudaGraph_t graph = nullptr;
     cudaError_t e = cudaStreamEndCapture(S.stream, &graph);
     if (st != TOR_OK) {
@@ -501,7 +512,9 @@ static tor_status slot_launch(tor_ctx* ctx, Slot& S) {
     }
     S.graphs.push_back({key, S.gen, exec});
   }
+  CK(cudaEventRecord(S.ev[0], S.stream), "event");
   CK(cudaGraphLaunch(exec, S.stream), "graph launch");
+  CK(cudaEventRecord(S.ev[4], S.stream), "event");
   CK(cudaEventRecord(S.done, S.stream), "event");
   return TOR_OK;
 }
@@ -536,10 +549,12 @@ static tor_status slot_finish(Slot& S, tor_result* out, double* unit_partials, d
     }
   }
   if (times) {
-    float ms[4] = {0, 0, 0, 0};
-    cudaEventElapsedTime(&ms[0], S.ev[1], S.ev[2]);
-    cudaEventElapsedTime(&ms[1], S.ev[2], S.ev[3]);
-    cudaEventElapsedTime(&ms[2], S.ev[3], S.ev[4]);
+    float ms[4] = {-1, -1, -1, -1};
+    if (!S.graphed) {
+      cudaEventElapsedTime(&ms[0], S.ev[1], S.ev[2]);
+      cudaEventElapsedTime(&ms[1], S.ev[2], S.ev[3]);
+      cudaEventElapsedTime(&ms[2], S.ev[3], S.ev[4]);
+    }
     cudaEventElapsedTime(&ms[3], S.ev[0], S.ev[4]);
     cudaGetLastError();
     for (int i = 0; i < 4; ++i) times[i] = ms[i];
@@ -567,8 +582,12 @@ static tor_status run_blocking(tor_ctx* ctx, const std::vector<MatIn>& ins, tor_
 // ---------------------------------------------------------------------------
 // Serving thread: continuous batching over several slots.
 // ---------------------------------------------------------------------------
+// Marks requests taken from the queue as finished; releases their session.
 static void complete(tor_ctx* ctx, std::vector<Request*>& reqs) {  // caller holds q_mu
-  for (Request* r : reqs) r->done = true;
+  for (Request* r : reqs) {
+    r->done = true;
+    if (r->sess) --r->sess->inflight;
+  }
   ctx->done_cv.notify_all();
 }
 
@@ -620,8 +639,10 @@ static void server_loop(tor_ctx* ctx) {
           const double t = std::ldexp(1.0, std::max(0, std::min(n, 64)));
           if (!batch.empty() && terms + t > ctx->max_batch_terms) break;
           terms += t;
-          batch.push_back(ctx->queue.front());
+          Request* r = ctx->queue.front();
           ctx->queue.pop_front();
+          if (r->sess) ++r->sess->inflight;  // the session's matrices stay alive until complete()
+          batch.push_back(r);
         }
       }
       if (batch.empty()) break;
@@ -632,6 +653,7 @@ static void server_loop(tor_ctx* ctx) {
         size_t need = job_bytes(ctx, ins, ins.size());
         while (batch.size() > 1 && reserved + need > ctx->cfg.mem_budget) {
           std::lock_guard<std::mutex> lk(ctx->q_mu);
+          if (batch.back()->sess) --batch.back()->sess->inflight;
           ctx->queue.push_front(batch.back());
           batch.pop_back();
           ins.pop_back();
@@ -645,6 +667,7 @@ static void server_loop(tor_ctx* ctx) {
             batch[0]->res.status = TOR_ENOMEM;
             complete(ctx, batch);
           } else {  // wait for a job in flight to finish
+            if (batch[0]->sess) --batch[0]->sess->inflight;
             ctx->queue.push_front(batch[0]);
           }
           break;
@@ -802,7 +825,7 @@ const char* tor_strerror(tor_status s) {
   return "unknown status";
 }
 
-const char* tor_last_error(tor_ctx* ctx) { return ctx ? ctx->last_error.c_str() : ""; }
+const char* tor_last_error(tor_ctx* ctx) { return ctx ? ctx->last_error.c_str() : g_create_error.c_str(); }
 
 tor_status tor_plan_load(tor_ctx* ctx, const char* path);
 
@@ -816,10 +839,7 @@ tor_status tor_create(const tor_config* cfg, tor_ctx** out) {
   if (c.timeout_s < 0) return TOR_EINVAL;
   int ndev = 0;
   cudaError_t e = cudaGetDeviceCount(&ndev);
-  if (e != cudaSuccess) {
-    cudaGetLastError();
-    return TOR_ECUDA;
-  }
+  if (e != cudaSuccess) return cuda_fail(nullptr, e, "cudaGetDeviceCount");
   if (c.device < 0 || c.device >= ndev) return TOR_EINVAL;
   tor_ctx* ctx = new tor_ctx();
   ctx->cfg = c;
@@ -870,8 +890,14 @@ void tor_destroy(tor_ctx* ctx) {
   if (ctx->server.joinable()) ctx->server.join();
   for (auto& kv : ctx->reqs) delete kv.second;
   ctx->reqs.clear();
+  for (tor_session* s : ctx->sessions) s->ctx = nullptr;  // sessions outlive the context, detached
+  ctx->sessions.clear();
   cudaSetDevice(ctx->cfg.device);
-  if (ctx->main.stream) cudaStreamSynchronize(ctx->main.stream);
+  if (ctx->main.stream) {
+    const cudaError_t e = cudaStreamSynchronize(ctx->main.stream);
+    if (e != cudaSuccess && getenv("TOR_DEBUG"))
+      fprintf(stderr, "libtor: tor_destroy: stream synchronize failed: %s\n", cudaGetErrorString(e));
+  }
   ctx->main.release();
   for (auto& s : ctx->serve) s->release();
   ctx->serve.clear();
@@ -1022,6 +1048,7 @@ tor_status tor_session_create(tor_ctx* ctx, int n_total, const tor_c128* M, int 
   if (kind == TOR_SESSION_SIGMA && !hpd_inverse(K, m)) return TOR_ENOTPD;
   tor_session* s = new tor_session();
   s->ctx = ctx;
+  s->device = ctx->cfg.device;
   s->N = N;
   s->off.assign(N + 1, 0);
   long long tot = 0;
@@ -1070,13 +1097,38 @@ tor_status tor_session_create(tor_ctx* ctx, int n_total, const tor_c128* M, int 
     delete s;
     return st;
   }
+  {
+    std::lock_guard<std::mutex> lk(ctx->q_mu);
+    ctx->sessions.push_back(s);
+  }
   *out = s;
   return TOR_OK;
 }
 
 void tor_session_destroy(tor_session* s) {
   if (!s) return;
-  if (s->ctx) cudaSetDevice(s->ctx->cfg.device);
+  if (tor_ctx* ctx = s->ctx) {
+    // Drop the session's queued requests, then wait until no job in flight
+    // reads its matrices any more; only then free them.
+    std::unique_lock<std::mutex> lk(ctx->q_mu);
+    s->closing = true;
+    std::deque<Request*> keep;
+    for (Request* r : ctx->queue) {
+      if (r->sess == s) {
+        r->res = tor_result{};
+        r->res.n = r->in.n;
+        r->res.status = TOR_ECANCELED;
+        r->done = true;
+      } else {
+        keep.push_back(r);
+      }
+    }
+    ctx->queue.swap(keep);
+    ctx->done_cv.notify_all();
+    ctx->done_cv.wait(lk, [&] { return s->inflight == 0 && s->blocking == 0; });
+    ctx->sessions.erase(std::remove(ctx->sessions.begin(), ctx->sessions.end(), s), ctx->sessions.end());
+  }
+  cudaSetDevice(s->device);
   s->d_O.release();
   delete s;
 }
@@ -1108,8 +1160,21 @@ tor_status tor_eval_marginal(tor_ctx* ctx, tor_session* s, int j, int k, const i
   std::vector<int> own;
   tor_status st = marginal_in(s, j, k, modes, ins[0], own);
   if (st != TOR_OK) return st;
-  std::lock_guard<std::mutex> lk(ctx->run_mu);
-  return run_blocking(ctx, ins, out, nullptr, 0);
+  {
+    std::lock_guard<std::mutex> lq(ctx->q_mu);
+    if (s->closing) return TOR_EINVAL;
+    ++s->blocking;
+  }
+  {
+    std::lock_guard<std::mutex> lk(ctx->run_mu);
+    st = run_blocking(ctx, ins, out, nullptr, 0);
+  }
+  {
+    std::lock_guard<std::mutex> lq(ctx->q_mu);
+    --s->blocking;
+  }
+  ctx->done_cv.notify_all();
+  return st;
 }
 
 tor_status tor_submit_marginal(tor_ctx* ctx, tor_session* s, int j, int k, const int* modes, uint64_t* ticket) {
@@ -1121,6 +1186,14 @@ tor_status tor_submit_marginal(tor_ctx* ctx, tor_session* s, int j, int k, const
     return st;
   }
   r->in.modes = k ? r->modes.data() : nullptr;
+  r->sess = s;
+  {
+    std::lock_guard<std::mutex> lq(ctx->q_mu);
+    if (s->closing) {
+      delete r;
+      return TOR_EINVAL;
+    }
+  }
   return enqueue_request(ctx, r, ticket);
 }
 

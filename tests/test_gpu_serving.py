@@ -174,3 +174,32 @@ def test_cancel_stops_a_running_evaluation():
         assert not th.is_alive()
         assert out["r"].status == binding.TOR_ECANCELED
         assert binding.tor_eval(c, inputs.config_n8().O).status == 0
+
+
+def test_session_destroyed_while_requests_run():
+    # Destroying a session with requests still queued or on the GPU must not
+    # free its matrices under the running kernels: queued requests are
+    # cancelled, running ones finish first, and the context keeps working.
+    inst = inputs.lossy_squeezed(40, 21, (0.5, 1.2), 0.3)
+    rng = np.random.default_rng(3)
+    with binding.Context(device=0) as c:
+        sess = binding.Session(c, inst.sigma)
+        tickets = []
+        for _ in range(3000):  # ~1e10 subset terms: most are still queued when the session goes
+            k = int(rng.integers(2, 27))
+            j = int(rng.integers(k, 41))
+            S = sorted(rng.choice(j, size=k, replace=False).tolist())
+            tickets.append(binding.tor_submit_marginal(c, sess, j, S))
+        time.sleep(0.05)
+        sess.close()
+        ok = cancelled = 0
+        for t in tickets:
+            st, r = binding.tor_poll(c, t, 120.0)
+            assert st in (binding.TOR_OK, binding.TOR_ECANCELED)
+            ok += st == binding.TOR_OK
+            cancelled += st == binding.TOR_ECANCELED
+        assert ok + cancelled == len(tickets) and cancelled > 0
+        assert binding.tor_eval(c, inputs.config_n8().O).status == binding.TOR_OK
+        # a session may also outlive its context
+        sess2 = binding.Session(c, inst.sigma)
+    sess2.close()
