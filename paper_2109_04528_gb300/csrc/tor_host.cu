@@ -633,11 +633,16 @@ static void server_loop(tor_ctx* ctx) {
       std::vector<Request*> batch;
       {
         std::lock_guard<std::mutex> lk(ctx->q_mu);
+        // FIFO; a large request (over 1/8 of the batch cap) runs as a batch of its own,
+        // so small requests never wait for a large one to finish
         double terms = 0;
+        bool large = false;
         while (!ctx->queue.empty() && (int)batch.size() < ctx->max_batch) {
           const int n = ctx->queue.front()->in.n;
           const double t = std::ldexp(1.0, std::max(0, std::min(n, 64)));
-          if (!batch.empty() && terms + t > ctx->max_batch_terms) break;
+          const bool big = t > ctx->max_batch_terms / 8;
+          if (!batch.empty() && (large || big || terms + t > ctx->max_batch_terms)) break;
+          large = big;
           terms += t;
           Request* r = ctx->queue.front();
           ctx->queue.pop_front();
