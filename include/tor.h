@@ -192,6 +192,20 @@ tor_status tor_set_prefix_depth(tor_ctx* ctx, int n, int p);
 tor_status tor_eval_units(tor_ctx* ctx, int n, const tor_c128* O, int ld, double* partials,
                           size_t partials_len, tor_result* out);
 
+/* ---- sharding one matrix across processes or GPUs ----
+ *
+ * The final reduction of tor_eval is a fixed binary tree whose leaves are the
+ * matrix's warp tasks: 2^(p-5) of them for prefix depth p >= 5, each the sum
+ * of 32 units.  tor_plan_leaves gives that count (2^p units for p < 5).
+ * tor_eval_range evaluates the leaves [leaf_lo, leaf_lo + leaf_count) only and
+ * returns their binary-tree sum in out (hi, lo, abs_sum, status).  leaf_count
+ * must be a power of two and leaf_lo a multiple of it, and p >= 5.  Combining
+ * the results of the 2^s equal aligned ranges with the same tree (double-double
+ * addition, left operand first) reproduces tor_eval's result bitwise. */
+long long tor_plan_leaves(tor_ctx* ctx, int n);
+tor_status tor_eval_range(tor_ctx* ctx, int n, const tor_c128* O, int ld, long long leaf_lo, long long leaf_count,
+                          tor_result* out);
+
 /* Device time of the last tor_eval / tor_eval_batch, split by kernel, from CUDA
  * events on the context's stream: [0] intake, [1] units, [2] reduce, [3] total
  * (ms).  With TOR_GRAPHS only the total is measured; [0..2] are -1.  times

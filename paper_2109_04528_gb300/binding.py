@@ -27,7 +27,8 @@ EXPORTS = ["tor_config_default", "tor_create", "tor_destroy", "tor_eval", "tor_e
            "tor_poll", "tor_cancel", "tor_strerror", "tor_last_error", "tor_plan_prefix_depth",
            "tor_set_prefix_depth", "tor_eval_units", "tor_last_times", "tor_probe_fp64",
            "tor_eval_noalloc", "tor_autotune", "tor_plan_save", "tor_plan_load", "tor_serving_stats",
-           "tor_session_create", "tor_session_destroy", "tor_eval_marginal", "tor_submit_marginal"]
+           "tor_session_create", "tor_session_destroy", "tor_eval_marginal", "tor_submit_marginal",
+           "tor_plan_leaves", "tor_eval_range"]
 TOR_NOALLOC_MAX_N = 16
 
 
@@ -115,6 +116,9 @@ def load_library():
     lib.tor_session_destroy.restype = None
     lib.tor_eval_marginal.argtypes = [c_void_p, c_void_p, c_int, c_int, P(c_int), P(tor_result)]
     lib.tor_submit_marginal.argtypes = [c_void_p, c_void_p, c_int, c_int, P(c_int), P(ctypes.c_uint64)]
+    lib.tor_plan_leaves.argtypes = [c_void_p, c_int]
+    lib.tor_plan_leaves.restype = LL
+    lib.tor_eval_range.argtypes = [c_void_p, c_int, c_void_p, c_int, LL, LL, P(tor_result)]
     _LIB = lib
     return lib
 
@@ -288,6 +292,21 @@ def tor_eval_units(ctx: Context, O):
         raise TorError(st, ctx.last_error() or "tor_eval_units")
     del keep
     return TorResult.of(res), p, parts
+
+
+def tor_plan_leaves(ctx: Context, n: int) -> int:
+    return int(ctx._lib.tor_plan_leaves(ctx.handle, n))
+
+
+def tor_eval_range(ctx: Context, O, leaf_lo: int, leaf_count: int) -> TorResult:
+    """Partial Tor over reduction leaves [leaf_lo, leaf_lo + leaf_count) (one shard)."""
+    keep, n, ld, ptr = _matrix_args(ctx, O)
+    res = tor_result()
+    st = ctx._lib.tor_eval_range(ctx.handle, n, ctypes.c_void_p(ptr), ld, leaf_lo, leaf_count, ctypes.byref(res))
+    if st != TOR_OK:
+        raise TorError(st, ctx.last_error() or "tor_eval_range")
+    del keep
+    return TorResult.of(res)
 
 
 def tor_submit(ctx: Context, O) -> int:

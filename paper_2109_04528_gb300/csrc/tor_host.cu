@@ -107,6 +107,8 @@ struct MatIn {
   int layout = TOR_LAYOUT_BLOCK;
   bool dev = false;             // O is a device pointer
   const int* modes = nullptr;   // host list of n source modes (session marginals), or null
+  long long leaf_lo = 0;        // tor_eval_range: first reduction leaf (warp task) to evaluate
+  long long leaf_count = -1;    // tor_eval_range: number of leaves; -1 = all
 };
 
 struct Slot {
@@ -320,6 +322,13 @@ static tor_status slot_prepare(tor_ctx* ctx, Slot& S, const std::vector<MatIn>& 
     D.part_off = S.parts;
     S.parts += 1ll << p;
     D.red_log2 = p >= 5 ? p - 5 : p;
+    D.red_lo = 0;
+    if (m.leaf_count > 0) {  // a shard: leaves [leaf_lo, leaf_lo + leaf_count) only (p >= 5)
+      int lg = 0;
+      while ((1ll << lg) < m.leaf_count) ++lg;
+      D.red_log2 = lg;
+      D.red_lo = m.leaf_lo;
+    }
     D.red_off = S.reds;
     S.reds += 1ll << D.red_log2;
     S.b_elems += tri(m.n);
@@ -334,8 +343,12 @@ static tor_status slot_prepare(tor_ctx* ctx, Slot& S, const std::vector<MatIn>& 
     while (k < J && S.mats[k].n == S.mats[j].n) ++k;
     const int p = S.mats[j].p, M = S.mats[j].n - p;
     if (p >= 5) {
-      for (int a = j; a < k; ++a)
-        for (int t = 0; t < (1 << (p - 5)); ++t) S.tasks.push_back({a, t, 1, M});
+      for (int a = j; a < k; ++a) {
+        const MatIn& m = ins[S.act[a]];
+        const long long t0 = m.leaf_count > 0 ? m.leaf_lo : 0;
+        const long long t1 = m.leaf_count > 0 ? m.leaf_lo + m.leaf_count : (1ll << (p - 5));
+        for (long long t = t0; t < t1; ++t) S.tasks.push_back({a, (int)t, 1, M});
+      }
     } else {
       const long long units = (long long)(k - j) << p;
       for (long long t = 0; t * 32 < units; ++t) S.tasks.push_back({j, (int)t, k - j, M});
@@ -477,6 +490,7 @@ static tor_status slot_launch(tor_ctx* ctx, Slot& S) {
   for (const MatDesc& D : S.mats)
     key = mix(key, (uint64_t)D.n | (uint64_t)D.p << 8 | (uint64_t)D.n_src << 16 | (uint64_t)D.layout << 28 |
                        (uint64_t)(D.modes != nullptr) << 29);
+  for (const MatDesc& D : S.mats) key = mix(key, (uint64_t)D.red_lo << 8 ^ (uint64_t)D.red_log2);
   key = mix(key, (uint64_t)S.o_elems);
   key = mix(key, (uint64_t)S.mode_elems);
   key = mix(key, (uint64_t)S.tasks.size());
@@ -989,6 +1003,34 @@ tor_status tor_eval_units(tor_ctx* ctx, int n, const tor_c128* O, int ld, double
   ins[0].dev = (ctx->cfg.flags & TOR_IN_DEVICE) != 0;
   std::lock_guard<std::mutex> lk(ctx->run_mu);
   return run_blocking(ctx, ins, out, partials, partials_len);
+}
+
+long long tor_plan_leaves(tor_ctx* ctx, int n) {
+  if (!ctx || n < 1 || n > 64) return -1;
+  const int p = plan_p(ctx, n);
+  return 1ll << (p >= 5 ? p - 5 : p);
+}
+
+tor_status tor_eval_range(tor_ctx* ctx, int n, const tor_c128* O, int ld, long long leaf_lo, long long leaf_count,
+                          tor_result* out) {
+  if (!ctx || !out || n < 1 || n > 64) return TOR_EINVAL;
+  const int p = plan_p(ctx, n);
+  if (p < 5) return TOR_EINVAL;
+  const long long L = 1ll << (p - 5);
+  if (leaf_count < 1 || (leaf_count & (leaf_count - 1)) || leaf_lo < 0 || leaf_lo % leaf_count ||
+      leaf_lo + leaf_count > L)
+    return TOR_EINVAL;
+  std::vector<MatIn> ins(1);
+  ins[0].n = n;
+  ins[0].O = O;
+  ins[0].ld = ld;
+  ins[0].n_src = n;
+  ins[0].layout = ctx->cfg.layout;
+  ins[0].dev = (ctx->cfg.flags & TOR_IN_DEVICE) != 0;
+  ins[0].leaf_lo = leaf_lo;
+  ins[0].leaf_count = leaf_count;
+  std::lock_guard<std::mutex> lk(ctx->run_mu);
+  return run_blocking(ctx, ins, out, nullptr, 0);
 }
 
 tor_status tor_submit(tor_ctx* ctx, int n, const tor_c128* O, int ld, uint64_t* ticket) {

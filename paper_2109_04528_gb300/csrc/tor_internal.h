@@ -21,6 +21,7 @@ struct MatDesc {
   int n, p, ld, layout;
   int n_src;            // modes of the source matrix (n unless `modes` selects a submatrix)
   int pad;
+  long long red_lo;     // first reduction leaf this job evaluates (tor_eval_range); 0 otherwise
 };
 
 // One warp task.  p >= 5: 32 units of matrix `mat` sharing the decisions on

@@ -250,7 +250,7 @@ __device__ __forceinline__ void write_task_partial(const UnitsParams& prm, const
       a = a + a2;
     }
   }
-  if (lane == 0) prm.red_leaves[D.red_off + sub] = Part{h, l, a, 0.0};
+  if (lane == 0) prm.red_leaves[D.red_off + (sub - D.red_lo)] = Part{h, l, a, 0.0};
 }
 
 // p >= 5: the warp builds the task node (depth p - 5) cooperatively, fans it

@@ -105,6 +105,7 @@ __global__ void k_noalloc_setup(const double2* O, int n, int ld, int layout) {
     D->B = (double2*)(base + OFF_B);
     D->part_off = 0;
     D->red_off = 0;
+    D->red_lo = 0;
     D->red_log2 = p >= 5 ? p - 5 : p;
     D->n = n;
     D->p = p;

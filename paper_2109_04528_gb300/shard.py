@@ -1,0 +1,62 @@
+"""Sharding one Torontonian across processes (one per GPU).
+
+The final reduction of tor_eval is a fixed binary tree over the matrix's
+reduction leaves (its warp tasks).  A shard evaluates an aligned power-of-two
+range of leaves with tor_eval_range; merging the shards' partial sums with the
+same tree and the same double-double addition reproduces the single-GPU
+result bitwise.  The exchange is one gather of three doubles per rank.
+"""
+from __future__ import annotations
+
+
+def shard_range(n_leaves: int, world: int, rank: int):
+    """(leaf_lo, leaf_count) of `rank` among `world` ranks (world a power of two <= n_leaves)."""
+    if world < 1 or world & (world - 1) or world > n_leaves or not 0 <= rank < world:
+        raise ValueError("world must be a power of two no larger than the number of leaves")
+    count = n_leaves // world
+    return rank * count, count
+
+
+def two_sum(a: float, b: float):
+    s = a + b
+    bb = s - a
+    return s, (a - (s - bb)) + (b - bb)
+
+
+def dd_add(x, y):
+    """(hi, lo, abs) + (hi, lo, abs): TwoSum of the highs, lows folded in, FastTwoSum."""
+    s, e = two_sum(x[0], y[0])
+    e = e + (x[1] + y[1])
+    h = s + e
+    return (h, e - (h - s), x[2] + y[2])
+
+
+def tree_merge(parts):
+    """Binary-tree sum of a power-of-two list of (hi, lo, abs), left operand first."""
+    parts = list(parts)
+    if not parts or len(parts) & (len(parts) - 1):
+        raise ValueError("need a power-of-two number of parts")
+    while len(parts) > 1:
+        parts = [dd_add(parts[i], parts[i + 1]) for i in range(0, len(parts), 2)]
+    return parts[0]
+
+
+def gather_merge(partial, group=None):
+    """All-gather each rank's (hi, lo, abs) (torch.distributed) and merge in rank order."""
+    import torch.distributed as dist
+    world = dist.get_world_size(group)
+    got = [None] * world
+    dist.all_gather_object(got, tuple(float(v) for v in partial), group=group)
+    return tree_merge(got)
+
+
+def distributed_tor(ctx, O, group=None):
+    """Tor of one matrix with its leaves split over the ranks of `group`; every rank
+    gets the merged (hi, lo, abs)."""
+    import torch.distributed as dist
+
+    from . import binding
+    n = O.shape[0] // 2
+    lo, count = shard_range(binding.tor_plan_leaves(ctx, n), dist.get_world_size(group), dist.get_rank(group))
+    r = binding.tor_eval_range(ctx, O, lo, count)
+    return gather_merge((r.hi, r.lo, r.abs_sum), group)

@@ -1,0 +1,75 @@
+"""Sharding of one Torontonian across ranks (host logic, gloo, world_size 2, CPU).
+
+Each rank computes its leaves' partial sums -- on CPU the leaves are warp
+tasks of 32 prefix units whose sums come from the oracle -- and the ranks
+merge them through torch.distributed.  The merged result must equal the
+single-process tree bitwise and the full oracle sum to binary128 accuracy.
+"""
+import os
+
+import numpy as np
+import pytest
+
+from paper_2109_04528_gb300 import inputs, shard
+
+N, P = 9, 6  # 2^(P-5) = 2 leaves (warp tasks), each 32 units of 2^(N-P) subsets
+
+
+def task_partial(oracle_mod, O, t):
+    # lane l of task t takes unit u = t | (l << (P-5)); lanes merge by the same binary tree
+    units = []
+    for lane in range(32):
+        r = oracle_mod.tor_unit(O, P, t | (lane << (P - 5)), threads=1)
+        units.append((r.hi, r.lo, r.abs_sum))
+    return shard.tree_merge(units)
+
+
+def _rank_main(rank, world, port, out_dir):
+    import torch.distributed as dist
+
+    import oracle
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    O = inputs.lossy_squeezed(N, 1234, (0.5, 1.2), 0.4).O
+    lo, count = shard.shard_range(1 << (P - 5), world, rank)
+    mine = shard.tree_merge([task_partial(oracle, O, t) for t in range(lo, lo + count)])
+    merged = shard.gather_merge(mine)
+    np.save(os.path.join(out_dir, f"r{rank}.npy"), np.array(merged))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_tree_merge_is_binary_and_ordered():
+    parts = [(float(i), 0.0, 1.0) for i in range(8)]
+    assert shard.tree_merge(parts) == (28.0, 0.0, 8.0)
+    with pytest.raises(ValueError):
+        shard.tree_merge(parts[:3])
+    assert shard.shard_range(16, 4, 3) == (12, 4)
+    with pytest.raises(ValueError):
+        shard.shard_range(4, 3, 0)
+
+
+def test_dd_add_is_error_free_on_cancelling_terms():
+    a = (1.0, 1e-17, 1.0)
+    b = (-1.0, 2e-17, 1.0)
+    h, lo, ab = shard.dd_add(a, b)
+    assert h == 3e-17 and lo == 0.0 and ab == 2.0
+
+
+def test_two_ranks_gloo_match_single_process(oracle_mod, tmp_path):
+    import socket
+
+    import torch.multiprocessing as mp
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    port = s.getsockname()[1]
+    s.close()
+    mp.start_processes(_rank_main, args=(2, port, str(tmp_path)), nprocs=2, join=True, start_method="spawn")
+    r0 = tuple(np.load(tmp_path / "r0.npy"))
+    r1 = tuple(np.load(tmp_path / "r1.npy"))
+    assert r0 == r1
+    O = inputs.lossy_squeezed(N, 1234, (0.5, 1.2), 0.4).O
+    single = shard.tree_merge([task_partial(oracle_mod, O, t) for t in range(1 << (P - 5))])
+    assert r0 == tuple(single)
+    full = oracle_mod.tor_brute(O)
+    assert abs((r0[0] - full.hi) + (r0[1] - full.lo)) <= 1e-25 * full.abs_sum
