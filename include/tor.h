@@ -116,10 +116,15 @@ tor_status tor_eval(tor_ctx* ctx, int n, const tor_c128* O, int ld, tor_result* 
 tor_status tor_eval_batch(tor_ctx* ctx, int count, const int* n, const tor_c128* const* O,
                           const int* ld, tor_result* out);
 
-/* Queues one matrix for evaluation and returns at once with a ticket.  Queued
- * and running requests are batched by the context's serving loop; a request
- * that arrives while others run is admitted as device memory frees up.
- * TOR_EAGAIN if the queue is full. */
+/* Queues one matrix for evaluation and returns at once with a ticket.  The
+ * context's serving thread batches queued requests continuously: a request
+ * that arrives while others run is admitted as soon as a slot and the device
+ * memory budget allow.  Large requests (more than 2^25 subset terms) run one
+ * at a time in a low-priority lane whose persistent kernel yields the SMs
+ * every ~5 ms; small requests are batched FIFO into high-priority lanes and
+ * may pass a large request that waits.  Each result is bitwise the same as
+ * tor_eval of the same matrix on the same context.  TOR_EAGAIN if the queue
+ * is full. */
 tor_status tor_submit(tor_ctx* ctx, int n, const tor_c128* O, int ld, uint64_t* ticket);
 
 /* Waits up to timeout_s (0 = do not wait, < 0 = forever) for a ticket.

@@ -135,6 +135,11 @@ struct Slot {
   int cancel_epoch = 0;
   bool busy = false;
   bool graphed = false;  // the last pass was a graph replay
+  // serving state
+  cudaEvent_t units_done = nullptr;  // end of a time slice of k_units
+  int phase = 0;                     // 0 idle, 1 k_units slice in flight, 2 reduce and copies in flight
+  bool large = false;                // runs one large request, time-sliced, low priority
+  double t_start = 0;
 
   void release() {
     for (DevBuf* b : {&d_O, &d_B, &d_mats, &d_tasks, &d_partials, &d_flags, &d_results, &d_lane, &d_warp, &d_ctl,
@@ -146,6 +151,7 @@ struct Slot {
     for (int i = 0; i < 5; ++i)
       if (ev[i]) cudaEventDestroy(ev[i]);
     if (done) cudaEventDestroy(done);
+    if (units_done) cudaEventDestroy(units_done);
     if (own_stream && stream) cudaStreamDestroy(stream);
     stream = nullptr;
   }
@@ -194,7 +200,7 @@ struct tor_ctx {
   std::thread server;
   bool server_started = false, stopping = false;
   size_t queue_limit = 1 << 20;
-  int n_serve_slots = 2;
+  int n_serve_slots = 3;  // one large lane + two small lanes
   int max_batch = 4096;
   double max_batch_terms = 268435456.0;  // ~45 ms of GPU work per served batch (2^28 subset terms)
   std::vector<std::unique_ptr<Slot>> serve;
@@ -240,17 +246,22 @@ static int plan_p(tor_ctx* ctx, int n) {
   return std::max(0, std::min(p, n - 1));
 }
 
-static cudaError_t slot_init(Slot& s, cudaStream_t stream) {
+// priority: 0 = default; < 0 = the device's highest; > 0 = its lowest
+static cudaError_t slot_init(Slot& s, cudaStream_t stream, int priority = 0) {
   cudaError_t e;
   if (stream) {
     s.stream = stream;
     s.own_stream = false;
   } else {
-    if ((e = cudaStreamCreateWithFlags(&s.stream, cudaStreamNonBlocking)) != cudaSuccess) return e;
+    int lo = 0, hi = 0;
+    cudaDeviceGetStreamPriorityRange(&lo, &hi);  // numerically lower = higher priority
+    const int prio = priority < 0 ? hi : priority > 0 ? lo : 0;
+    if ((e = cudaStreamCreateWithPriority(&s.stream, cudaStreamNonBlocking, prio)) != cudaSuccess) return e;
     s.own_stream = true;
   }
   for (int i = 0; i < 5; ++i)
     if ((e = cudaEventCreate(&s.ev[i])) != cudaSuccess) return e;
+  if ((e = cudaEventCreateWithFlags(&s.units_done, cudaEventDisableTiming)) != cudaSuccess) return e;
   return cudaEventCreateWithFlags(&s.done, cudaEventDisableTiming);
 }
 
@@ -428,9 +439,10 @@ static uint64_t mix(uint64_t h, uint64_t v) {
   return h;
 }
 
-// The stream operations of one pass (what a graph captures; the timing
-// events stay outside graphs).
-static tor_status slot_record(tor_ctx* ctx, Slot& S, bool timed) {
+// The stream operations of one pass, in three phases: front (inputs,
+// descriptors, k_intake), units (k_units, possibly one time slice of it),
+// back (k_reduce, results).  The timing events stay outside graphs.
+static tor_status rec_front(tor_ctx* ctx, Slot& S, bool timed) {
   cudaStream_t s = S.stream;
   const int J = S.J;
   if (timed) CK(cudaEventRecord(S.ev[0], s), "event");
@@ -445,6 +457,12 @@ static tor_status slot_record(tor_ctx* ctx, Slot& S, bool timed) {
   const bool check = !(ctx->cfg.flags & TOR_NO_CHECK);
   CK(launch_intake((const MatDesc*)S.d_mats.p, J, check ? 1 : 0, (int*)S.d_flags.p, s), "k_intake");
   if (timed) CK(cudaEventRecord(S.ev[2], s), "event");
+  return TOR_OK;
+}
+
+// One launch of k_units; with slice_ns > 0 it stops taking tasks after that
+// long and copies (ticket, abort word) to h_ctl so the host can relaunch it.
+static tor_status rec_units(tor_ctx* ctx, Slot& S, long long slice_ns) {
   UnitsParams prm;
   prm.mats = (const MatDesc*)S.d_mats.p;
   prm.tasks = (const TaskDesc*)S.d_tasks.p;
@@ -461,7 +479,18 @@ static tor_status slot_record(tor_ctx* ctx, Slot& S, bool timed) {
   prm.cancel = ctx->d_cancel;
   prm.cancel_epoch = S.cancel_epoch;
   prm.budget_ns = ctx->cfg.timeout_s > 0 ? (long long)(ctx->cfg.timeout_s * 1e9) : 0;
-  CK(launch_units(prm, ctx->grid, s), "k_units");
+  prm.slice_ns = slice_ns;
+  CK(launch_units(prm, ctx->grid, S.stream), "k_units");
+  if (slice_ns > 0) {
+    CK(cudaMemcpyAsync(S.h_ctl.p, S.d_ctl.p, 2 * sizeof(int), cudaMemcpyDeviceToHost, S.stream), "D2H ticket");
+    CK(cudaEventRecord(S.units_done, S.stream), "event");
+  }
+  return TOR_OK;
+}
+
+static tor_status rec_back(tor_ctx* ctx, Slot& S, bool timed) {
+  cudaStream_t s = S.stream;
+  const int J = S.J;
   if (timed) CK(cudaEventRecord(S.ev[3], s), "event");
   CK(launch_reduce((const MatDesc*)S.d_mats.p, J, (const Part*)S.d_partials.p + S.parts, (const int*)S.d_flags.p,
                    (ResultRec*)S.d_results.p, s),
@@ -472,8 +501,15 @@ static tor_status slot_record(tor_ctx* ctx, Slot& S, bool timed) {
     CK(cudaMemcpyAsync((char*)S.h_results.p + J * sizeof(ResultRec), S.d_partials.p, S.parts * 32,
                        cudaMemcpyDeviceToHost, s),
        "D2H partials");
-  CK(cudaMemcpyAsync(S.h_ctl.p, (int*)S.d_ctl.p + 1, sizeof(int), cudaMemcpyDeviceToHost, s), "D2H abort");
+  CK(cudaMemcpyAsync(S.h_ctl.p, S.d_ctl.p, 2 * sizeof(int), cudaMemcpyDeviceToHost, s), "D2H control");
   return TOR_OK;
+}
+
+static tor_status slot_record(tor_ctx* ctx, Slot& S, bool timed) {
+  tor_status st = rec_front(ctx, S, timed);
+  if (st == TOR_OK) st = rec_units(ctx, S, 0);
+  if (st == TOR_OK) st = rec_back(ctx, S, timed);
+  return st;
 }
 
 // Enqueues the prepared job (graph replay when enabled and the shape repeats).
@@ -537,7 +573,7 @@ static tor_status slot_launch(tor_ctx* ctx, Slot& S) {
 static tor_status slot_finish(Slot& S, tor_result* out, double* unit_partials, double* times) {
   tor_status first = TOR_OK;
   const ResultRec* hr = (const ResultRec*)S.h_results.p;
-  const int abort_word = *(const int*)S.h_ctl.p;
+  const int abort_word = ((const int*)S.h_ctl.p)[1];
   for (int j = 0; j < S.J; ++j) {
     tor_result& r = out[S.act[j]];
     const ResultRec& q = hr[j];
@@ -605,27 +641,75 @@ static void complete(tor_ctx* ctx, std::vector<Request*>& reqs) {  // caller hol
   ctx->done_cv.notify_all();
 }
 
+// Work of one request in subset terms (2^n).
+static double request_terms(const Request* r) { return std::ldexp(1.0, std::max(0, std::min(r->in.n, 64))); }
+
+// Serving slots: serve[0] is the large lane (one large request at a time, low
+// stream priority, k_units in time slices), the others are small lanes (FIFO
+// batches of small requests, high priority).  A slice boundary lets the
+// pending blocks of a high-priority small batch take the SMs; the large
+// request continues from its task ticket right after, so it is never
+// restarted and its result does not depend on the interruption.
 static void server_loop(tor_ctx* ctx) {
   cudaSetDevice(ctx->cfg.device);
   struct InFlight {
     std::vector<Request*> reqs;
     std::vector<tor_result> res;
+    bool failed = false;
   };
   std::vector<InFlight> fl(ctx->serve.size());
   size_t reserved = 0;
+  const long long slice_ns = 5000000;  // 5 ms
+  auto fail_slot = [&](size_t i, tor_status st) {
+    Slot& S = *ctx->serve[i];
+    for (int a : S.act) fl[i].res[a].status = st;
+    fl[i].failed = true;
+  };
   for (;;) {
     bool progressed = false;
-    // 1. completions
+    // 1. advance slots in flight
     for (size_t i = 0; i < ctx->serve.size(); ++i) {
       Slot& S = *ctx->serve[i];
       if (!S.busy) continue;
-      const cudaError_t q = cudaEventQuery(S.done);
-      if (q == cudaErrorNotReady) continue;
-      if (q == cudaSuccess) {
-        slot_finish(S, fl[i].res.data(), nullptr, nullptr);
-      } else {
-        cudaGetLastError();
-        for (int a : S.act) fl[i].res[a].status = TOR_ECUDA;
+      if (S.phase == 1) {  // a k_units slice has ended?
+        const cudaError_t q = cudaEventQuery(S.units_done);
+        if (q == cudaErrorNotReady) continue;
+        tor_status st = TOR_OK;
+        if (q != cudaSuccess) {
+          cudaGetLastError();
+          st = TOR_ECUDA;
+        } else {
+          const unsigned ticket = ((const unsigned*)S.h_ctl.p)[0];
+          const int abort_word = ((const int*)S.h_ctl.p)[1];
+          const bool timed_out = ctx->cfg.timeout_s > 0 && now_s() - S.t_start > ctx->cfg.timeout_s;
+          if (ticket < S.tasks.size() && !abort_word && !timed_out) {
+            st = rec_units(ctx, S, slice_ns);  // continue from the ticket
+            if (st == TOR_OK) {
+              progressed = true;
+              continue;
+            }
+          } else if (timed_out && ticket < S.tasks.size()) {
+            int* w = (int*)S.h_ctl.p + 8;  // pinned; the results of this job become TOR_ETIMEOUT
+            *w = ABORT_TIMEOUT;
+            cudaMemcpyAsync((int*)S.d_ctl.p + 1, w, sizeof(int), cudaMemcpyHostToDevice, S.stream);
+          }
+        }
+        if (st == TOR_OK) st = rec_back(ctx, S, false);
+        if (st == TOR_OK && cudaEventRecord(S.done, S.stream) != cudaSuccess) st = TOR_ECUDA;
+        if (st != TOR_OK) fail_slot(i, st);
+        S.phase = 2;
+        progressed = true;
+        if (st == TOR_OK) continue;
+      }
+      // phase 2: reduce and copies
+      if (!fl[i].failed) {
+        const cudaError_t q = cudaEventQuery(S.done);
+        if (q == cudaErrorNotReady) continue;
+        if (q == cudaSuccess) slot_finish(S, fl[i].res.data(), nullptr, nullptr);
+        else {
+          cudaGetLastError();
+          fail_slot(i, TOR_ECUDA);
+        }
       }
       {
         std::lock_guard<std::mutex> lk(ctx->q_mu);
@@ -636,35 +720,37 @@ static void server_loop(tor_ctx* ctx) {
       ctx->batches += 1;
       reserved -= S.bytes;
       S.busy = false;
-      fl[i].reqs.clear();
-      fl[i].res.clear();
+      S.phase = 0;
+      fl[i] = InFlight();
       progressed = true;
     }
-    // 2. admission into free slots
+    // 2. admission: large requests FIFO into the large lane, small requests
+    //    FIFO into the small lanes (they may pass a large request that waits)
     for (size_t i = 0; i < ctx->serve.size(); ++i) {
       Slot& S = *ctx->serve[i];
       if (S.busy) continue;
+      const bool large_lane = (i == 0);
+      const double big = ctx->max_batch_terms / 8;
       std::vector<Request*> batch;
       {
         std::lock_guard<std::mutex> lk(ctx->q_mu);
-        // FIFO; a large request (over 1/8 of the batch cap) runs as a batch of its own,
-        // so small requests never wait for a large one to finish
         double terms = 0;
-        bool large = false;
-        while (!ctx->queue.empty() && (int)batch.size() < ctx->max_batch) {
-          const int n = ctx->queue.front()->in.n;
-          const double t = std::ldexp(1.0, std::max(0, std::min(n, 64)));
-          const bool big = t > ctx->max_batch_terms / 8;
-          if (!batch.empty() && (large || big || terms + t > ctx->max_batch_terms)) break;
-          large = big;
+        for (auto it = ctx->queue.begin(); it != ctx->queue.end() && (int)batch.size() < ctx->max_batch;) {
+          Request* r = *it;
+          const double t = request_terms(r);
+          const bool is_big = t > big;
+          if (is_big != large_lane) {
+            ++it;
+            continue;
+          }
+          if (!batch.empty() && (large_lane || terms + t > ctx->max_batch_terms)) break;
           terms += t;
-          Request* r = ctx->queue.front();
-          ctx->queue.pop_front();
           if (r->sess) ++r->sess->inflight;  // the session's matrices stay alive until complete()
           batch.push_back(r);
+          it = ctx->queue.erase(it);
         }
       }
-      if (batch.empty()) break;
+      if (batch.empty()) continue;
       std::vector<MatIn> ins;
       for (Request* r : batch) ins.push_back(r->in);
       // device-memory budget: shrink the batch until it fits beside the jobs in flight
@@ -689,13 +775,23 @@ static void server_loop(tor_ctx* ctx) {
             if (batch[0]->sess) --batch[0]->sess->inflight;
             ctx->queue.push_front(batch[0]);
           }
-          break;
+          continue;
         }
       }
       std::vector<tor_result> res(ins.size());
       bool any = false;
       tor_status st = slot_prepare(ctx, S, ins, res.data(), false, &any);
-      if (any) st = slot_launch(ctx, S);
+      if (any) {
+        S.cancel_epoch = __atomic_load_n(ctx->h_cancel, __ATOMIC_SEQ_CST);
+        S.graphed = false;
+        S.t_start = now_s();
+        st = rec_front(ctx, S, false);
+        if (st == TOR_OK) st = rec_units(ctx, S, large_lane ? slice_ns : 0);
+        if (st == TOR_OK && !large_lane) {
+          st = rec_back(ctx, S, false);
+          if (st == TOR_OK && cudaEventRecord(S.done, S.stream) != cudaSuccess) st = TOR_ECUDA;
+        }
+      }
       if (!any || st == TOR_ECUDA || st == TOR_ENOMEM) {
         // nothing to run, or the launch failed: complete now
         std::lock_guard<std::mutex> lk(ctx->q_mu);
@@ -707,6 +803,8 @@ static void server_loop(tor_ctx* ctx) {
         continue;
       }
       S.busy = true;
+      S.large = large_lane;
+      S.phase = large_lane ? 1 : 2;
       reserved += S.bytes;
       fl[i].reqs = std::move(batch);
       fl[i].res = std::move(res);
@@ -714,7 +812,7 @@ static void server_loop(tor_ctx* ctx) {
     }
     // 3. idle / stop
     bool busy = false;
-    for (auto& s : ctx->serve) busy |= s->busy;
+    for (auto& sl : ctx->serve) busy |= sl->busy;
     std::unique_lock<std::mutex> lk(ctx->q_mu);
     if (ctx->stopping && !busy && ctx->queue.empty()) return;
     if (!progressed) {
@@ -729,7 +827,7 @@ static tor_status start_server(tor_ctx* ctx) {  // caller holds q_mu
   cudaSetDevice(ctx->cfg.device);
   for (int i = 0; i < ctx->n_serve_slots; ++i) {
     std::unique_ptr<Slot> s(new Slot());
-    cudaError_t e = slot_init(*s, nullptr);
+    cudaError_t e = slot_init(*s, nullptr, i == 0 ? 1 : -1);  // large lane low priority, small lanes high
     if (e != cudaSuccess) {
       s->release();
       return cuda_fail(ctx, e, "serving slot");

@@ -50,6 +50,8 @@ struct UnitsParams {
   const volatile int* cancel;  // host-mapped cancel counter
   int cancel_epoch;            // its value when the job started; a change = stop
   long long budget_ns;         // 0 = no time limit
+  long long slice_ns;          // > 0: warps stop taking tasks after this long (no abort); the host
+                               // relaunches the kernel, which continues from the ticket
   int* abort_word;             // ABORT_* bits set by the kernel
 };
 

@@ -366,10 +366,12 @@ __global__ void __launch_bounds__(kUnitsThreads, 2) k_units(const UnitsParams pr
     unsigned t = 0xffffffffu;
     if (lane == 0) {
       int ab = 0;
+      const long long el = (long long)(global_ns() - t0);
       if (*prm.cancel != prm.cancel_epoch) ab = ABORT_CANCEL;
-      else if (prm.budget_ns > 0 && (long long)(global_ns() - t0) > prm.budget_ns) ab = ABORT_TIMEOUT;
+      else if (prm.budget_ns > 0 && el > prm.budget_ns) ab = ABORT_TIMEOUT;
       if (ab) atomicOr(prm.abort_word, ab);
-      else if (*(volatile int*)prm.abort_word == 0) t = atomicAdd(prm.ticket, 1u);
+      else if (*(volatile int*)prm.abort_word == 0 && !(prm.slice_ns > 0 && el > prm.slice_ns))
+        t = atomicAdd(prm.ticket, 1u);
     }
     t = __shfl_sync(0xffffffffu, t, 0);
     if (t >= (unsigned)prm.ntasks) break;

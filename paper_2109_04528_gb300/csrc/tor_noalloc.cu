@@ -185,6 +185,7 @@ extern "C" tor_status tor_eval_noalloc(int device, int n, const tor_c128* O, int
       prm.cancel = (const volatile int*)(base + OFF_CTL) + 2;
       prm.cancel_epoch = 0;
       prm.budget_ns = 0;
+      prm.slice_ns = 0;
       prm.partials = (Part*)(base + OFF_PARTS);
       prm.red_leaves = (Part*)(base + OFF_REDS);
       prm.mat_flags = (int*)(base + OFF_FLAGS);

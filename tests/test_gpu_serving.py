@@ -203,3 +203,23 @@ def test_session_destroyed_while_requests_run():
         # a session may also outlive its context
         sess2 = binding.Session(c, inst.sigma)
     sess2.close()
+
+
+def test_small_requests_pass_a_large_one(ctx):
+    # a large request (2^30 terms, time-sliced in the low-priority lane) and small
+    # ones submitted after it: the small ones finish first, every result is
+    # bitwise the tor_eval result
+    big = inputs.config_single(30).O
+    small = [inputs.lossy_squeezed(k, 70 + k, (0.5, 1.2), 0.4).O for k in range(6, 16)]
+    ref_big = binding.tor_eval(ctx, big)
+    ref_small = [binding.tor_eval(ctx, O) for O in small]
+    tb = binding.tor_submit(ctx, big)
+    time.sleep(0.02)
+    ts = [binding.tor_submit(ctx, O) for O in small]
+    for t, ref in zip(ts, ref_small):
+        st, r = binding.tor_poll(ctx, t, 60.0)
+        assert st == 0 and same(r, ref)
+    st, _ = binding.tor_poll(ctx, tb, 0.0)
+    assert st == binding.TOR_EAGAIN  # the large one is still running
+    st, r = binding.tor_poll(ctx, tb, 60.0)
+    assert st == 0 and same(r, ref_big)
