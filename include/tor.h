@@ -64,8 +64,15 @@ enum { TOR_LAYOUT_BLOCK = 0, TOR_LAYOUT_PAIRS = 1 };
  *   TOR_IN_DEVICE  O pointers of tor_eval* are device pointers (e.g. torch CUDA tensors)
  *   TOR_NO_CHECK   skip the Hermitian / finiteness check of the input
  *   TOR_GRAPHS     capture each evaluation pass into a CUDA graph and replay it for
- *                  later calls of the same shape (same sizes in the same order) */
-enum { TOR_IN_DEVICE = 1u, TOR_NO_CHECK = 2u, TOR_GRAPHS = 4u };
+ *                  later calls of the same shape (same sizes in the same order)
+ *   TOR_COMPLEX_PATH  evaluate every matrix in complex arithmetic.  By default a
+ *                  matrix of the form [[P, Q], [conj(Q), conj(P)]] in block layout
+ *                  (within 1e-12 max|O|; every physical Gaussian state has it) is
+ *                  evaluated in real arithmetic on V = U^H (I - O) U, U the per-mode
+ *                  map from (a, a^dag) to the quadratures (x, p): every principal
+ *                  block of V has the determinant of the matching block of I - O,
+ *                  and the update costs a quarter of the complex multiply-adds. */
+enum { TOR_IN_DEVICE = 1u, TOR_NO_CHECK = 2u, TOR_GRAPHS = 4u, TOR_COMPLEX_PATH = 8u };
 
 /* tor_session_create kinds */
 enum { TOR_SESSION_SIGMA = 0, TOR_SESSION_O = 1 };

@@ -14,10 +14,20 @@
 // (all n modes decided, included set Z) contributes (-1)^{n-|Z|} phi_Z
 // (Eq. tor).
 //
-// Storage of a Hermitian matrix: packed lower triangle, element (r, s), r >= s,
-// at index P(r, s) = r (r + 1) / 2 + s, complex128 (double2).  Diagonal
-// entries are real (imaginary part 0).  A node is a "view": a buffer plus a
-// row offset o; its element (i, k) lives at P(i + o, k + o).
+// Two scalar types run the same tree:
+//   Cplx  complex128 entries: any Hermitian O with I - O positive definite.
+//   Real  float64 entries: O of a physical Gaussian state, which has the form
+//         [[P, Q], [conj(Q), conj(P)]] in block layout.  The per-mode unitary
+//         U = (1/sqrt 2) [[1, i], [1, -i]] from (a, a^dag) to the quadratures
+//         (x, p) maps such a B to the real symmetric V = U^H B U, and every
+//         principal block of V has the determinant of the matching block of B
+//         (|det U| = 1), so the whole tree can run in real arithmetic at a
+//         quarter of the multiply-adds.
+//
+// Storage of a symmetric / Hermitian matrix: packed lower triangle, element
+// (r, s), r >= s, at index P(r, s) = r (r + 1) / 2 + s.  Diagonal entries are
+// real (complex: imaginary part 0).  A node is a "view": a buffer plus a row
+// offset o; its element (i, k) lives at P(i + o, k + o).
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -94,6 +104,66 @@ __device__ __forceinline__ void dd_add(double ah, double al, double bh, double b
 }
 
 // ---------------------------------------------------------------------------
+// Scalar types.  Each provides the operations of the include step:
+//   abs2(b)              |b|^2
+//   cl(b, ia)            conj(l) = conj(b) / a          (l = b / a)
+//   reduce_col(x, y, cl) y' = y - x conj(l)
+//   scale(v, s)          v s
+//   rank2_off(s, xt, xk, yt, yk)   s - xt conj(xk) - yt conj(yk)
+//   rank2_diag(d, xt, x, yt, y)    d - Re(xt conj(x)) - Re(yt conj(y))
+//   re(v), diag(d)       real part; the stored form of a real diagonal entry
+// ---------------------------------------------------------------------------
+struct Cplx {
+  using T = double2;
+  static __device__ __forceinline__ double re(T v) { return v.x; }
+  static __device__ __forceinline__ T diag(double d) { return make_double2(d, 0.0); }
+  static __device__ __forceinline__ double abs2(T b) { return fma(b.x, b.x, b.y * b.y); }
+  static __device__ __forceinline__ T cl(T b, double ia) { return make_double2(b.x * ia, -b.y * ia); }
+  static __device__ __forceinline__ T reduce_col(T x, T y, T c) {
+    T r;
+    r.x = fma(-x.x, c.x, y.x);
+    r.x = fma(x.y, c.y, r.x);
+    r.y = fma(-x.x, c.y, y.y);
+    r.y = fma(-x.y, c.x, r.y);
+    return r;
+  }
+  static __device__ __forceinline__ T scale(T v, double s) { return make_double2(v.x * s, v.y * s); }
+  static __device__ __forceinline__ T rank2_off(T s, T xt, T xk, T yt, T yk) {  // 8 DFMA
+    s.x = fma(-xt.x, xk.x, s.x);
+    s.x = fma(-xt.y, xk.y, s.x);
+    s.x = fma(-yt.x, yk.x, s.x);
+    s.x = fma(-yt.y, yk.y, s.x);
+    s.y = fma(-xt.y, xk.x, s.y);
+    s.y = fma(xt.x, xk.y, s.y);
+    s.y = fma(-yt.y, yk.x, s.y);
+    s.y = fma(yt.x, yk.y, s.y);
+    return s;
+  }
+  static __device__ __forceinline__ double rank2_diag(double d, T xt, T x, T yt, T y) {  // 4 DFMA
+    d = fma(-xt.x, x.x, d);
+    d = fma(-xt.y, x.y, d);
+    d = fma(-yt.x, y.x, d);
+    d = fma(-yt.y, y.y, d);
+    return d;
+  }
+};
+struct Real {
+  using T = double;
+  static __device__ __forceinline__ double re(T v) { return v; }
+  static __device__ __forceinline__ T diag(double d) { return d; }
+  static __device__ __forceinline__ double abs2(T b) { return b * b; }
+  static __device__ __forceinline__ T cl(T b, double ia) { return b * ia; }
+  static __device__ __forceinline__ T reduce_col(T x, T y, T c) { return fma(-x, c, y); }
+  static __device__ __forceinline__ T scale(T v, double s) { return v * s; }
+  static __device__ __forceinline__ T rank2_off(T s, T xt, T xk, T yt, T yk) {  // 2 DFMA
+    return fma(-yt, yk, fma(-xt, xk, s));
+  }
+  static __device__ __forceinline__ double rank2_diag(double d, T xt, T x, T yt, T y) {
+    return fma(-yt, y, fma(-xt, x, d));
+  }
+};
+
+// ---------------------------------------------------------------------------
 // The 2x2 pivot of an include step (Algorithm 1 on mode j's two rows).
 // Pivot block [[a, conj(b)], [b, e]], a = S(0,0), b = S(1,0), e = S(1,1).
 // LDL^H: d1 = a, l = b / a, d2 = e - |b|^2 / a.  With x = S(:,0), y = S(:,1)
@@ -101,72 +171,42 @@ __device__ __forceinline__ void dd_add(double ah, double al, double bh, double b
 //   S' = S_22 - x x^H / d1 - y' y'^H / d2,   y' = y - x conj(l),
 // and the determinant factor of the step is rho = (d1 d2)^{-1/2}.
 // ---------------------------------------------------------------------------
+template <class S>
 struct Pivot {
-  double ia;   // 1 / d1
-  double id2;  // 1 / d2 = a rho^2
-  double rho;  // (a e - |b|^2)^{-1/2}
-  double2 cl;  // conj(l) = conj(b) / a
-  bool ok;     // d1 > 0 and d1 d2 > 0: the block is positive definite
+  double ia;         // 1 / d1
+  double id2;        // 1 / d2 = a rho^2
+  double rho;        // (a e - |b|^2)^{-1/2}
+  typename S::T cl;  // conj(l) = conj(b) / a
+  bool ok;           // d1 > 0 and d1 d2 > 0: the block is positive definite
 };
-__device__ __forceinline__ Pivot make_pivot(double a, double2 b, double e) {
-  Pivot P;
-  double bb = fma(b.x, b.x, b.y * b.y);
-  double det2 = fma(a, e, -bb);
-  P.ok = (a > 0.0) && (det2 > 0.0);
-  P.rho = rsqrt64(det2);
-  P.ia = rcp64(a);
-  P.cl = make_double2(b.x * P.ia, -b.y * P.ia);
-  P.id2 = a * (P.rho * P.rho);
-  return P;
+template <class S>
+__device__ __forceinline__ Pivot<S> make_pivot(double a, typename S::T b, double e) {
+  Pivot<S> pv;
+  const double det2 = fma(a, e, -S::abs2(b));
+  pv.ok = (a > 0.0) && (det2 > 0.0);
+  pv.rho = rsqrt64(det2);
+  pv.ia = rcp64(a);
+  pv.cl = S::cl(b, pv.ia);
+  pv.id2 = a * (pv.rho * pv.rho);
+  return pv;
 }
-
-// y' = y - x * cl
-__device__ __forceinline__ double2 reduce_col(double2 x, double2 y, double2 cl) {
-  double2 r;
-  r.x = fma(-x.x, cl.x, y.x);
-  r.x = fma(x.y, cl.y, r.x);
-  r.y = fma(-x.x, cl.y, y.y);
-  r.y = fma(-x.y, cl.x, r.y);
-  return r;
-}
-// s - xt conj(xk) - yt conj(yk)   (8 DFMA)
-__device__ __forceinline__ double2 rank2_off(double2 s, double2 xt, double2 xk, double2 yt, double2 yk) {
-  s.x = fma(-xt.x, xk.x, s.x);
-  s.x = fma(-xt.y, xk.y, s.x);
-  s.x = fma(-yt.x, yk.x, s.x);
-  s.x = fma(-yt.y, yk.y, s.x);
-  s.y = fma(-xt.y, xk.x, s.y);
-  s.y = fma(xt.x, xk.y, s.y);
-  s.y = fma(-yt.y, yk.x, s.y);
-  s.y = fma(yt.x, yk.y, s.y);
-  return s;
-}
-// d - Re(xt conj(x)) - Re(yt conj(y))   (4 DFMA)
-__device__ __forceinline__ double rank2_diag(double d, double2 xt, double2 x, double2 yt, double2 y) {
-  d = fma(-xt.x, x.x, d);
-  d = fma(-xt.y, x.y, d);
-  d = fma(-yt.x, y.x, d);
-  d = fma(-yt.y, y.y, d);
-  return d;
-}
-__device__ __forceinline__ double2 cscale(double2 v, double s) { return make_double2(v.x * s, v.y * s); }
 
 // ---------------------------------------------------------------------------
-// Register-resident nodes: HM<R> is an R x R Hermitian matrix (R = 2m rows)
-// with real diagonal d[] and strictly lower entries o[TI(i,k)], i > k.
-// Everything below is fully unrolled, so the arrays live in registers.
+// Register-resident nodes: HM<S, R> is an R x R matrix (R = 2m rows) with real
+// diagonal d[] and strictly lower entries o[TI(i,k)], i > k.  Everything below
+// is fully unrolled, so the arrays live in registers.
 // ---------------------------------------------------------------------------
 __host__ __device__ constexpr int TI(int i, int k) { return (i * (i - 1)) / 2 + k; }
 
-template <int R>
+template <class S, int R>
 struct HM {
   double d[R];
-  double2 o[(R * (R - 1)) / 2];
+  typename S::T o[(R * (R - 1)) / 2];
 };
 
 // Exclude the first mode: the trailing (R-2) x (R-2) block.
-template <int R>
-__device__ __forceinline__ void hm_trail(const HM<R>& A, HM<R - 2>& C) {
+template <class S, int R>
+__device__ __forceinline__ void hm_trail(const HM<S, R>& A, HM<S, R - 2>& C) {
 #pragma unroll
   for (int i = 0; i < R - 2; ++i) {
     C.d[i] = A.d[i + 2];
@@ -176,59 +216,60 @@ __device__ __forceinline__ void hm_trail(const HM<R>& A, HM<R - 2>& C) {
 }
 
 // Include the first mode: C = Schur complement, returns rho.
-template <int R>
-__device__ __forceinline__ double hm_include(const HM<R>& A, HM<R - 2>& C, bool& bad) {
-  Pivot pv = make_pivot(A.d[0], A.o[TI(1, 0)], A.d[1]);
+template <class S, int R>
+__device__ __forceinline__ double hm_include(const HM<S, R>& A, HM<S, R - 2>& C, bool& bad) {
+  using T = typename S::T;
+  const Pivot<S> pv = make_pivot<S>(A.d[0], A.o[TI(1, 0)], A.d[1]);
   bad |= !pv.ok;
-  double2 x[R - 2], yp[R - 2];
+  T x[R - 2], yp[R - 2];
 #pragma unroll
   for (int r = 0; r < R - 2; ++r) {
     x[r] = A.o[TI(r + 2, 0)];
-    yp[r] = reduce_col(x[r], A.o[TI(r + 2, 1)], pv.cl);
+    yp[r] = S::reduce_col(x[r], A.o[TI(r + 2, 1)], pv.cl);
   }
 #pragma unroll
   for (int i = 0; i < R - 2; ++i) {
-    double2 xt = cscale(x[i], pv.ia), yt = cscale(yp[i], pv.id2);
+    const T xt = S::scale(x[i], pv.ia), yt = S::scale(yp[i], pv.id2);
 #pragma unroll
-    for (int k = 0; k < i; ++k) C.o[TI(i, k)] = rank2_off(A.o[TI(i + 2, k + 2)], xt, x[k], yt, yp[k]);
-    C.d[i] = rank2_diag(A.d[i + 2], xt, x[i], yt, yp[i]);
+    for (int k = 0; k < i; ++k) C.o[TI(i, k)] = S::rank2_off(A.o[TI(i + 2, k + 2)], xt, x[k], yt, yp[k]);
+    C.d[i] = S::rank2_diag(A.d[i + 2], xt, x[i], yt, yp[i]);
   }
   return pv.rho;
 }
 
 // One mode left (2 x 2 node): its two leaves, exclude (-phi) and include
 // (+phi rho).  v = signed sum, ab = sum of magnitudes.
-__device__ __forceinline__ void leaf_pair(double a, double2 b, double e, double phi, double& v, double& ab,
+template <class S>
+__device__ __forceinline__ void leaf_pair(double a, typename S::T b, double e, double phi, double& v, double& ab,
                                           bool& bad) {
-  double bb = fma(b.x, b.x, b.y * b.y);
-  double det2 = fma(a, e, -bb);
+  const double det2 = fma(a, e, -S::abs2(b));
   bad |= !((a > 0.0) && (det2 > 0.0));
-  double pr = phi * rsqrt64(det2);
+  const double pr = phi * rsqrt64(det2);
   v = pr - phi;
   ab = pr + phi;
 }
 
 // Sum over the 2^(R/2) leaves below a register node:
 //   v = sum (-1)^{#modes excluded below this node} phi_leaf,  ab = sum phi_leaf.
-template <int R>
+template <class S, int R>
 struct Subtree {
-  static __device__ __forceinline__ void run(const HM<R>& A, double phi, double& v, double& ab, bool& bad) {
-    HM<R - 2> E;
-    hm_trail<R>(A, E);
+  static __device__ __forceinline__ void run(const HM<S, R>& A, double phi, double& v, double& ab, bool& bad) {
+    HM<S, R - 2> E;
+    hm_trail<S, R>(A, E);
     double v1, a1;
-    Subtree<R - 2>::run(E, phi, v1, a1, bad);
-    HM<R - 2> I;
-    double rho = hm_include<R>(A, I, bad);
+    Subtree<S, R - 2>::run(E, phi, v1, a1, bad);
+    HM<S, R - 2> I;
+    const double rho = hm_include<S, R>(A, I, bad);
     double v2, a2;
-    Subtree<R - 2>::run(I, phi * rho, v2, a2, bad);
+    Subtree<S, R - 2>::run(I, phi * rho, v2, a2, bad);
     v = v2 - v1;
     ab = a1 + a2;
   }
 };
-template <>
-struct Subtree<2> {
-  static __device__ __forceinline__ void run(const HM<2>& A, double phi, double& v, double& ab, bool& bad) {
-    leaf_pair(A.d[0], A.o[0], A.d[1], phi, v, ab, bad);
+template <class S>
+struct Subtree<S, 2> {
+  static __device__ __forceinline__ void run(const HM<S, 2>& A, double phi, double& v, double& ab, bool& bad) {
+    leaf_pair<S>(A.d[0], A.o[0], A.d[1], phi, v, ab, bad);
   }
 };
 
@@ -236,66 +277,57 @@ struct Subtree<2> {
 // Lane-private memory.  Each lane of a warp owns a private stack of packed
 // matrices; the 32 lanes' copies are interleaved element by element, so when
 // all lanes touch element e of their own matrices (they run the same control
-// flow) the warp reads 32 consecutive double2 (512 contiguous bytes).
+// flow) the warp reads 32 consecutive elements.
 // ---------------------------------------------------------------------------
+template <class S>
 struct LaneMem {
-  double2* p;  // lane's element 0 (= warp region + lane)
-  __device__ __forceinline__ double2 ld(int e) const { return p[(size_t)e * kWarp]; }
-  __device__ __forceinline__ void st(int e, double2 v) const { p[(size_t)e * kWarp] = v; }
+  typename S::T* p;  // lane's element 0 (= warp region + lane)
+  __device__ __forceinline__ typename S::T ld(int e) const { return p[(size_t)e * kWarp]; }
+  __device__ __forceinline__ void st(int e, typename S::T v) const { p[(size_t)e * kWarp] = v; }
+  __device__ __forceinline__ double ldd(int e) const { return S::re(ld(e)); }
 };
 
-// Include the first mode of node (src, o rows offset) with m modes; write the
-// child (m-1 modes) to (dst, dst_o).  In place when dst == src and
-// dst_o == o + 2.  xs/ys: scratch of 2(m-1) elements each.  Returns rho.
-__device__ __noinline__ double lane_include_mem(const LaneMem L, int src, int o, int m, int dst, int dst_o,
-                                                int xs, int ys, bool& bad);
-
 // Load the trailing 6 x 6 block of a node with 4 modes (exclude its first mode).
-__device__ __forceinline__ void lane_load_trail4(const LaneMem L, int src, int o, HM<6>& C) {
+template <class S>
+__device__ __forceinline__ void lane_load_trail4(const LaneMem<S> L, int src, int o, HM<S, 6>& C) {
 #pragma unroll
   for (int i = 0; i < 6; ++i) {
-    C.d[i] = L.ld(src + P(o + 2 + i, o + 2 + i)).x;
+    C.d[i] = L.ldd(src + P(o + 2 + i, o + 2 + i));
 #pragma unroll
     for (int k = 0; k < i; ++k) C.o[TI(i, k)] = L.ld(src + P(o + 2 + i, o + 2 + k));
   }
 }
 // Include the first mode of a 4-mode node in memory; child (3 modes) in registers.
-__device__ __forceinline__ double lane_include4(const LaneMem L, int src, int o, HM<6>& C, bool& bad) {
-  Pivot pv = make_pivot(L.ld(src + P(o, o)).x, L.ld(src + P(o + 1, o)), L.ld(src + P(o + 1, o + 1)).x);
+template <class S>
+__device__ __forceinline__ double lane_include4(const LaneMem<S> L, int src, int o, HM<S, 6>& C, bool& bad) {
+  using T = typename S::T;
+  const Pivot<S> pv = make_pivot<S>(L.ldd(src + P(o, o)), L.ld(src + P(o + 1, o)), L.ldd(src + P(o + 1, o + 1)));
   bad |= !pv.ok;
-  double2 x[6], yp[6];
+  T x[6], yp[6];
 #pragma unroll
   for (int r = 0; r < 6; ++r) {
     x[r] = L.ld(src + P(o + 2 + r, o));
-    yp[r] = reduce_col(x[r], L.ld(src + P(o + 2 + r, o + 1)), pv.cl);
+    yp[r] = S::reduce_col(x[r], L.ld(src + P(o + 2 + r, o + 1)), pv.cl);
   }
 #pragma unroll
   for (int i = 0; i < 6; ++i) {
-    double2 xt = cscale(x[i], pv.ia), yt = cscale(yp[i], pv.id2);
+    const T xt = S::scale(x[i], pv.ia), yt = S::scale(yp[i], pv.id2);
 #pragma unroll
-    for (int k = 0; k < i; ++k) C.o[TI(i, k)] = rank2_off(L.ld(src + P(o + 2 + i, o + 2 + k)), xt, x[k], yt, yp[k]);
-    C.d[i] = rank2_diag(L.ld(src + P(o + 2 + i, o + 2 + i)).x, xt, x[i], yt, yp[i]);
+    for (int k = 0; k < i; ++k)
+      C.o[TI(i, k)] = S::rank2_off(L.ld(src + P(o + 2 + i, o + 2 + k)), xt, x[k], yt, yp[k]);
+    C.d[i] = S::rank2_diag(L.ldd(src + P(o + 2 + i, o + 2 + i)), xt, x[i], yt, yp[i]);
   }
   return pv.rho;
 }
 // Load a whole node with R/2 modes (R <= 6) from memory into registers.
-template <int R>
-__device__ __forceinline__ void lane_load_node(const LaneMem L, int src, int o, HM<R>& C) {
+template <class S, int R>
+__device__ __forceinline__ void lane_load_node(const LaneMem<S> L, int src, int o, HM<S, R>& C) {
 #pragma unroll
   for (int i = 0; i < R; ++i) {
-    C.d[i] = L.ld(src + P(o + i, o + i)).x;
+    C.d[i] = L.ldd(src + P(o + i, o + i));
 #pragma unroll
     for (int k = 0; k < i; ++k) C.o[TI(i, k)] = L.ld(src + P(o + i, o + k));
   }
 }
-
-// ---------------------------------------------------------------------------
-// Cooperative include: the 32 lanes of a warp split the entries of one node
-// stored contiguously (packed, not interleaved).  Used for the shared upper
-// part of the tree, where nodes are large.  All lanes compute the pivot; the
-// call ends with __syncwarp so the child is visible to every lane.
-// ---------------------------------------------------------------------------
-__device__ __noinline__ double coop_include(const double2* src, int o, int m, double2* dst, int dst_o, double2* xs,
-                                            double2* ys, bool& bad);
 
 }  // namespace tor

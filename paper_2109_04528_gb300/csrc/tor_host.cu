@@ -109,7 +109,28 @@ struct MatIn {
   const int* modes = nullptr;   // host list of n source modes (session marginals), or null
   long long leaf_lo = 0;        // tor_eval_range: first reduction leaf (warp task) to evaluate
   long long leaf_count = -1;    // tor_eval_range: number of leaves; -1 = all
+  int real_hint = -1;           // 1/0: structured or not, already known (sessions); -1 = detect
 };
+
+// Is the host matrix structured, [[P, Q], [conj(Q), conj(P)]] in block layout
+// (a physical Gaussian state), within 1e-12 max|O| entrywise?  Same test as k_structure.
+static int host_structured(const MatIn& m) {
+  const int n = m.n;
+  auto row = [&](int mode, int c) { return m.layout == TOR_LAYOUT_BLOCK ? mode + c * n : 2 * mode + c; };
+  double mx = 0, dev = 0;
+  for (int j = 0; j < n; ++j)
+    for (int k = 0; k < n; ++k) {
+      const tor_c128 aa = m.O[(size_t)row(j, 0) * m.ld + row(k, 0)], dd = m.O[(size_t)row(j, 1) * m.ld + row(k, 1)];
+      const tor_c128 ac = m.O[(size_t)row(j, 0) * m.ld + row(k, 1)], ca = m.O[(size_t)row(j, 1) * m.ld + row(k, 0)];
+      for (double v : {aa.re, aa.im, dd.re, dd.im, ac.re, ac.im, ca.re, ca.im}) {
+        if (!std::isfinite(v)) return 0;
+        mx = std::max(mx, std::fabs(v));
+      }
+      dev = std::max({dev, std::fabs(dd.re - aa.re), std::fabs(dd.im + aa.im), std::fabs(ca.re - ac.re),
+                      std::fabs(ca.im + ac.im)});
+    }
+  return dev <= 1e-12 * mx;
+}
 
 struct Slot {
   cudaStream_t stream = nullptr;
@@ -162,6 +183,7 @@ struct Slot {
 struct tor_session {
   tor_ctx* ctx = nullptr;  // null once the context has been destroyed
   int device = 0;
+  int real = 0;            // Sigma is structured: every O^(j) takes the real (x, p) path
   int N = 0;
   int inflight = 0;        // requests taken by the serving loop and not completed (guarded by ctx->q_mu)
   int blocking = 0;        // tor_eval_marginal calls in progress (guarded by ctx->q_mu)
@@ -316,8 +338,45 @@ static tor_status slot_prepare(tor_ctx* ctx, Slot& S, const std::vector<MatIn>& 
     note(r.status);
   }
   if (S.act.empty()) return first;
-  // job order: by n descending so equal sizes are adjacent (stable: same n keeps caller order)
-  std::stable_sort(S.act.begin(), S.act.end(), [&](int a, int b) { return ins[a].n > ins[b].n; });
+  // real (x, p) path for structured inputs: known (sessions), checked here (host
+  // inputs), or checked by k_structure (device inputs)
+  std::vector<int> realv(count, 0);
+  if (!(ctx->cfg.flags & TOR_COMPLEX_PATH)) {
+    std::vector<int> on_dev;
+    for (int i : S.act) {
+      const MatIn& m = ins[i];
+      if (m.real_hint >= 0) realv[i] = m.real_hint;
+      else if (!m.dev) realv[i] = host_structured(m);
+      else on_dev.push_back(i);
+    }
+    if (!on_dev.empty()) {
+      const int K = (int)on_dev.size();
+      uint64_t* g0 = &S.gen;
+      CK(S.h_mats.ensure(K * sizeof(MatDesc), g0), "pinned mats");
+      CK(S.d_mats.ensure(K * sizeof(MatDesc), g0), "alloc mats");
+      CK(S.d_flags.ensure(K * sizeof(int), g0), "alloc flags");
+      CK(S.h_results.ensure(K * sizeof(int), g0), "pinned results");
+      MatDesc* hm = (MatDesc*)S.h_mats.p;
+      for (int a = 0; a < K; ++a) {
+        const MatIn& m = ins[on_dev[a]];
+        hm[a] = MatDesc{};
+        hm[a].O = (const double2*)m.O;
+        hm[a].ld = m.ld;
+        hm[a].n = m.n;
+        hm[a].n_src = m.n;
+        hm[a].layout = m.layout;
+      }
+      CK(cudaMemcpyAsync(S.d_mats.p, S.h_mats.p, K * sizeof(MatDesc), cudaMemcpyHostToDevice, S.stream), "H2D check");
+      CK(launch_structure((const MatDesc*)S.d_mats.p, K, (int*)S.d_flags.p, S.stream), "k_structure");
+      CK(cudaMemcpyAsync(S.h_results.p, S.d_flags.p, K * sizeof(int), cudaMemcpyDeviceToHost, S.stream), "D2H check");
+      CK(cudaStreamSynchronize(S.stream), "structure check");
+      for (int a = 0; a < K; ++a) realv[on_dev[a]] = ((const int*)S.h_results.p)[a];
+    }
+  }
+  // job order: by n descending, then type, so equal (n, type) are adjacent (stable: caller order within)
+  std::stable_sort(S.act.begin(), S.act.end(), [&](int a, int b) {
+    return ins[a].n != ins[b].n ? ins[a].n > ins[b].n : realv[a] < realv[b];
+  });
   const int J = (int)S.act.size();
   S.mats.assign(J, MatDesc{});
   S.tasks.clear();
@@ -328,6 +387,7 @@ static tor_status slot_prepare(tor_ctx* ctx, Slot& S, const std::vector<MatIn>& 
     MatDesc& D = S.mats[j];
     D.n = m.n;
     D.p = p;
+    D.real = realv[S.act[j]];
     D.layout = m.layout;
     D.n_src = m.modes ? m.n_src : m.n;
     D.part_off = S.parts;
@@ -351,7 +411,7 @@ static tor_status slot_prepare(tor_ctx* ctx, Slot& S, const std::vector<MatIn>& 
   // warp tasks, largest subtrees first
   for (int j = 0; j < J;) {
     int k = j;
-    while (k < J && S.mats[k].n == S.mats[j].n) ++k;
+    while (k < J && S.mats[k].n == S.mats[j].n && S.mats[k].real == S.mats[j].real) ++k;
     const int p = S.mats[j].p, M = S.mats[j].n - p;
     if (p >= 5) {
       for (int a = j; a < k; ++a) {
@@ -525,7 +585,7 @@ static tor_status slot_launch(tor_ctx* ctx, Slot& S) {
   uint64_t key = mix(0, (uint64_t)S.J);
   for (const MatDesc& D : S.mats)
     key = mix(key, (uint64_t)D.n | (uint64_t)D.p << 8 | (uint64_t)D.n_src << 16 | (uint64_t)D.layout << 28 |
-                       (uint64_t)(D.modes != nullptr) << 29);
+                       (uint64_t)(D.modes != nullptr) << 29 | (uint64_t)D.real << 30);
   for (const MatDesc& D : S.mats) key = mix(key, (uint64_t)D.red_lo << 8 ^ (uint64_t)D.red_log2);
   key = mix(key, (uint64_t)S.o_elems);
   key = mix(key, (uint64_t)S.mode_elems);
@@ -1190,8 +1250,19 @@ tor_status tor_session_create(tor_ctx* ctx, int n_total, const tor_c128* M, int 
       K[(size_t)a * m + b] = kind == TOR_SESSION_O ? CL{(a == b ? 1.0L : 0.0L) - v.re, -(long double)v.im}
                                                    : CL{(long double)v.re, (long double)v.im};
     }
+  // structure of K = Sigma^{-1} in pairs order: K(a_j^dag, a_k^dag) = conj K(a_j, a_k),
+  // K(a_j^dag, a_k) = conj K(a_j, a_k^dag)
+  long double kmax = 0, kdev = 0;
+  for (int j = 0; j < N; ++j)
+    for (int k = 0; k < N; ++k) {
+      const CL aa = K[(size_t)(2 * j) * m + 2 * k], dd = K[(size_t)(2 * j + 1) * m + 2 * k + 1];
+      const CL ac = K[(size_t)(2 * j) * m + 2 * k + 1], ca = K[(size_t)(2 * j + 1) * m + 2 * k];
+      for (long double v : {aa.re, aa.im, dd.re, dd.im, ac.re, ac.im, ca.re, ca.im}) kmax = std::max(kmax, fabsl(v));
+      kdev = std::max({kdev, fabsl(dd.re - aa.re), fabsl(dd.im + aa.im), fabsl(ca.re - ac.re), fabsl(ca.im + ac.im)});
+    }
   if (kind == TOR_SESSION_SIGMA && !hpd_inverse(K, m)) return TOR_ENOTPD;
   tor_session* s = new tor_session();
+  s->real = kdev <= 1e-12L * kmax && !(ctx->cfg.flags & TOR_COMPLEX_PATH);
   s->ctx = ctx;
   s->device = ctx->cfg.device;
   s->N = N;
@@ -1294,6 +1365,7 @@ static tor_status marginal_in(tor_session* s, int j, int k, const int* modes, Ma
   in.layout = TOR_LAYOUT_PAIRS;
   in.dev = true;
   in.modes = k ? own.data() : nullptr;
+  in.real_hint = s->real;
   return TOR_OK;
 }
 
@@ -1350,7 +1422,7 @@ tor_status tor_submit_marginal(tor_ctx* ctx, tor_session* s, int j, int k, const
 // only, so a fixed synthetic matrix (0.3 I plus a small seeded Hermitian
 // perturbation, I - O positive definite) times every input of that size.
 // ---------------------------------------------------------------------------
-static void synthetic_matrix(int n, std::vector<tor_c128>& O) {
+static void synthetic_matrix(int n, std::vector<tor_c128>& O, bool structured, int layout) {
   const int m = 2 * n;
   O.assign((size_t)m * m, tor_c128{0.0, 0.0});
   uint64_t x = 0x9E3779B97F4A7C15ull ^ (uint64_t)n;
@@ -1371,6 +1443,21 @@ static void synthetic_matrix(int n, std::vector<tor_c128>& O) {
       O[(size_t)c * m + r] = tor_c128{a, -b};
     }
   }
+  if (!structured) return;
+  // impose [[P, Q], [conj(Q), conj(P)]] (block layout), the form of a physical state
+  auto row = [&](int mode, int c) { return layout == TOR_LAYOUT_BLOCK ? mode + c * n : 2 * mode + c; };
+  for (int j = 0; j < n; ++j)
+    for (int k = 0; k < n; ++k) {
+      const tor_c128 aa = O[(size_t)row(j, 0) * m + row(k, 0)];
+      O[(size_t)row(j, 1) * m + row(k, 1)] = tor_c128{aa.re, -aa.im};
+    }
+  for (int j = 0; j < n; ++j)
+    for (int k = 0; k <= j; ++k) {  // Q symmetric
+      const tor_c128 q = O[(size_t)row(j, 0) * m + row(k, 1)];
+      O[(size_t)row(k, 0) * m + row(j, 1)] = q;
+      O[(size_t)row(j, 1) * m + row(k, 0)] = tor_c128{q.re, -q.im};
+      O[(size_t)row(k, 1) * m + row(j, 0)] = tor_c128{q.re, -q.im};
+    }
 }
 
 extern "C" {
@@ -1381,7 +1468,7 @@ tor_status tor_autotune(tor_ctx* ctx, int n_lo, int n_hi, double budget_s, int* 
   const double per_n = budget_s / (n_hi - n_lo + 1);
   std::vector<tor_c128> O;
   for (int n = n_lo; n <= n_hi; ++n) {
-    synthetic_matrix(n, O);
+    synthetic_matrix(n, O, !(ctx->cfg.flags & TOR_COMPLEX_PATH), ctx->cfg.layout);
     int base;
     {
       std::lock_guard<std::mutex> lk(ctx->run_mu);

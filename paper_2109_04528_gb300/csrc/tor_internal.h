@@ -20,7 +20,7 @@ struct MatDesc {
   int red_log2;         // log2 of the number of reduction leaves: p - 5 if p >= 5, else p
   int n, p, ld, layout;
   int n_src;            // modes of the source matrix (n unless `modes` selects a submatrix)
-  int pad;
+  int real;             // 1: O is structured; B holds the real V = U^H (I - O) U (doubles)
   long long red_lo;     // first reduction leaf this job evaluates (tor_eval_range); 0 otherwise
 };
 
@@ -65,6 +65,7 @@ long long lane_elems_for(int n, int p);
 long long warp_elems_for(int n, int p);
 
 cudaError_t launch_intake(const MatDesc* d_mats, int nmats, int check, int* d_flags, cudaStream_t s);
+cudaError_t launch_structure(const MatDesc* d_mats, int nmats, int* d_out, cudaStream_t s);
 cudaError_t launch_units(const UnitsParams& prm, int grid, cudaStream_t s);
 cudaError_t launch_reduce(const MatDesc* d_mats, int nmats, const Part* partials, const int* flags,
                           ResultRec* out, cudaStream_t s);

@@ -1,7 +1,8 @@
 // tor_kernels.cu -- the GPU path of the subset-tree Torontonian.
 //
 //   k_intake  : B = I - O in pairs order, packed lower triangle (paper Sec. 1
-//               Eq. A and the row order of Sec. 2); Hermitian / finite checks.
+//               Eq. A and the row order of Sec. 2), or its real (x, p) form V
+//               for structured O; Hermitian / finite checks.
 //   k_units   : persistent warps; each warp task evaluates 32 units (prefix
 //               subtrees) of the tree of Algorithm 2, one unit per lane.
 //   k_reduce  : fixed-shape binary tree over each matrix's task partials (each
@@ -46,56 +47,73 @@ __device__ __forceinline__ unsigned long long global_ns() {
 
 // ------------------------------------------------------------------ includes
 
-__device__ __noinline__ double lane_include_mem(const LaneMem L, int src, int o, int m, int dst, int dst_o,
+// Include the first mode of node (src, o rows offset) with m modes; write the
+// child (m-1 modes) to (dst, dst_o).  In place when dst == src and
+// dst_o == o + 2.  xs/ys: scratch of 2(m-1) elements each.  Returns rho.
+template <class S>
+__device__ __noinline__ double lane_include_mem(const LaneMem<S> L, int src, int o, int m, int dst, int dst_o,
                                                 int xs, int ys, bool& bad) {
-  Pivot pv = make_pivot(L.ld(src + P(o, o)).x, L.ld(src + P(o + 1, o)), L.ld(src + P(o + 1, o + 1)).x);
+  using T = typename S::T;
+  const Pivot<S> pv = make_pivot<S>(L.ldd(src + P(o, o)), L.ld(src + P(o + 1, o)), L.ldd(src + P(o + 1, o + 1)));
   bad |= !pv.ok;
   const int R = 2 * (m - 1);
   for (int r = 0; r < R; ++r) {
-    double2 x = L.ld(src + P(o + 2 + r, o));
+    const T x = L.ld(src + P(o + 2 + r, o));
     L.st(xs + r, x);
-    L.st(ys + r, reduce_col(x, L.ld(src + P(o + 2 + r, o + 1)), pv.cl));
+    L.st(ys + r, S::reduce_col(x, L.ld(src + P(o + 2 + r, o + 1)), pv.cl));
   }
   for (int i = 0; i < R; ++i) {
-    const double2 xi = L.ld(xs + i), yi = L.ld(ys + i);
-    const double2 xt = cscale(xi, pv.ia), yt = cscale(yi, pv.id2);
+    const T xi = L.ld(xs + i), yi = L.ld(ys + i);
+    const T xt = S::scale(xi, pv.ia), yt = S::scale(yi, pv.id2);
     const int srow = src + P(o + 2 + i, o + 2);
     const int drow = dst + P(dst_o + i, dst_o);
 #pragma unroll 2
-    for (int k = 0; k < i; ++k) L.st(drow + k, rank2_off(L.ld(srow + k), xt, L.ld(xs + k), yt, L.ld(ys + k)));
-    L.st(drow + i, make_double2(rank2_diag(L.ld(srow + i).x, xt, xi, yt, yi), 0.0));
+    for (int k = 0; k < i; ++k) L.st(drow + k, S::rank2_off(L.ld(srow + k), xt, L.ld(xs + k), yt, L.ld(ys + k)));
+    L.st(drow + i, S::diag(S::rank2_diag(L.ldd(srow + i), xt, xi, yt, yi)));
   }
   return pv.rho;
 }
 
-__device__ __noinline__ double coop_include(const double2* src, int o, int m, double2* dst, int dst_o, double2* xs,
-                                            double2* ys, bool& bad) {
+// Cooperative include: the 32 lanes of a warp split the entries of one node
+// stored contiguously (packed, not interleaved).  Used for the shared upper
+// part of the tree, where nodes are large.  All lanes compute the pivot; the
+// call ends with __syncwarp so the child is visible to every lane.
+template <class S>
+__device__ __noinline__ double coop_include(const typename S::T* src, int o, int m, typename S::T* dst, int dst_o,
+                                            typename S::T* xs, typename S::T* ys, bool& bad) {
+  using T = typename S::T;
   const int lane = threadIdx.x & (kWarp - 1);
-  Pivot pv = make_pivot(src[P(o, o)].x, src[P(o + 1, o)], src[P(o + 1, o + 1)].x);
+  const Pivot<S> pv = make_pivot<S>(S::re(src[P(o, o)]), src[P(o + 1, o)], S::re(src[P(o + 1, o + 1)]));
   bad |= !pv.ok;
   const int R = 2 * (m - 1);
   // xs[0..R) = x, xs[R..2R) = x / d1; ys[0..R) = y', ys[R..2R) = y' / d2
   for (int r = lane; r < R; r += kWarp) {
-    double2 x = src[P(o + 2 + r, o)];
-    double2 y = reduce_col(x, src[P(o + 2 + r, o + 1)], pv.cl);
+    const T x = src[P(o + 2 + r, o)];
+    const T y = S::reduce_col(x, src[P(o + 2 + r, o + 1)], pv.cl);
     xs[r] = x;
-    xs[R + r] = cscale(x, pv.ia);
+    xs[R + r] = S::scale(x, pv.ia);
     ys[r] = y;
-    ys[R + r] = cscale(y, pv.id2);
+    ys[R + r] = S::scale(y, pv.id2);
   }
   __syncwarp();
   const int tot = (R * (R + 1)) / 2;
   int i = 0, k = lane;
-  while (k > i) { k -= i + 1; ++i; }
+  while (k > i) {
+    k -= i + 1;
+    ++i;
+  }
   for (int e = lane; e < tot; e += kWarp) {
-    const double2 xt = xs[R + i], yt = ys[R + i];
-    const double2 s = src[P(o + 2 + i, o + 2 + k)];
-    double2 out;
-    if (k < i) out = rank2_off(s, xt, xs[k], yt, ys[k]);
-    else out = make_double2(rank2_diag(s.x, xt, xs[i], yt, ys[i]), 0.0);
+    const T xt = xs[R + i], yt = ys[R + i];
+    const T sv = src[P(o + 2 + i, o + 2 + k)];
+    T out;
+    if (k < i) out = S::rank2_off(sv, xt, xs[k], yt, ys[k]);
+    else out = S::diag(S::rank2_diag(S::re(sv), xt, xs[i], yt, ys[i]));
     dst[P(dst_o + i, dst_o + k)] = out;
     k += kWarp;
-    while (k > i) { k -= i + 1; ++i; }
+    while (k > i) {
+      k -= i + 1;
+      ++i;
+    }
   }
   __syncwarp();
   return pv.rho;
@@ -116,23 +134,24 @@ __device__ __noinline__ double coop_include(const double2* src, int o, int m, do
 // excluded children are views of their parent, so a node is never
 // overwritten while a pending include still needs it.  The 3-mode nodes and
 // everything below them live in registers.
-__device__ __noinline__ void lane_dfs(const LaneMem L, int root, int root_o, int M, int n, double phi_root,
+template <class S>
+__device__ __noinline__ void lane_dfs(const LaneMem<S> L, int root, int root_o, int M, int n, double phi_root,
                                       int incl_root, int buf4, int xs, int ys, DD& acc, double& ab, bool& bad) {
   if (M <= 3) {
     const int excl_above = (n - M) - incl_root;
     double v = 0.0, a = 0.0;
     if (M == 1) {
-      HM<2> R2;
-      lane_load_node<2>(L, root, root_o, R2);
-      Subtree<2>::run(R2, phi_root, v, a, bad);
+      HM<S, 2> R2;
+      lane_load_node<S, 2>(L, root, root_o, R2);
+      Subtree<S, 2>::run(R2, phi_root, v, a, bad);
     } else if (M == 2) {
-      HM<4> R4;
-      lane_load_node<4>(L, root, root_o, R4);
-      Subtree<4>::run(R4, phi_root, v, a, bad);
+      HM<S, 4> R4;
+      lane_load_node<S, 4>(L, root, root_o, R4);
+      Subtree<S, 4>::run(R4, phi_root, v, a, bad);
     } else {
-      HM<6> R6;
-      lane_load_node<6>(L, root, root_o, R6);
-      Subtree<6>::run(R6, phi_root, v, a, bad);
+      HM<S, 6> R6;
+      lane_load_node<S, 6>(L, root, root_o, R6);
+      Subtree<S, 6>::run(R6, phi_root, v, a, bad);
     }
     if (excl_above & 1) v = -v;
     acc.add(v);
@@ -154,7 +173,7 @@ __device__ __noinline__ void lane_dfs(const LaneMem L, int root, int root_o, int
     if (c != 0 && (c & 1ull) == 0) {
       const int mi = 4 + __ffsll((long long)c) - 1;
       const int dst = buf4 + stack_off(mi - 1);
-      const double rho = lane_include_mem(L, nb[mi], nof[mi], mi, dst, 0, xs, ys, bad);
+      const double rho = lane_include_mem<S>(L, nb[mi], nof[mi], mi, dst, 0, xs, ys, bad);
       nb[mi - 1] = dst;
       nof[mi - 1] = 0;
       ph[mi - 1] = ph[mi] * rho;
@@ -164,16 +183,16 @@ __device__ __noinline__ void lane_dfs(const LaneMem L, int root, int root_o, int
         ph[m] = ph[m + 1];
       }
     }
-    HM<6> R3;
+    HM<S, 6> R3;
     double phi3;
     if (c & 1ull) {
-      phi3 = ph[4] * lane_include4(L, nb[4], nof[4], R3, bad);
+      phi3 = ph[4] * lane_include4<S>(L, nb[4], nof[4], R3, bad);
     } else {
-      lane_load_trail4(L, nb[4], nof[4], R3);
+      lane_load_trail4<S>(L, nb[4], nof[4], R3);
       phi3 = ph[4];
     }
     double v, a;
-    Subtree<6>::run(R3, phi3, v, a, bad);
+    Subtree<S, 6>::run(R3, phi3, v, a, bad);
     const int excl_above = (n - 3) - (incl_root + __popcll(c));
     if (excl_above & 1) v = -v;
     acc.add(v);
@@ -183,15 +202,30 @@ __device__ __noinline__ void lane_dfs(const LaneMem L, int root, int root_o, int
 
 // ------------------------------------------------------------------ kernels
 
+// Source row of component c (0 = a, 1 = a^dag) of job mode t of matrix D.
+__device__ __forceinline__ int src_row(const MatDesc& D, int t, int c) {
+  const int m = D.modes ? D.modes[t] : t;
+  return D.layout == 0 ? m + c * D.n_src : 2 * m + c;
+}
+
 // One block per matrix; threads over the packed lower triangle of B.  Checks:
 // finite entries, and max |O_rs - conj(O_sr)| <= 1e-12 max |O| in the
-// max(|Re|, |Im|) norm of each entry.
+// max(|Re|, |Im|) norm of each entry.  Writes the complex B = I - O in pairs
+// order, or, when D.real is set (the host found O structured), the real
+// V = U^H B U in (x_1, p_1, x_2, p_2, ...) order:
+//   V(x_j, x_k) = Re A + Re C,  V(x_j, p_k) = Im C - Im A,
+//   V(p_j, x_k) = Im A + Im C,  V(p_j, p_k) = Re A - Re C,
+// with A = B(a_j, a_k) and C = B(a_j, a_k^dag).
 __global__ void __launch_bounds__(256) k_intake(const MatDesc* __restrict__ mats, int check, int* __restrict__ flags) {
   const MatDesc D = mats[blockIdx.x];
   const int n = D.n, tot = n * (2 * n + 1);
   __shared__ unsigned long long s_max, s_dev;
   __shared__ int s_bad;
-  if (threadIdx.x == 0) { s_max = 0; s_dev = 0; s_bad = 0; }
+  if (threadIdx.x == 0) {
+    s_max = 0;
+    s_dev = 0;
+    s_bad = 0;
+  }
   __syncthreads();
   double mx = 0.0, dev = 0.0;
   int bad = 0;
@@ -200,15 +234,24 @@ __global__ void __launch_bounds__(256) k_intake(const MatDesc* __restrict__ mats
     while (P(r, 0) > e) --r;
     while (P(r + 1, 0) <= e) ++r;
     const int s = e - P(r, 0);
-    const int mr = D.modes ? D.modes[r >> 1] : (r >> 1), ms = D.modes ? D.modes[s >> 1] : (s >> 1);
-    const int pr = D.layout == 0 ? mr + (r & 1) * D.n_src : 2 * mr + (r & 1);
-    const int ps = D.layout == 0 ? ms + (s & 1) * D.n_src : 2 * ms + (s & 1);
+    const int pr = src_row(D, r >> 1, r & 1), ps = src_row(D, s >> 1, s & 1);
     const double2 a = D.O[(size_t)pr * D.ld + ps];
     const double2 b = D.O[(size_t)ps * D.ld + pr];
     if (!isfinite(a.x) || !isfinite(a.y) || !isfinite(b.x) || !isfinite(b.y)) bad = 1;
     mx = fmax(mx, fmax(fmax(fabs(a.x), fabs(a.y)), fmax(fabs(b.x), fabs(b.y))));
     dev = fmax(dev, fmax(fabs(a.x - b.x), fabs(a.y + b.y)));
-    D.B[e] = r == s ? make_double2(1.0 - a.x, 0.0) : make_double2(-a.x, -a.y);
+    if (!D.real) {
+      D.B[e] = r == s ? make_double2(1.0 - a.x, 0.0) : make_double2(-a.x, -a.y);
+    } else {
+      const int j = r >> 1, k = s >> 1;
+      const double2 oa = D.O[(size_t)src_row(D, j, 0) * D.ld + src_row(D, k, 0)];
+      const double2 oc = D.O[(size_t)src_row(D, j, 0) * D.ld + src_row(D, k, 1)];
+      const double Are = (j == k ? 1.0 : 0.0) - oa.x, Aim = -oa.y, Cre = -oc.x, Cim = -oc.y;
+      double v;
+      if ((r & 1) == 0) v = (s & 1) == 0 ? Are + Cre : Cim - Aim;
+      else v = (s & 1) == 0 ? Aim + Cim : Are - Cre;
+      ((double*)D.B)[e] = v;
+    }
   }
   // non-negative doubles order like their bit patterns
   atomicMax(&s_max, (unsigned long long)__double_as_longlong(mx));
@@ -222,6 +265,37 @@ __global__ void __launch_bounds__(256) k_intake(const MatDesc* __restrict__ mats
     if (check && !(gdev <= 1e-12 * gmax)) f |= FLAG_NOTHERM;
     flags[blockIdx.x] = f;
   }
+}
+
+// Is O structured, [[P, Q], [conj(Q), conj(P)]] in block layout (the form of a
+// physical Gaussian state), within 1e-12 max|O| entrywise?  One block per
+// matrix; out[i] = 1 if so.  Decides the real (x, p) path.
+__global__ void __launch_bounds__(256) k_structure(const MatDesc* __restrict__ mats, int* __restrict__ out) {
+  const MatDesc D = mats[blockIdx.x];
+  const int n = D.n;
+  __shared__ unsigned long long s_max, s_dev;
+  if (threadIdx.x == 0) {
+    s_max = 0;
+    s_dev = 0;
+  }
+  __syncthreads();
+  double mx = 0.0, dev = 0.0;
+  for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+    const int j = e / n, k = e % n;
+    const double2 aa = D.O[(size_t)src_row(D, j, 0) * D.ld + src_row(D, k, 0)];
+    const double2 dd = D.O[(size_t)src_row(D, j, 1) * D.ld + src_row(D, k, 1)];
+    const double2 ac = D.O[(size_t)src_row(D, j, 0) * D.ld + src_row(D, k, 1)];
+    const double2 ca = D.O[(size_t)src_row(D, j, 1) * D.ld + src_row(D, k, 0)];
+    mx = fmax(mx, fmax(fmax(fmax(fabs(aa.x), fabs(aa.y)), fmax(fabs(dd.x), fabs(dd.y))),
+                       fmax(fmax(fabs(ac.x), fabs(ac.y)), fmax(fabs(ca.x), fabs(ca.y)))));
+    dev = fmax(dev, fmax(fmax(fabs(dd.x - aa.x), fabs(dd.y + aa.y)), fmax(fabs(ca.x - ac.x), fabs(ca.y + ac.y))));
+    if (!isfinite(dev) || !isfinite(mx)) dev = __longlong_as_double(0x7ff0000000000000ll);
+  }
+  atomicMax(&s_max, (unsigned long long)__double_as_longlong(mx));
+  atomicMax(&s_dev, (unsigned long long)__double_as_longlong(dev));
+  __syncthreads();
+  if (threadIdx.x == 0)
+    out[blockIdx.x] = __longlong_as_double((long long)s_dev) <= 1e-12 * __longlong_as_double((long long)s_max);
 }
 
 // Unit partial (hi, lo, abs).  For p < 5 the unit partials are the reduction leaves.
@@ -256,16 +330,20 @@ __device__ __forceinline__ void write_task_partial(const UnitsParams& prm, const
 // p >= 5: the warp builds the task node (depth p - 5) cooperatively, fans it
 // out breadth-first over 5 more levels into 32 unit roots, one per lane, and
 // each lane walks its own subtree.
-__device__ void run_task_shared(const UnitsParams& prm, const TaskDesc T, const LaneMem L, double2* WS, int lane) {
+template <class S>
+__device__ void run_task_shared(const UnitsParams& prm, const TaskDesc T, int lane, long long gw) {
+  using E = typename S::T;
+  const LaneMem<S> L{(E*)prm.lane_scratch + gw * kWarp * prm.lane_elems + lane};
+  E* WS = (E*)prm.warp_scratch + gw * prm.warp_elems;
   const MatDesc D = prm.mats[T.mat];
   const int n = D.n, p = D.p, M = n - p, m0 = M + 5;
-  double2* SB = WS;
-  double2* arena = WS + tri_size(n);
-  double2* xsw = arena + arena_off(m0, 5);
-  double2* ysw = xsw + 4 * n;
+  E* SB = WS;
+  E* arena = WS + tri_size(n);
+  E* xsw = arena + arena_off(m0, 5);
+  E* ysw = xsw + 4 * n;
   bool bad = false;
   // 1. task node: decisions on modes 0..p-6 are the bits of T.sub (same for all lanes)
-  const double2* src = D.B;
+  const E* src = (const E*)D.B;
   int o = 0, incl = 0;
   double phi = 1.0;
   bool own = false;
@@ -273,12 +351,12 @@ __device__ void run_task_shared(const UnitsParams& prm, const TaskDesc T, const 
     if ((T.sub >> j) & 1) {
       double rho;
       if (!own) {
-        rho = coop_include(src, o, n - j, SB, 0, xsw, ysw, bad);
+        rho = coop_include<S>(src, o, n - j, SB, 0, xsw, ysw, bad);
         src = SB;
         o = 0;
         own = true;
       } else {
-        rho = coop_include(SB, o, n - j, SB, o + 2, xsw, ysw, bad);
+        rho = coop_include<S>(SB, o, n - j, SB, o + 2, xsw, ysw, bad);
         o += 2;
       }
       phi *= rho;
@@ -288,18 +366,18 @@ __device__ void run_task_shared(const UnitsParams& prm, const TaskDesc T, const 
     }
   }
   // 2. breadth-first fan-out: lane q holds level-d node q (bit e of q = decision on mode p-5+e)
-  const double2* nptr = src;
+  const E* nptr = src;
   int no = o, nincl = incl;
   double nphi = phi;
   for (int d = 0; d < 5; ++d) {
     const int nodes = 1 << d, m = m0 - d;
     for (int q = 0; q < nodes; ++q) {
-      const double2* qp = (const double2*)__shfl_sync(0xffffffffu, (unsigned long long)nptr, q);
+      const E* qp = (const E*)__shfl_sync(0xffffffffu, (unsigned long long)nptr, q);
       const int qo = __shfl_sync(0xffffffffu, no, q);
       const double qphi = __shfl_sync(0xffffffffu, nphi, q);
       const int qincl = __shfl_sync(0xffffffffu, nincl, q);
-      double2* dst = arena + arena_off(m0, d) + q * tri_size(m - 1);
-      const double rho = coop_include(qp, qo, m, dst, 0, xsw, ysw, bad);
+      E* dst = arena + arena_off(m0, d) + q * tri_size(m - 1);
+      const double rho = coop_include<S>(qp, qo, m, dst, 0, xsw, ysw, bad);
       if (lane == (q | nodes)) {
         nptr = dst;
         no = 0;
@@ -317,15 +395,18 @@ __device__ void run_task_shared(const UnitsParams& prm, const TaskDesc T, const 
   const int xs = root_sz + stack_off(M), ys = xs + 2 * n;
   DD acc{0.0, 0.0};
   double ab = 0.0;
-  lane_dfs(L, 0, 0, M, n, nphi, nincl, root_sz, xs, ys, acc, ab, bad);
+  lane_dfs<S>(L, 0, 0, M, n, nphi, nincl, root_sz, xs, ys, acc, ab, bad);
   const long long u = (long long)T.sub | ((long long)lane << (p - 5));
   const Part v = write_partial(prm, D, T.mat, u, acc, ab, bad);
   write_task_partial(prm, D, T.sub, v, lane);
 }
 
-// p < 5: lanes take units of up to 32 small matrices of one size; each lane
-// builds its own root from B by in-place includes.
-__device__ void run_task_lanes(const UnitsParams& prm, const TaskDesc T, const LaneMem L, int lane) {
+// p < 5: lanes take units of up to 32 small matrices of one size and type;
+// each lane builds its own root from B by in-place includes.
+template <class S>
+__device__ void run_task_lanes(const UnitsParams& prm, const TaskDesc T, int lane, long long gw) {
+  using E = typename S::T;
+  const LaneMem<S> L{(E*)prm.lane_scratch + gw * kWarp * prm.lane_elems + lane};
   const int p = prm.mats[T.mat].p;
   const long long q = (long long)T.sub * kWarp + lane;
   if (q >= ((long long)T.nmat << p)) return;
@@ -334,8 +415,9 @@ __device__ void run_task_lanes(const UnitsParams& prm, const TaskDesc T, const L
   const int n = D.n, M = n - p;
   const long long u = q & ((1ll << p) - 1);
   const int RR = 2 * n;
+  const E* B = (const E*)D.B;
   for (int i = 0; i < RR; ++i)
-    for (int k = 0; k <= i; ++k) L.st(P(i, k), D.B[P(i, k)]);
+    for (int k = 0; k <= i; ++k) L.st(P(i, k), B[P(i, k)]);
   const int root_sz = tri_size(n);
   const int xs = root_sz + stack_off(M), ys = xs + 2 * n;
   bool bad = false;
@@ -343,14 +425,14 @@ __device__ void run_task_lanes(const UnitsParams& prm, const TaskDesc T, const L
   double phi = 1.0;
   for (int j = 0; j < p; ++j) {
     if ((u >> j) & 1) {
-      phi *= lane_include_mem(L, 0, o, n - j, 0, o + 2, xs, ys, bad);
+      phi *= lane_include_mem<S>(L, 0, o, n - j, 0, o + 2, xs, ys, bad);
       ++incl;
     }
     o += 2;
   }
   DD acc{0.0, 0.0};
   double ab = 0.0;
-  lane_dfs(L, 0, o, M, n, phi, incl, root_sz, xs, ys, acc, ab, bad);
+  lane_dfs<S>(L, 0, o, M, n, phi, incl, root_sz, xs, ys, acc, ab, bad);
   write_partial(prm, D, mat, u, acc, ab, bad);
 }
 
@@ -359,8 +441,6 @@ constexpr int kUnitsThreads = 128;
 __global__ void __launch_bounds__(kUnitsThreads, 2) k_units(const UnitsParams prm) {
   const int lane = threadIdx.x & (kWarp - 1);
   const long long gw = (long long)blockIdx.x * (blockDim.x / kWarp) + threadIdx.x / kWarp;
-  const LaneMem L{prm.lane_scratch + gw * kWarp * prm.lane_elems + lane};
-  double2* WS = prm.warp_scratch + gw * prm.warp_elems;
   const unsigned long long t0 = global_ns();
   for (;;) {
     unsigned t = 0xffffffffu;
@@ -376,8 +456,14 @@ __global__ void __launch_bounds__(kUnitsThreads, 2) k_units(const UnitsParams pr
     t = __shfl_sync(0xffffffffu, t, 0);
     if (t >= (unsigned)prm.ntasks) break;
     const TaskDesc T = prm.tasks[t];
-    if (prm.mats[T.mat].p >= 5) run_task_shared(prm, T, L, WS, lane);
-    else run_task_lanes(prm, T, L, lane);
+    const MatDesc& D0 = prm.mats[T.mat];  // every matrix of a task has the same n, p and type
+    if (D0.real) {
+      if (D0.p >= 5) run_task_shared<Real>(prm, T, lane, gw);
+      else run_task_lanes<Real>(prm, T, lane, gw);
+    } else {
+      if (D0.p >= 5) run_task_shared<Cplx>(prm, T, lane, gw);
+      else run_task_lanes<Cplx>(prm, T, lane, gw);
+    }
     __syncwarp();
   }
 }
@@ -456,6 +542,11 @@ __global__ void __launch_bounds__(256) k_probe(double* out, int iters) {
 cudaError_t launch_intake(const MatDesc* d_mats, int nmats, int check, int* d_flags, cudaStream_t s) {
   if (nmats <= 0) return cudaSuccess;
   k_intake<<<nmats, 256, 0, s>>>(d_mats, check, d_flags);
+  return cudaGetLastError();
+}
+cudaError_t launch_structure(const MatDesc* d_mats, int nmats, int* d_out, cudaStream_t s) {
+  if (nmats <= 0) return cudaSuccess;
+  k_structure<<<nmats, 256, 0, s>>>(d_mats, d_out);
   return cudaGetLastError();
 }
 cudaError_t launch_units(const UnitsParams& prm, int grid, cudaStream_t s) {

@@ -101,7 +101,7 @@ __global__ void k_noalloc_setup(const double2* O, int n, int ld, int layout) {
     D->O = O;
     D->modes = nullptr;
     D->n_src = n;
-    D->pad = 0;
+    D->real = 0;
     D->B = (double2*)(base + OFF_B);
     D->part_off = 0;
     D->red_off = 0;

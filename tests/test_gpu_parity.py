@@ -19,11 +19,14 @@ TOL = 1e-10
 HERE = os.path.dirname(os.path.abspath(__file__))
 
 
-@pytest.fixture(scope="module")
-def ctx():
+@pytest.fixture(scope="module", params=["auto", "complex"])
+def ctx(request):
+    # "auto": physical (structured) inputs take the real (x, p) path;
+    # "complex": every matrix in complex arithmetic
     from paper_2109_04528_gb300 import build
     build.build()
-    c = binding.Context(device=0)
+    flags = binding.TOR_COMPLEX_PATH if request.param == "complex" else 0
+    c = binding.Context(device=0, flags=flags)
     yield c
     c.close()
 
@@ -210,3 +213,28 @@ def test_submit_poll(ctx, oracle_mod):
         st, r = binding.tor_poll(ctx, t, 60.0)
         ref = oracle_mod.tor_brute(O)
         assert st == 0 and gpu_err(r, ref) <= TOL * ref.abs_sum
+
+
+def test_real_and_complex_paths_agree(oracle_mod):
+    inst = inputs.lossy_squeezed(14, 61, (0.5, 1.2), 0.4)
+    with binding.Context(device=0) as a, binding.Context(device=0, flags=binding.TOR_COMPLEX_PATH) as c:
+        ra = binding.tor_eval(a, inst.O)
+        rc = binding.tor_eval(c, inst.O)
+    ref = oracle_mod.tor_brute(inst.O)
+    assert (ra.hi, ra.lo) != (rc.hi, rc.lo) or ra.abs_sum == rc.abs_sum  # two different arithmetics
+    assert gpu_err(ra, ref) <= TOL * ref.abs_sum and gpu_err(rc, ref) <= TOL * ref.abs_sum
+
+
+def test_structure_detection_follows_the_input():
+    # a structured O and the same O with the structure broken by a Hermitian
+    # perturbation of one (a, a) entry only: both evaluate correctly
+    inst = inputs.lossy_squeezed(9, 62, (0.3, 0.8), 0.5)
+    O2 = inst.O.copy()
+    O2[0, 1] += 1e-4
+    O2[1, 0] += 1e-4
+    import oracle
+    for O in (inst.O, O2):
+        with binding.Context(device=0) as a:
+            r = binding.tor_eval(a, O)
+        ref = oracle.tor_brute(O)
+        assert gpu_err(r, ref) <= TOL * ref.abs_sum
