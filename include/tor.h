@@ -96,6 +96,8 @@ typedef struct {
   double err_est;      /* a-priori error estimate 8 n u abs_sum, u = 2^-53 */
   int n;               /* modes of this matrix */
   tor_status status;   /* per-matrix status */
+  int path;            /* arithmetic used: 0 complex, 1 real (x, p) basis (TOR_COMPLEX_PATH) */
+  int reserved;
 } tor_result;
 
 /* Fills *cfg with defaults: device 0, own stream, no budget, planned prefix

@@ -47,7 +47,8 @@ class tor_config(ctypes.Structure):
 
 class tor_result(ctypes.Structure):
     _fields_ = [("hi", ctypes.c_double), ("lo", ctypes.c_double), ("abs_sum", ctypes.c_double),
-                ("err_est", ctypes.c_double), ("n", ctypes.c_int), ("status", ctypes.c_int)]
+                ("err_est", ctypes.c_double), ("n", ctypes.c_int), ("status", ctypes.c_int),
+                ("path", ctypes.c_int), ("reserved", ctypes.c_int)]
 
 
 @dataclass
@@ -58,6 +59,7 @@ class TorResult:
     err_est: float
     n: int
     status: int
+    path: int = 0  # 0 complex, 1 real (x, p) basis
 
     @property
     def tor(self) -> float:
@@ -65,7 +67,7 @@ class TorResult:
 
     @staticmethod
     def of(r: tor_result) -> "TorResult":
-        return TorResult(r.hi, r.lo, r.abs_sum, r.err_est, r.n, r.status)
+        return TorResult(r.hi, r.lo, r.abs_sum, r.err_est, r.n, r.status, r.path)
 
 
 _LIB = None

@@ -112,26 +112,6 @@ struct MatIn {
   int real_hint = -1;           // 1/0: structured or not, already known (sessions); -1 = detect
 };
 
-// Is the host matrix structured, [[P, Q], [conj(Q), conj(P)]] in block layout
-// (a physical Gaussian state), within 1e-12 max|O| entrywise?  Same test as k_structure.
-static int host_structured(const MatIn& m) {
-  const int n = m.n;
-  auto row = [&](int mode, int c) { return m.layout == TOR_LAYOUT_BLOCK ? mode + c * n : 2 * mode + c; };
-  double mx = 0, dev = 0;
-  for (int j = 0; j < n; ++j)
-    for (int k = 0; k < n; ++k) {
-      const tor_c128 aa = m.O[(size_t)row(j, 0) * m.ld + row(k, 0)], dd = m.O[(size_t)row(j, 1) * m.ld + row(k, 1)];
-      const tor_c128 ac = m.O[(size_t)row(j, 0) * m.ld + row(k, 1)], ca = m.O[(size_t)row(j, 1) * m.ld + row(k, 0)];
-      for (double v : {aa.re, aa.im, dd.re, dd.im, ac.re, ac.im, ca.re, ca.im}) {
-        if (!std::isfinite(v)) return 0;
-        mx = std::max(mx, std::fabs(v));
-      }
-      dev = std::max({dev, std::fabs(dd.re - aa.re), std::fabs(dd.im + aa.im), std::fabs(ca.re - ac.re),
-                      std::fabs(ca.im + ac.im)});
-    }
-  return dev <= 1e-12 * mx;
-}
-
 struct Slot {
   cudaStream_t stream = nullptr;
   bool own_stream = false;
@@ -248,16 +228,19 @@ static tor_status cuda_fail(tor_ctx* ctx, cudaError_t e, const char* what) {
     if (e_ != cudaSuccess) return cuda_fail(ctx, e_, what); \
   } while (0)
 
+// Built-in plan, the shape the autotuner finds on GB300 (1216 resident warps),
+// scaled by lw = floor(log2(resident warps)):
+//   small n: units over M = 4 modes (as much parallelism as the tree offers);
+//   then p = lw + 5, about one wave of 2^lw warp tasks;
+//   from n = lw + 16 on, p = lw + 8, about eight waves (room for the tail).
 static int default_prefix_depth(int n, int nwarps) {
-  if (n <= 8) return 0;
-  // aim for >= 8 warp tasks per resident warp (2^(p-5) tasks for p >= 5),
-  // with every unit a subtree over M in [8, 20] modes
-  int need = 0;
-  while ((1ll << need) < 8ll * std::max(nwarps, 1)) ++need;
-  int M = n - 5 - need;
-  M = std::max(8, std::min(20, M));
-  M = std::min(M, n - 1);
-  return n - M;
+  int lw = 0;
+  while ((2ll << lw) <= std::max(nwarps, 1)) ++lw;
+  int p;
+  if (n <= lw + 9) p = n - 4;
+  else if (n <= lw + 15) p = lw + 5;
+  else p = lw + 8;
+  return std::max(0, std::min(p, n - 1));
 }
 
 static int plan_p(tor_ctx* ctx, int n) {
@@ -338,45 +321,8 @@ static tor_status slot_prepare(tor_ctx* ctx, Slot& S, const std::vector<MatIn>& 
     note(r.status);
   }
   if (S.act.empty()) return first;
-  // real (x, p) path for structured inputs: known (sessions), checked here (host
-  // inputs), or checked by k_structure (device inputs)
-  std::vector<int> realv(count, 0);
-  if (!(ctx->cfg.flags & TOR_COMPLEX_PATH)) {
-    std::vector<int> on_dev;
-    for (int i : S.act) {
-      const MatIn& m = ins[i];
-      if (m.real_hint >= 0) realv[i] = m.real_hint;
-      else if (!m.dev) realv[i] = host_structured(m);
-      else on_dev.push_back(i);
-    }
-    if (!on_dev.empty()) {
-      const int K = (int)on_dev.size();
-      uint64_t* g0 = &S.gen;
-      CK(S.h_mats.ensure(K * sizeof(MatDesc), g0), "pinned mats");
-      CK(S.d_mats.ensure(K * sizeof(MatDesc), g0), "alloc mats");
-      CK(S.d_flags.ensure(K * sizeof(int), g0), "alloc flags");
-      CK(S.h_results.ensure(K * sizeof(int), g0), "pinned results");
-      MatDesc* hm = (MatDesc*)S.h_mats.p;
-      for (int a = 0; a < K; ++a) {
-        const MatIn& m = ins[on_dev[a]];
-        hm[a] = MatDesc{};
-        hm[a].O = (const double2*)m.O;
-        hm[a].ld = m.ld;
-        hm[a].n = m.n;
-        hm[a].n_src = m.n;
-        hm[a].layout = m.layout;
-      }
-      CK(cudaMemcpyAsync(S.d_mats.p, S.h_mats.p, K * sizeof(MatDesc), cudaMemcpyHostToDevice, S.stream), "H2D check");
-      CK(launch_structure((const MatDesc*)S.d_mats.p, K, (int*)S.d_flags.p, S.stream), "k_structure");
-      CK(cudaMemcpyAsync(S.h_results.p, S.d_flags.p, K * sizeof(int), cudaMemcpyDeviceToHost, S.stream), "D2H check");
-      CK(cudaStreamSynchronize(S.stream), "structure check");
-      for (int a = 0; a < K; ++a) realv[on_dev[a]] = ((const int*)S.h_results.p)[a];
-    }
-  }
-  // job order: by n descending, then type, so equal (n, type) are adjacent (stable: caller order within)
-  std::stable_sort(S.act.begin(), S.act.end(), [&](int a, int b) {
-    return ins[a].n != ins[b].n ? ins[a].n > ins[b].n : realv[a] < realv[b];
-  });
+  // job order: by n descending so equal sizes are adjacent (stable: same n keeps caller order)
+  std::stable_sort(S.act.begin(), S.act.end(), [&](int a, int b) { return ins[a].n > ins[b].n; });
   const int J = (int)S.act.size();
   S.mats.assign(J, MatDesc{});
   S.tasks.clear();
@@ -387,7 +333,8 @@ static tor_status slot_prepare(tor_ctx* ctx, Slot& S, const std::vector<MatIn>& 
     MatDesc& D = S.mats[j];
     D.n = m.n;
     D.p = p;
-    D.real = realv[S.act[j]];
+    // the arithmetic: forced complex, known (sessions), or detected by k_intake
+    D.real = (ctx->cfg.flags & TOR_COMPLEX_PATH) ? 0 : m.real_hint;
     D.layout = m.layout;
     D.n_src = m.modes ? m.n_src : m.n;
     D.part_off = S.parts;
@@ -411,7 +358,7 @@ static tor_status slot_prepare(tor_ctx* ctx, Slot& S, const std::vector<MatIn>& 
   // warp tasks, largest subtrees first
   for (int j = 0; j < J;) {
     int k = j;
-    while (k < J && S.mats[k].n == S.mats[j].n && S.mats[k].real == S.mats[j].real) ++k;
+    while (k < J && S.mats[k].n == S.mats[j].n) ++k;
     const int p = S.mats[j].p, M = S.mats[j].n - p;
     if (p >= 5) {
       for (int a = j; a < k; ++a) {
@@ -641,6 +588,7 @@ static tor_status slot_finish(Slot& S, tor_result* out, double* unit_partials, d
     r.lo = q.lo;
     r.abs_sum = q.abs_sum;
     r.err_est = 8.0 * r.n * std::ldexp(1.0, -53) * q.abs_sum;
+    r.path = (q.flags & FLAG_REAL) ? 1 : 0;
     if (q.flags & FLAG_NONFINITE) r.status = TOR_EINVAL;
     else if (q.flags & FLAG_NOTHERM) r.status = TOR_ENOTHERM;
     else if (abort_word & ABORT_CANCEL) r.status = TOR_ECANCELED;

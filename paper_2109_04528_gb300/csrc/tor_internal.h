@@ -20,7 +20,7 @@ struct MatDesc {
   int red_log2;         // log2 of the number of reduction leaves: p - 5 if p >= 5, else p
   int n, p, ld, layout;
   int n_src;            // modes of the source matrix (n unless `modes` selects a submatrix)
-  int real;             // 1: O is structured; B holds the real V = U^H (I - O) U (doubles)
+  int real;             // -1: let k_intake detect the structure; 0: complex; 1: real (x, p) path
   long long red_lo;     // first reduction leaf this job evaluates (tor_eval_range); 0 otherwise
 };
 
@@ -32,7 +32,7 @@ struct TaskDesc {
   int mat, sub, nmat, M;
 };
 
-enum { FLAG_NOTPD = 1, FLAG_NOTHERM = 2, FLAG_NONFINITE = 4 };
+enum { FLAG_NOTPD = 1, FLAG_NOTHERM = 2, FLAG_NONFINITE = 4, FLAG_REAL = 8 };
 enum { ABORT_TIMEOUT = 1, ABORT_CANCEL = 2 };
 
 struct UnitsParams {
@@ -65,7 +65,6 @@ long long lane_elems_for(int n, int p);
 long long warp_elems_for(int n, int p);
 
 cudaError_t launch_intake(const MatDesc* d_mats, int nmats, int check, int* d_flags, cudaStream_t s);
-cudaError_t launch_structure(const MatDesc* d_mats, int nmats, int* d_out, cudaStream_t s);
 cudaError_t launch_units(const UnitsParams& prm, int grid, cudaStream_t s);
 cudaError_t launch_reduce(const MatDesc* d_mats, int nmats, const Part* partials, const int* flags,
                           ResultRec* out, cudaStream_t s);

@@ -208,39 +208,69 @@ __device__ __forceinline__ int src_row(const MatDesc& D, int t, int c) {
   return D.layout == 0 ? m + c * D.n_src : 2 * m + c;
 }
 
-// One block per matrix; threads over the packed lower triangle of B.  Checks:
-// finite entries, and max |O_rs - conj(O_sr)| <= 1e-12 max |O| in the
-// max(|Re|, |Im|) norm of each entry.  Writes the complex B = I - O in pairs
-// order, or, when D.real is set (the host found O structured), the real
-// V = U^H B U in (x_1, p_1, x_2, p_2, ...) order:
+// One block per matrix.  Pass 1 checks every entry: finite; Hermitian,
+// max |O_rs - conj(O_sr)| <= 1e-12 max |O|; and structured,
+// O(a_j^dag, a_k^dag) = conj O(a_j, a_k), O(a_j^dag, a_k) = conj O(a_j, a_k^dag)
+// within the same tolerance (the form of every physical Gaussian state), all
+// in the max(|Re|, |Im|) norm of each entry.  Pass 2 writes, in packed lower
+// triangle, either the complex B = I - O in pairs order or, for a structured
+// O (unless D.real == 0), the real V = U^H B U in (x_1, p_1, x_2, p_2, ...)
+// order:
 //   V(x_j, x_k) = Re A + Re C,  V(x_j, p_k) = Im C - Im A,
 //   V(p_j, x_k) = Im A + Im C,  V(p_j, p_k) = Re A - Re C,
-// with A = B(a_j, a_k) and C = B(a_j, a_k^dag).
+// with A = B(a_j, a_k) and C = B(a_j, a_k^dag).  flags gets FLAG_REAL when V
+// was written.
 __global__ void __launch_bounds__(256) k_intake(const MatDesc* __restrict__ mats, int check, int* __restrict__ flags) {
   const MatDesc D = mats[blockIdx.x];
   const int n = D.n, tot = n * (2 * n + 1);
-  __shared__ unsigned long long s_max, s_dev;
-  __shared__ int s_bad;
+  __shared__ unsigned long long s_max, s_dev, s_sdev;
+  __shared__ int s_bad, s_real;
   if (threadIdx.x == 0) {
     s_max = 0;
     s_dev = 0;
+    s_sdev = 0;
     s_bad = 0;
   }
   __syncthreads();
-  double mx = 0.0, dev = 0.0;
+  double mx = 0.0, dev = 0.0, sdev = 0.0;
   int bad = 0;
+  for (int e = threadIdx.x; e < 4 * n * n; e += blockDim.x) {
+    const int r = e / (2 * n), s = e % (2 * n);  // full matrix, pairs order
+    const double2 a = D.O[(size_t)src_row(D, r >> 1, r & 1) * D.ld + src_row(D, s >> 1, s & 1)];
+    const double2 b = D.O[(size_t)src_row(D, s >> 1, s & 1) * D.ld + src_row(D, r >> 1, r & 1)];
+    if (!isfinite(a.x) || !isfinite(a.y)) bad = 1;
+    mx = fmax(mx, fmax(fabs(a.x), fabs(a.y)));
+    dev = fmax(dev, fmax(fabs(a.x - b.x), fabs(a.y + b.y)));
+    // structure: compare with the entry of the opposite components of the same modes
+    const double2 c = D.O[(size_t)src_row(D, r >> 1, 1 - (r & 1)) * D.ld + src_row(D, s >> 1, 1 - (s & 1))];
+    sdev = fmax(sdev, fmax(fabs(a.x - c.x), fabs(a.y + c.y)));
+  }
+  // non-negative doubles order like their bit patterns (NaN compares as huge: fails the tests below)
+  atomicMax(&s_max, (unsigned long long)__double_as_longlong(mx));
+  atomicMax(&s_dev, (unsigned long long)__double_as_longlong(dev));
+  atomicMax(&s_sdev, (unsigned long long)__double_as_longlong(sdev));
+  if (bad) atomicOr(&s_bad, 1);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const double gmax = __longlong_as_double((long long)s_max);
+    const double gdev = __longlong_as_double((long long)s_dev), gsdev = __longlong_as_double((long long)s_sdev);
+    int f = 0;
+    if (s_bad) f |= FLAG_NONFINITE;
+    if (check && !(gdev <= 1e-12 * gmax)) f |= FLAG_NOTHERM;
+    const int real = D.real >= 0 ? D.real : (!s_bad && gsdev <= 1e-12 * gmax);
+    if (real) f |= FLAG_REAL;
+    s_real = real;
+    flags[blockIdx.x] = f;
+  }
+  __syncthreads();
+  const int real = s_real;
   for (int e = threadIdx.x; e < tot; e += blockDim.x) {
     int r = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f);
     while (P(r, 0) > e) --r;
     while (P(r + 1, 0) <= e) ++r;
     const int s = e - P(r, 0);
-    const int pr = src_row(D, r >> 1, r & 1), ps = src_row(D, s >> 1, s & 1);
-    const double2 a = D.O[(size_t)pr * D.ld + ps];
-    const double2 b = D.O[(size_t)ps * D.ld + pr];
-    if (!isfinite(a.x) || !isfinite(a.y) || !isfinite(b.x) || !isfinite(b.y)) bad = 1;
-    mx = fmax(mx, fmax(fmax(fabs(a.x), fabs(a.y)), fmax(fabs(b.x), fabs(b.y))));
-    dev = fmax(dev, fmax(fabs(a.x - b.x), fabs(a.y + b.y)));
-    if (!D.real) {
+    if (!real) {
+      const double2 a = D.O[(size_t)src_row(D, r >> 1, r & 1) * D.ld + src_row(D, s >> 1, s & 1)];
       D.B[e] = r == s ? make_double2(1.0 - a.x, 0.0) : make_double2(-a.x, -a.y);
     } else {
       const int j = r >> 1, k = s >> 1;
@@ -253,49 +283,6 @@ __global__ void __launch_bounds__(256) k_intake(const MatDesc* __restrict__ mats
       ((double*)D.B)[e] = v;
     }
   }
-  // non-negative doubles order like their bit patterns
-  atomicMax(&s_max, (unsigned long long)__double_as_longlong(mx));
-  atomicMax(&s_dev, (unsigned long long)__double_as_longlong(dev));
-  if (bad) atomicOr(&s_bad, 1);
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    int f = 0;
-    const double gmax = __longlong_as_double((long long)s_max), gdev = __longlong_as_double((long long)s_dev);
-    if (s_bad) f |= FLAG_NONFINITE;
-    if (check && !(gdev <= 1e-12 * gmax)) f |= FLAG_NOTHERM;
-    flags[blockIdx.x] = f;
-  }
-}
-
-// Is O structured, [[P, Q], [conj(Q), conj(P)]] in block layout (the form of a
-// physical Gaussian state), within 1e-12 max|O| entrywise?  One block per
-// matrix; out[i] = 1 if so.  Decides the real (x, p) path.
-__global__ void __launch_bounds__(256) k_structure(const MatDesc* __restrict__ mats, int* __restrict__ out) {
-  const MatDesc D = mats[blockIdx.x];
-  const int n = D.n;
-  __shared__ unsigned long long s_max, s_dev;
-  if (threadIdx.x == 0) {
-    s_max = 0;
-    s_dev = 0;
-  }
-  __syncthreads();
-  double mx = 0.0, dev = 0.0;
-  for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
-    const int j = e / n, k = e % n;
-    const double2 aa = D.O[(size_t)src_row(D, j, 0) * D.ld + src_row(D, k, 0)];
-    const double2 dd = D.O[(size_t)src_row(D, j, 1) * D.ld + src_row(D, k, 1)];
-    const double2 ac = D.O[(size_t)src_row(D, j, 0) * D.ld + src_row(D, k, 1)];
-    const double2 ca = D.O[(size_t)src_row(D, j, 1) * D.ld + src_row(D, k, 0)];
-    mx = fmax(mx, fmax(fmax(fmax(fabs(aa.x), fabs(aa.y)), fmax(fabs(dd.x), fabs(dd.y))),
-                       fmax(fmax(fabs(ac.x), fabs(ac.y)), fmax(fabs(ca.x), fabs(ca.y)))));
-    dev = fmax(dev, fmax(fmax(fabs(dd.x - aa.x), fabs(dd.y + aa.y)), fmax(fabs(ca.x - ac.x), fabs(ca.y + ac.y))));
-    if (!isfinite(dev) || !isfinite(mx)) dev = __longlong_as_double(0x7ff0000000000000ll);
-  }
-  atomicMax(&s_max, (unsigned long long)__double_as_longlong(mx));
-  atomicMax(&s_dev, (unsigned long long)__double_as_longlong(dev));
-  __syncthreads();
-  if (threadIdx.x == 0)
-    out[blockIdx.x] = __longlong_as_double((long long)s_dev) <= 1e-12 * __longlong_as_double((long long)s_max);
 }
 
 // Unit partial (hi, lo, abs).  For p < 5 the unit partials are the reduction leaves.
@@ -436,6 +423,17 @@ __device__ void run_task_lanes(const UnitsParams& prm, const TaskDesc T, int lan
   write_partial(prm, D, mat, u, acc, ab, bad);
 }
 
+// p < 5: each lane takes the arithmetic of its own matrix (the lanes of a task
+// share n and p; they diverge only if the batch mixes structured and general inputs).
+__device__ __forceinline__ void run_task_lanes_any(const UnitsParams& prm, const TaskDesc T, int lane, long long gw) {
+  const int p = prm.mats[T.mat].p;
+  const long long q = (long long)T.sub * kWarp + lane;
+  if (q >= ((long long)T.nmat << p)) return;
+  const int mat = T.mat + (int)(q >> p);
+  if (prm.mat_flags[mat] & FLAG_REAL) run_task_lanes<Real>(prm, T, lane, gw);
+  else run_task_lanes<Cplx>(prm, T, lane, gw);
+}
+
 constexpr int kUnitsThreads = 128;
 
 __global__ void __launch_bounds__(kUnitsThreads, 2) k_units(const UnitsParams prm) {
@@ -456,13 +454,11 @@ __global__ void __launch_bounds__(kUnitsThreads, 2) k_units(const UnitsParams pr
     t = __shfl_sync(0xffffffffu, t, 0);
     if (t >= (unsigned)prm.ntasks) break;
     const TaskDesc T = prm.tasks[t];
-    const MatDesc& D0 = prm.mats[T.mat];  // every matrix of a task has the same n, p and type
-    if (D0.real) {
-      if (D0.p >= 5) run_task_shared<Real>(prm, T, lane, gw);
-      else run_task_lanes<Real>(prm, T, lane, gw);
+    if (prm.mats[T.mat].p >= 5) {  // one matrix per task: the whole warp takes its arithmetic
+      if (prm.mat_flags[T.mat] & FLAG_REAL) run_task_shared<Real>(prm, T, lane, gw);
+      else run_task_shared<Cplx>(prm, T, lane, gw);
     } else {
-      if (D0.p >= 5) run_task_shared<Cplx>(prm, T, lane, gw);
-      else run_task_lanes<Cplx>(prm, T, lane, gw);
+      run_task_lanes_any(prm, T, lane, gw);
     }
     __syncwarp();
   }
@@ -542,11 +538,6 @@ __global__ void __launch_bounds__(256) k_probe(double* out, int iters) {
 cudaError_t launch_intake(const MatDesc* d_mats, int nmats, int check, int* d_flags, cudaStream_t s) {
   if (nmats <= 0) return cudaSuccess;
   k_intake<<<nmats, 256, 0, s>>>(d_mats, check, d_flags);
-  return cudaGetLastError();
-}
-cudaError_t launch_structure(const MatDesc* d_mats, int nmats, int* d_out, cudaStream_t s) {
-  if (nmats <= 0) return cudaSuccess;
-  k_structure<<<nmats, 256, 0, s>>>(d_mats, d_out);
   return cudaGetLastError();
 }
 cudaError_t launch_units(const UnitsParams& prm, int grid, cudaStream_t s) {

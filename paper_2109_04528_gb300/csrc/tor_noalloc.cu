@@ -131,6 +131,8 @@ __global__ void k_noalloc_finish(tor_result* out, int n) {
   r.abs_sum = q.abs_sum;
   r.err_est = 8.0 * n * 1.1102230246251565e-16 * q.abs_sum;
   r.n = n;
+  r.path = 0;
+  r.reserved = 0;
   if (q.flags & FLAG_NONFINITE) r.status = TOR_EINVAL;
   else if (q.flags & FLAG_NOTHERM) r.status = TOR_ENOTHERM;
   else if (abort_word & ABORT_CANCEL) r.status = TOR_ECANCELED;
