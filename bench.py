@@ -355,6 +355,8 @@ def main():
     ap.add_argument("--impl", default="libtor", choices=["libtor", "reference"])
     ap.add_argument("--cpu-budget", type=float, default=12.0, help="seconds of oracle time for cpu_baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--complex-path", action="store_true",
+                    help="evaluate every matrix in complex arithmetic (TOR_COMPLEX_PATH)")
     ap.add_argument("--autotune", type=float, default=0.0,
                     help="seconds for the prefix-depth autotuner before timing (0 = built-in plan)")
     ap.add_argument("--serve-window", type=float, default=2.0, help="serve: seconds of the overload window")
@@ -383,9 +385,10 @@ def main():
     stream = torch.cuda.Stream(device=device)
     dmats = [torch.from_numpy(m).to(device) for m in mats]
     # device-resident inputs, plain launches (per-kernel CUDA-event times for the roofline)
-    ctx_dev = binding.Context(device=local, stream=stream.cuda_stream, flags=binding.TOR_IN_DEVICE)
+    xf = binding.TOR_COMPLEX_PATH if args.complex_path else 0
+    ctx_dev = binding.Context(device=local, stream=stream.cuda_stream, flags=binding.TOR_IN_DEVICE | xf)
     # host inputs through the C ABI, replayed as a CUDA graph
-    ctx_host = binding.Context(device=local, stream=stream.cuda_stream, flags=binding.TOR_GRAPHS)
+    ctx_host = binding.Context(device=local, stream=stream.cuda_stream, flags=binding.TOR_GRAPHS | xf)
     tuned = None
     if args.autotune > 0:
         sizes = sorted(set(ns))
@@ -439,7 +442,7 @@ def main():
     # the same device-resident step replayed as a CUDA graph
     graph_ms = None
     with binding.Context(device=local, stream=stream.cuda_stream,
-                         flags=binding.TOR_IN_DEVICE | binding.TOR_GRAPHS) as ctx_g:
+                         flags=binding.TOR_IN_DEVICE | binding.TOR_GRAPHS | xf) as ctx_g:
         if tuned:
             ctx_g.load_plan(plan_file)
         timed(ctx_g, dmats, 2)
@@ -448,7 +451,8 @@ def main():
     plain = None
     if len(mats) > 8:
         # the plain GPU path: one tor_eval (launch + sync) per matrix, same kernels and plan
-        with binding.Context(device=local, stream=stream.cuda_stream, flags=binding.TOR_IN_DEVICE) as ctx_plain:
+        with binding.Context(device=local, stream=stream.cuda_stream,
+                             flags=binding.TOR_IN_DEVICE | xf) as ctx_plain:
             if tuned:
                 ctx_plain.load_plan(plan_file)
             for m in dmats[:64]:

@@ -74,7 +74,8 @@ _LIB = None
 
 
 def library_path() -> str:
-    return _build.library_path()
+    """The built library; the environment variable TOR_LIBRARY names another build to load."""
+    return os.environ.get("TOR_LIBRARY") or _build.library_path()
 
 
 def load_library():

@@ -436,7 +436,7 @@ __device__ __forceinline__ void run_task_lanes_any(const UnitsParams& prm, const
 
 constexpr int kUnitsThreads = 128;
 
-__global__ void __launch_bounds__(kUnitsThreads, 2) k_units(const UnitsParams prm) {
+__global__ void __launch_bounds__(kUnitsThreads, 4) k_units(const UnitsParams prm) {
   const int lane = threadIdx.x & (kWarp - 1);
   const long long gw = (long long)blockIdx.x * (blockDim.x / kWarp) + threadIdx.x / kWarp;
   const unsigned long long t0 = global_ns();
