@@ -1,0 +1,106 @@
+"""Floating-point operation counts of three ways to evaluate Eq. (tor), and
+the fit of the polynomial exponent omega of Sec. 3 (Eq. linear_fit):
+
+    omega ln N = ln(FLOs) - (N/2) ln 2 - C,      N = 2n (matrix size).
+
+The counts are exact sums over the subset trees, done combinatorially (no
+enumeration of the 2^n subsets), with one convention throughout: a complex
+multiply-add = 8 flops, a complex |x|^2 = 4, a complex-by-real division = 2,
+a real multiply or add = 1, sqrt / 1/sqrt = 1.
+
+  standard   every determinant by its own Cholesky decomposition (Algorithm 1),
+             Sec. 1 / Sec. 3 ("each determinant evaluated independently").
+  algorithm2 the paper's recursion (Algorithm 2): remove one mode per step,
+             reuse L11 and L21 of the parent factor, recompute L22 (Fig. 2).
+  rank2      this library's walk: include/exclude one mode per level, extend
+             the factor by the mode's two rows with a rank-2 Schur update of
+             the trailing block (right-looking), so the polynomial factor per
+             subset is O(1) amortised.
+"""
+from __future__ import annotations
+
+import math
+
+
+def cholesky_flops(rows: int, start: int = 0) -> int:
+    """Algorithm 1 on an m x m Hermitian matrix, computing rows start..m-1 only
+    (rows < start, and their columns in later rows, already known).
+
+    Entry (i, j), j < i: j complex MACs and one division; diagonal (i, i):
+    i |.|^2 updates, a subtraction and a sqrt.  Columns < start of rows
+    >= start are also reused (the L21 block)."""
+    f = 0
+    for i in range(start, rows):
+        for j in range(start, i):
+            f += 8 * j + 2
+        f += 4 * i + 1 + 1
+    return f
+
+
+def det_term_flops(rows: int) -> int:
+    """det = prod |L_ii|^2 (rows multiplies), 1/sqrt, sign and accumulation."""
+    return rows + 1 + 2
+
+
+def standard_flops(n: int) -> int:
+    """Sum over all subsets of an independent Cholesky of I - O_Z (2|Z| rows)."""
+    return sum(math.comb(n, k) * (cholesky_flops(2 * k) + det_term_flops(2 * k)) for k in range(n + 1))
+
+
+def algorithm2_flops(n: int) -> int:
+    """The remove-mode recursion of Algorithm 2.
+
+    Removing mode i from a node whose removed set R has r modes (all < i, the
+    recursion keeps removed indices increasing) leaves q_b = i - r kept modes
+    before i and q_a = n - 1 - i after it; the child's factor keeps its first
+    2 q_b rows and the L21 columns and recomputes the 2 q_a rows of L22.  The
+    number of such nodes is C(i, r)."""
+    f = cholesky_flops(2 * n) + det_term_flops(2 * n)  # root: L = chol(I - A)
+    for i in range(n):
+        for r in range(i + 1):
+            qb, qa = i - r, n - 1 - i
+            rows = 2 * (qb + qa)
+            f += math.comb(i, r) * (cholesky_flops(rows, 2 * qb) + det_term_flops(rows))
+    return f
+
+
+def rank2_flops(n: int) -> int:
+    """The add-direction rank-2 walk: at depth j the 2^j nodes include mode j
+    into a trailing block of m = n-1-j modes: pivot 10, pivot columns 40 m,
+    rank-2 update of the 2m x 2m lower triangle 32 m^2; every leaf 10."""
+    f = 10 * 2 ** n
+    for j in range(n):
+        m = n - 1 - j
+        f += 2 ** j * (32 * m * m + 40 * m + 10)
+    return f
+
+
+def fit_omega(counts: dict[int, int]) -> tuple[float, float]:
+    """Least-squares fit of Eq. (linear_fit): ln F - (N/2) ln 2 = omega ln N + C
+    over the given {N: FLOs}.  Returns (omega, C)."""
+    xs = [math.log(N) for N in counts]
+    ys = [math.log(F) - (N / 2) * math.log(2.0) for N, F in counts.items()]
+    k = len(xs)
+    mx, my = sum(xs) / k, sum(ys) / k
+    sxx = sum((x - mx) ** 2 for x in xs)
+    sxy = sum((x - mx) * (y - my) for x, y in zip(xs, ys))
+    omega = sxy / sxx
+    return omega, my - omega * mx
+
+
+def experiment(N_lo: int = 26, N_hi: int = 60):
+    """The Sec. 3 experiment on even N in [N_lo, N_hi]: omega of each method and
+    the standard / recursive ratios at N = 50 and N = 100."""
+    Ns = list(range(N_lo, N_hi + 1, 2))
+    out = {}
+    for name, fn in (("standard", standard_flops), ("algorithm2", algorithm2_flops), ("rank2", rank2_flops)):
+        out[name] = fit_omega({N: fn(N // 2) for N in Ns})[0]
+    out["ratio_std_alg2_N50"] = standard_flops(25) / algorithm2_flops(25)
+    out["ratio_std_alg2_N100"] = standard_flops(50) / algorithm2_flops(50)
+    out["ratio_alg2_rank2_N50"] = algorithm2_flops(25) / rank2_flops(25)
+    return out
+
+
+if __name__ == "__main__":
+    import json
+    print(json.dumps(experiment(), indent=1))
