@@ -65,33 +65,29 @@ def csrc_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(workload_name: str):
-    """DRAM bytes per k_units launch from the committed ncu capture, if it was
-    taken on this workload and on the kernel sources as they are now."""
+def profiled_traffic(workload_name: str, kernel: str = "k_units"):
+    """DRAM bytes per launch of `kernel` from the committed ncu capture, if it
+    was taken of that kernel on this workload and on the sources as they are now."""
     try:
         with open(os.path.join(ROOT, "profiles", "k_units_traffic.json")) as f:
             t = json.load(f)
     except (OSError, ValueError):
         return None
-    if t.get("workload") != workload_name or t.get("csrc_hash") != csrc_hash():
+    if t.get("workload") != workload_name or t.get("kernel") != kernel or t.get("csrc_hash") != csrc_hash():
         return None
     return t.get("dram_bytes_per_launch")
 
 
-def algorithmic_flops(n: int, real: bool = False) -> float:
-    """FP64 flops of the rank-2 subset-tree walk over all 2^n subsets.
-
-    Complex path: F(n) = sum_j 2^j (32 m_j^2 + 40 m_j + 10) + 10 2^n, m_j = n-1-j
-    (complex MAC = 8 flops, complex x real = 2, sqrt/rsqrt/div = 1).
-    Real (x, p) path, same convention (real FMA = 2): the update of the 2m x 2m
-    lower triangle costs 8 m^2 + 4 m, the pivot columns 8 m, the pivot 10:
-    F_real(n) = sum_j 2^j (8 m_j^2 + 12 m_j + 10) + 10 2^n."""
-    a, b = (8, 12) if real else (32, 40)
-    f = 10.0 * 2.0 ** n
-    for j in range(n):
-        m = n - 1 - j
-        f += 2.0 ** j * (a * m * m + b * m + 10)
-    return f
+def algorithmic_flops(n: int, path: int = 0) -> float:
+    """FP64 flops of the rank-2 subset-tree walk over all 2^n subsets in the
+    arithmetic the matrix took (tor_result.path).  FP64 complex path:
+    F(n) = sum_j 2^j (32 m_j^2 + 40 m_j + 10) + 10 2^n, m_j = n-1-j (complex
+    MAC = 8 flops, complex x real = 2, sqrt/rsqrt/div = 1); real (x, p) path
+    F_real(n) = sum_j 2^j (8 m_j^2 + 12 m_j + 10) + 10 2^n; the double-double
+    paths count every FP64 operation of the double-word algorithms
+    (paper_2109_04528_gb300.flops.path_flops)."""
+    from paper_2109_04528_gb300.flops import path_flops
+    return path_flops(n, path)
 
 
 class ClockSampler:
@@ -357,6 +353,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--complex-path", action="store_true",
                     help="evaluate every matrix in complex arithmetic (TOR_COMPLEX_PATH)")
+    ap.add_argument("--extended", action="store_true",
+                    help="double-double factor arithmetic (TOR_EXTENDED)")
     ap.add_argument("--autotune", type=float, default=0.0,
                     help="seconds for the prefix-depth autotuner before timing (0 = built-in plan)")
     ap.add_argument("--serve-window", type=float, default=2.0, help="serve: seconds of the overload window")
@@ -385,7 +383,7 @@ def main():
     stream = torch.cuda.Stream(device=device)
     dmats = [torch.from_numpy(m).to(device) for m in mats]
     # device-resident inputs, plain launches (per-kernel CUDA-event times for the roofline)
-    xf = binding.TOR_COMPLEX_PATH if args.complex_path else 0
+    xf = (binding.TOR_COMPLEX_PATH if args.complex_path else 0) | (binding.TOR_EXTENDED if args.extended else 0)
     ctx_dev = binding.Context(device=local, stream=stream.cuda_stream, flags=binding.TOR_IN_DEVICE | xf)
     # host inputs through the C ABI, replayed as a CUDA graph
     ctx_host = binding.Context(device=local, stream=stream.cuda_stream, flags=binding.TOR_GRAPHS | xf)
@@ -472,13 +470,14 @@ def main():
                  "what": "one blocking tor_eval per matrix (H2D descriptors, 3 kernels, D2H, sync), host-timed"}
     units_avg = sum(units_ms) / len(units_ms)
     # algorithmic flops of the arithmetic each matrix actually took
-    flops = float(sum(algorithmic_flops(n, paths.get(i, 0) == 1) for i, n in enumerate(ns)))
-    n_real = sum(1 for i in range(len(ns)) if paths.get(i, 0) == 1)
+    flops = float(sum(algorithmic_flops(n, paths.get(i, 0)) for i, n in enumerate(ns)))
+    n_real = sum(1 for i in range(len(ns)) if paths.get(i, 0) & 1)
+    ext = any(paths.get(i, 0) & 2 for i in range(len(ns)))
     achieved = flops / (units_avg * 1e-3) / 1e12
     line = {
         "metric": "subset terms/s", "value": value, "unit": "subset terms/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": tot_ms / args.steps,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64x2" if ext else "f64",
         "data": "synthetic",
         "config": {"workload": args.workload, "desc": desc, "n": ns, "terms_per_step": terms,
                    "l2": "flushed between steps (512 MB write)",
@@ -488,10 +487,13 @@ def main():
                 "h2d_bytes_per_step": int(sum(m.size * 16 for m in mats)),
                 "d2h_bytes_per_step": int(32 * len(mats))},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": fp64_tflops, "unit": "TFLOP/s",
-                     "frac": achieved / fp64_tflops, "traffic": profiled_traffic(args.workload),
-                     "kernel": "k_units", "peak_source": "FP64 DFMA probe (tor_probe_fp64), measured in this run",
+                     "frac": achieved / fp64_tflops,
+                     "traffic": profiled_traffic(args.workload, "k_units_ext" if ext else "k_units"),
+                     "kernel": "k_units_ext" if ext else "k_units",
+                     "peak_source": "FP64 DFMA probe (tor_probe_fp64), measured in this run",
                      "flops_per_launch": flops, "units_ms_avg": units_avg,
-                     "path": f"{n_real} of {len(ns)} matrices in the real (x,p) basis (F_real), rest complex (F)"},
+                     "path": f"{n_real} of {len(ns)} matrices in the real (x,p) basis, rest complex"
+                             + ("; double-double factor (every FP64 operation counted)" if ext else "")},
         "gpu_launches": 3 * args.steps,
         "clocks": clk.summary(),
     }

@@ -71,8 +71,15 @@ enum { TOR_LAYOUT_BLOCK = 0, TOR_LAYOUT_PAIRS = 1 };
  *                  evaluated in real arithmetic on V = U^H (I - O) U, U the per-mode
  *                  map from (a, a^dag) to the quadratures (x, p): every principal
  *                  block of V has the determinant of the matching block of I - O,
- *                  and the update costs a quarter of the complex multiply-adds. */
-enum { TOR_IN_DEVICE = 1u, TOR_NO_CHECK = 2u, TOR_GRAPHS = 4u, TOR_COMPLEX_PATH = 8u };
+ *                  and the update costs a quarter of the complex multiply-adds.
+ *   TOR_EXTENDED   extended-precision factor (paper Sec. 4, "X = extended"): B = I - O,
+ *                  every pivot, Schur-complement entry, determinant factor and term
+ *                  in double-double arithmetic (about 106-bit significands; the FP64
+ *                  path carries only the sum in double-double).  For weakly squeezed
+ *                  states, whose terms cancel almost completely, the error falls from
+ *                  ~1e-16 sum|term| to ~1e-30 sum|term|, at about 6x (real basis) to
+ *                  13x (complex) the FP64 instructions per term. */
+enum { TOR_IN_DEVICE = 1u, TOR_NO_CHECK = 2u, TOR_GRAPHS = 4u, TOR_COMPLEX_PATH = 8u, TOR_EXTENDED = 16u };
 
 /* tor_session_create kinds */
 enum { TOR_SESSION_SIGMA = 0, TOR_SESSION_O = 1 };
@@ -93,10 +100,11 @@ typedef struct {
 typedef struct {
   double hi, lo;       /* Tor as an unevaluated double-double sum hi + lo */
   double abs_sum;      /* sum over all subsets of |term|: the scale of the rounding error */
-  double err_est;      /* a-priori error estimate 8 n u abs_sum, u = 2^-53 */
+  double err_est;      /* a-priori error estimate 8 n u abs_sum, u = 2^-53 (2^-104 extended) */
   int n;               /* modes of this matrix */
   tor_status status;   /* per-matrix status */
-  int path;            /* arithmetic used: 0 complex, 1 real (x, p) basis (TOR_COMPLEX_PATH) */
+  int path;            /* arithmetic used: bit 0 real (x, p) basis (else complex, see
+                          TOR_COMPLEX_PATH), bit 1 double-double factor (TOR_EXTENDED) */
   int reserved;
 } tor_result;
 
@@ -272,7 +280,7 @@ tor_status tor_probe_fp64(int device, double seconds, double* dfma_per_s, double
  * arguments (n < 1, NULL pointers, ld < 2n, unknown layout or device),
  * TOR_ECUDA if a launch fails.
  *
- * All intermediate data lives in one static device array of 8 MiB compiled
+ * All intermediate data lives in one static device array of 12 MiB compiled
  * into the library, which every device that loads the library keeps until
  * the process exits.  Calls share it: calls whose GPU work overlaps (other
  * streams or threads on the same device) race and must be ordered by the

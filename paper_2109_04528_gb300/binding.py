@@ -19,7 +19,7 @@ TOR_OK, TOR_EINVAL, TOR_ENOTHERM, TOR_ENOTPD, TOR_ENOMEM, TOR_EAGAIN, TOR_ETIMEO
 STATUS_NAMES = ["TOR_OK", "TOR_EINVAL", "TOR_ENOTHERM", "TOR_ENOTPD", "TOR_ENOMEM", "TOR_EAGAIN",
                 "TOR_ETIMEOUT", "TOR_ECANCELED", "TOR_ECUDA", "TOR_ETOOBIG"]
 TOR_LAYOUT_BLOCK, TOR_LAYOUT_PAIRS = 0, 1
-TOR_IN_DEVICE, TOR_NO_CHECK, TOR_GRAPHS, TOR_COMPLEX_PATH = 1, 2, 4, 8
+TOR_IN_DEVICE, TOR_NO_CHECK, TOR_GRAPHS, TOR_COMPLEX_PATH, TOR_EXTENDED = 1, 2, 4, 8, 16
 TOR_SESSION_SIGMA, TOR_SESSION_O = 0, 1
 
 # Every symbol include/tor.h declares (the ABI test checks the library exports them).
@@ -59,7 +59,7 @@ class TorResult:
     err_est: float
     n: int
     status: int
-    path: int = 0  # 0 complex, 1 real (x, p) basis
+    path: int = 0  # bit 0: real (x, p) basis (else complex); bit 1: double-double factor
 
     @property
     def tor(self) -> float:

@@ -14,7 +14,7 @@
 // (all n modes decided, included set Z) contributes (-1)^{n-|Z|} phi_Z
 // (Eq. tor).
 //
-// Two scalar types run the same tree:
+// Four scalar types run the same tree:
 //   Cplx  complex128 entries: any Hermitian O with I - O positive definite.
 //   Real  float64 entries: O of a physical Gaussian state, which has the form
 //         [[P, Q], [conj(Q), conj(P)]] in block layout.  The per-mode unitary
@@ -23,6 +23,11 @@
 //         principal block of V has the determinant of the matching block of B
 //         (|det U| = 1), so the whole tree can run in real arithmetic at a
 //         quarter of the multiply-adds.
+//   CplxX, RealX  the same two in double-double arithmetic (about 106-bit
+//         significands): the extended-precision factor of Sec. 4, where the
+//         pivots, the Schur updates, phi and every term are carried in
+//         double-double (tor_dd.cuh).
+// Each type names its real scalar Re (double or dd_t) and its accumulator Acc.
 //
 // Storage of a symmetric / Hermitian matrix: packed lower triangle, element
 // (r, s), r >= s, at index P(r, s) = r (r + 1) / 2 + s.  Diagonal entries are
@@ -95,29 +100,53 @@ struct DD {
     c = __dadd_rn(c, e);
   }
 };
-// (ah, al) + (bh, bl) -> normalised double-double
+// (ah, al) + (bh, bl) -> normalised double-double, relative error <= 3 u^2
+// also under cancellation (Joldes, Muller, Popescu, "Tight and rigorous error
+// bounds for basic building blocks of double-word arithmetic", ACM TOMS 44
+// (2017), AccurateDWPlusDW).
 __device__ __forceinline__ void dd_add(double ah, double al, double bh, double bl, double& h, double& l) {
-  double s, e;
+  double s, e, t, f;
   two_sum(ah, bh, s, e);
-  e = __dadd_rn(e, __dadd_rn(al, bl));
+  two_sum(al, bl, t, f);
+  e = __dadd_rn(e, t);
+  fast_two_sum(s, e, s, e);
+  e = __dadd_rn(e, f);
   fast_two_sum(s, e, h, l);
 }
 
 // ---------------------------------------------------------------------------
 // Scalar types.  Each provides the operations of the include step:
-//   abs2(b)              |b|^2
+//   det2(a, b, e)        a e - |b|^2 (determinant of the 2x2 pivot block)
 //   cl(b, ia)            conj(l) = conj(b) / a          (l = b / a)
 //   reduce_col(x, y, cl) y' = y - x conj(l)
 //   scale(v, s)          v s
 //   rank2_off(s, xt, xk, yt, yk)   s - xt conj(xk) - yt conj(yk)
 //   rank2_diag(d, xt, x, yt, y)    d - Re(xt conj(x)) - Re(yt conj(y))
 //   re(v), diag(d)       real part; the stored form of a real diagonal entry
+// and, on its real scalar Re: mul, sub, neg, pos (> 0), rcp, rsqrt, hi (the
+// leading double), one, shfl (warp broadcast from a lane).
 // ---------------------------------------------------------------------------
-struct Cplx {
+struct Fp64Re {  // real scalar operations of the two FP64 types
+  using Re = double;
+  using Acc = DD;
+  static __device__ __forceinline__ double mul(double a, double b) { return a * b; }
+  static __device__ __forceinline__ double sub(double a, double b) { return a - b; }
+  static __device__ __forceinline__ double neg(double a) { return -a; }
+  static __device__ __forceinline__ bool pos(double a) { return a > 0.0; }
+  static __device__ __forceinline__ double rcp(double a) { return rcp64(a); }
+  static __device__ __forceinline__ double rsqrt(double a) { return rsqrt64(a); }
+  static __device__ __forceinline__ double hi(double a) { return a; }
+  static __device__ __forceinline__ double one() { return 1.0; }
+  static __device__ __forceinline__ double shfl(double a, int q) { return __shfl_sync(0xffffffffu, a, q); }
+  static __device__ __forceinline__ Acc acc0() { return DD{0.0, 0.0}; }
+  static __device__ __forceinline__ void acc_out(const Acc& a, double& h, double& l) { fast_two_sum(a.s, a.c, h, l); }
+};
+struct Cplx : Fp64Re {
   using T = double2;
   static __device__ __forceinline__ double re(T v) { return v.x; }
   static __device__ __forceinline__ T diag(double d) { return make_double2(d, 0.0); }
   static __device__ __forceinline__ double abs2(T b) { return fma(b.x, b.x, b.y * b.y); }
+  static __device__ __forceinline__ double det2(double a, T b, double e) { return fma(a, e, -abs2(b)); }
   static __device__ __forceinline__ T cl(T b, double ia) { return make_double2(b.x * ia, -b.y * ia); }
   static __device__ __forceinline__ T reduce_col(T x, T y, T c) {
     T r;
@@ -147,11 +176,12 @@ struct Cplx {
     return d;
   }
 };
-struct Real {
+struct Real : Fp64Re {
   using T = double;
   static __device__ __forceinline__ double re(T v) { return v; }
   static __device__ __forceinline__ T diag(double d) { return d; }
   static __device__ __forceinline__ double abs2(T b) { return b * b; }
+  static __device__ __forceinline__ double det2(double a, T b, double e) { return fma(a, e, -abs2(b)); }
   static __device__ __forceinline__ T cl(T b, double ia) { return b * ia; }
   static __device__ __forceinline__ T reduce_col(T x, T y, T c) { return fma(-x, c, y); }
   static __device__ __forceinline__ T scale(T v, double s) { return v * s; }
@@ -173,21 +203,23 @@ struct Real {
 // ---------------------------------------------------------------------------
 template <class S>
 struct Pivot {
-  double ia;         // 1 / d1
-  double id2;        // 1 / d2 = a rho^2
-  double rho;        // (a e - |b|^2)^{-1/2}
+  using Re = typename S::Re;
+  Re ia;             // 1 / d1
+  Re id2;            // 1 / d2 = a rho^2
+  Re rho;            // (a e - |b|^2)^{-1/2}
   typename S::T cl;  // conj(l) = conj(b) / a
   bool ok;           // d1 > 0 and d1 d2 > 0: the block is positive definite
 };
 template <class S>
-__device__ __forceinline__ Pivot<S> make_pivot(double a, typename S::T b, double e) {
+__device__ __forceinline__ Pivot<S> make_pivot(typename S::Re a, typename S::T b, typename S::Re e) {
+  using Re = typename S::Re;
   Pivot<S> pv;
-  const double det2 = fma(a, e, -S::abs2(b));
-  pv.ok = (a > 0.0) && (det2 > 0.0);
-  pv.rho = rsqrt64(det2);
-  pv.ia = rcp64(a);
+  const Re det2 = S::det2(a, b, e);
+  pv.ok = S::pos(a) && S::pos(det2);
+  pv.rho = S::rsqrt(det2);
+  pv.ia = S::rcp(a);
   pv.cl = S::cl(b, pv.ia);
-  pv.id2 = a * (pv.rho * pv.rho);
+  pv.id2 = S::mul(a, S::mul(pv.rho, pv.rho));
   return pv;
 }
 
@@ -200,7 +232,7 @@ __host__ __device__ constexpr int TI(int i, int k) { return (i * (i - 1)) / 2 + 
 
 template <class S, int R>
 struct HM {
-  double d[R];
+  typename S::Re d[R];
   typename S::T o[(R * (R - 1)) / 2];
 };
 
@@ -217,7 +249,7 @@ __device__ __forceinline__ void hm_trail(const HM<S, R>& A, HM<S, R - 2>& C) {
 
 // Include the first mode: C = Schur complement, returns rho.
 template <class S, int R>
-__device__ __forceinline__ double hm_include(const HM<S, R>& A, HM<S, R - 2>& C, bool& bad) {
+__device__ __forceinline__ typename S::Re hm_include(const HM<S, R>& A, HM<S, R - 2>& C, bool& bad) {
   using T = typename S::T;
   const Pivot<S> pv = make_pivot<S>(A.d[0], A.o[TI(1, 0)], A.d[1]);
   bad |= !pv.ok;
@@ -240,35 +272,40 @@ __device__ __forceinline__ double hm_include(const HM<S, R>& A, HM<S, R - 2>& C,
 // One mode left (2 x 2 node): its two leaves, exclude (-phi) and include
 // (+phi rho).  v = signed sum, ab = sum of magnitudes.
 template <class S>
-__device__ __forceinline__ void leaf_pair(double a, typename S::T b, double e, double phi, double& v, double& ab,
-                                          bool& bad) {
-  const double det2 = fma(a, e, -S::abs2(b));
-  bad |= !((a > 0.0) && (det2 > 0.0));
-  const double pr = phi * rsqrt64(det2);
-  v = pr - phi;
-  ab = pr + phi;
+__device__ __forceinline__ void leaf_pair(typename S::Re a, typename S::T b, typename S::Re e, typename S::Re phi,
+                                          typename S::Re& v, double& ab, bool& bad) {
+  using Re = typename S::Re;
+  const Re det2 = S::det2(a, b, e);
+  bad |= !(S::pos(a) && S::pos(det2));
+  const Re pr = S::mul(phi, S::rsqrt(det2));
+  v = S::sub(pr, phi);
+  ab = S::hi(pr) + S::hi(phi);
 }
 
 // Sum over the 2^(R/2) leaves below a register node:
 //   v = sum (-1)^{#modes excluded below this node} phi_leaf,  ab = sum phi_leaf.
 template <class S, int R>
 struct Subtree {
-  static __device__ __forceinline__ void run(const HM<S, R>& A, double phi, double& v, double& ab, bool& bad) {
+  using Re = typename S::Re;
+  static __device__ __forceinline__ void run(const HM<S, R>& A, Re phi, Re& v, double& ab, bool& bad) {
     HM<S, R - 2> E;
     hm_trail<S, R>(A, E);
-    double v1, a1;
+    Re v1;
+    double a1;
     Subtree<S, R - 2>::run(E, phi, v1, a1, bad);
     HM<S, R - 2> I;
-    const double rho = hm_include<S, R>(A, I, bad);
-    double v2, a2;
-    Subtree<S, R - 2>::run(I, phi * rho, v2, a2, bad);
-    v = v2 - v1;
+    const Re rho = hm_include<S, R>(A, I, bad);
+    Re v2;
+    double a2;
+    Subtree<S, R - 2>::run(I, S::mul(phi, rho), v2, a2, bad);
+    v = S::sub(v2, v1);
     ab = a1 + a2;
   }
 };
 template <class S>
 struct Subtree<S, 2> {
-  static __device__ __forceinline__ void run(const HM<S, 2>& A, double phi, double& v, double& ab, bool& bad) {
+  using Re = typename S::Re;
+  static __device__ __forceinline__ void run(const HM<S, 2>& A, Re phi, Re& v, double& ab, bool& bad) {
     leaf_pair<S>(A.d[0], A.o[0], A.d[1], phi, v, ab, bad);
   }
 };
@@ -284,7 +321,7 @@ struct LaneMem {
   typename S::T* p;  // lane's element 0 (= warp region + lane)
   __device__ __forceinline__ typename S::T ld(int e) const { return p[(size_t)e * kWarp]; }
   __device__ __forceinline__ void st(int e, typename S::T v) const { p[(size_t)e * kWarp] = v; }
-  __device__ __forceinline__ double ldd(int e) const { return S::re(ld(e)); }
+  __device__ __forceinline__ typename S::Re ldd(int e) const { return S::re(ld(e)); }
 };
 
 // Load the trailing 6 x 6 block of a node with 4 modes (exclude its first mode).
@@ -299,7 +336,7 @@ __device__ __forceinline__ void lane_load_trail4(const LaneMem<S> L, int src, in
 }
 // Include the first mode of a 4-mode node in memory; child (3 modes) in registers.
 template <class S>
-__device__ __forceinline__ double lane_include4(const LaneMem<S> L, int src, int o, HM<S, 6>& C, bool& bad) {
+__device__ __forceinline__ typename S::Re lane_include4(const LaneMem<S> L, int src, int o, HM<S, 6>& C, bool& bad) {
   using T = typename S::T;
   const Pivot<S> pv = make_pivot<S>(L.ldd(src + P(o, o)), L.ld(src + P(o + 1, o)), L.ldd(src + P(o + 1, o + 1)));
   bad |= !pv.ok;

@@ -210,6 +210,16 @@ struct tor_ctx {
   std::vector<tor_session*> sessions;  // live sessions of this context (guarded by q_mu)
 };
 
+// Bytes of one matrix entry the kernels may use: complex128, or a complex
+// double-double in extended precision (TOR_EXTENDED); and of one lane-scratch
+// element (a real and a complex area side by side).
+static size_t entry_bytes(const tor_ctx* ctx) {
+  return (ctx->cfg.flags & TOR_EXTENDED) ? kWarpEntryBytesExt : kWarpEntryBytes;
+}
+static size_t lane_entry_bytes(const tor_ctx* ctx) {
+  return (ctx->cfg.flags & TOR_EXTENDED) ? kLaneEntryBytesExt : kLaneEntryBytes;
+}
+
 // Last error of a call that had no context to record it in (tor_create).
 static thread_local std::string g_create_error;
 
@@ -285,9 +295,11 @@ static size_t job_bytes(tor_ctx* ctx, const std::vector<MatIn>& ins, size_t coun
     lane_e = std::max(lane_e, lane_elems_for(m.n, p));
     warp_e = std::max(warp_e, warp_elems_for(m.n, p));
   }
-  return (size_t)(o * 16 + b * 16 + parts * 32 + md * 4 + ntask * (long long)sizeof(TaskDesc) +
+  const size_t eb = entry_bytes(ctx);
+  return (size_t)(o * 16 + parts * 32 + md * 4 + ntask * (long long)sizeof(TaskDesc) +
                   (long long)count * (long long)(sizeof(MatDesc) + sizeof(ResultRec) + 4)) +
-         (size_t)ctx->nwarps * 32 * lane_e * 16 + (size_t)ctx->nwarps * warp_e * 16 + 4096;
+         (size_t)b * eb + (size_t)ctx->nwarps * 32 * lane_e * lane_entry_bytes(ctx) +
+         (size_t)ctx->nwarps * warp_e * eb + 4096;
 }
 
 // Validates the inputs, fills trivial results, plans the job and fills the
@@ -335,6 +347,7 @@ static tor_status slot_prepare(tor_ctx* ctx, Slot& S, const std::vector<MatIn>& 
     D.p = p;
     // the arithmetic: forced complex, known (sessions), or detected by k_intake
     D.real = (ctx->cfg.flags & TOR_COMPLEX_PATH) ? 0 : m.real_hint;
+    D.ext = (ctx->cfg.flags & TOR_EXTENDED) ? 1 : 0;
     D.layout = m.layout;
     D.n_src = m.modes ? m.n_src : m.n;
     D.part_off = S.parts;
@@ -376,8 +389,9 @@ static tor_status slot_prepare(tor_ctx* ctx, Slot& S, const std::vector<MatIn>& 
   std::stable_sort(S.tasks.begin(), S.tasks.end(), [](const TaskDesc& a, const TaskDesc& b) { return a.M > b.M; });
   S.want_parts = want_parts;
   // buffers
-  const size_t lane_bytes = (size_t)ctx->nwarps * 32 * S.lane_e * sizeof(double2);
-  const size_t warp_bytes = (size_t)ctx->nwarps * S.warp_e * sizeof(double2);
+  const size_t eb = entry_bytes(ctx);
+  const size_t lane_bytes = (size_t)ctx->nwarps * 32 * S.lane_e * lane_entry_bytes(ctx);
+  const size_t warp_bytes = (size_t)ctx->nwarps * S.warp_e * eb;
   S.bytes = job_bytes(ctx, ins, ins.size());
   if (ctx->cfg.mem_budget && S.bytes > ctx->cfg.mem_budget) {
     for (int j = 0; j < J; ++j) out[S.act[j]].status = TOR_ENOMEM;
@@ -387,7 +401,7 @@ static tor_status slot_prepare(tor_ctx* ctx, Slot& S, const std::vector<MatIn>& 
   }
   uint64_t* g = &S.gen;
   CK(S.d_O.ensure(S.o_elems * 16, g), "alloc O");
-  CK(S.d_B.ensure(S.b_elems * 16, g), "alloc B");
+  CK(S.d_B.ensure(S.b_elems * eb, g), "alloc B");
   CK(S.d_partials.ensure((S.parts + S.reds) * 32, g), "alloc partials");
   CK(S.d_mats.ensure(J * sizeof(MatDesc), g), "alloc mats");
   CK(S.d_tasks.ensure(S.tasks.size() * sizeof(TaskDesc), g), "alloc tasks");
@@ -432,7 +446,7 @@ static tor_status slot_prepare(tor_ctx* ctx, Slot& S, const std::vector<MatIn>& 
       oo += (long long)mm * mm;
     }
     D.B = dB + bo;
-    bo += tri(m.n);
+    bo += tri(m.n) * (long long)(eb / sizeof(double2));
   }
   memcpy(S.h_mats.p, S.mats.data(), J * sizeof(MatDesc));
   memcpy(S.h_tasks.p, S.tasks.data(), S.tasks.size() * sizeof(TaskDesc));
@@ -470,7 +484,7 @@ static tor_status rec_front(tor_ctx* ctx, Slot& S, bool timed) {
 // One launch of k_units; with slice_ns > 0 it stops taking tasks after that
 // long and copies (ticket, abort word) to h_ctl so the host can relaunch it.
 static tor_status rec_units(tor_ctx* ctx, Slot& S, long long slice_ns) {
-  UnitsParams prm;
+  UnitsParams prm{};
   prm.mats = (const MatDesc*)S.d_mats.p;
   prm.tasks = (const TaskDesc*)S.d_tasks.p;
   prm.ntasks = (int)S.tasks.size();
@@ -487,6 +501,7 @@ static tor_status rec_units(tor_ctx* ctx, Slot& S, long long slice_ns) {
   prm.cancel_epoch = S.cancel_epoch;
   prm.budget_ns = ctx->cfg.timeout_s > 0 ? (long long)(ctx->cfg.timeout_s * 1e9) : 0;
   prm.slice_ns = slice_ns;
+  prm.ext = (ctx->cfg.flags & TOR_EXTENDED) ? 1 : 0;
   CK(launch_units(prm, ctx->grid, S.stream), "k_units");
   if (slice_ns > 0) {
     CK(cudaMemcpyAsync(S.h_ctl.p, S.d_ctl.p, 2 * sizeof(int), cudaMemcpyDeviceToHost, S.stream), "D2H ticket");
@@ -532,7 +547,7 @@ static tor_status slot_launch(tor_ctx* ctx, Slot& S) {
   uint64_t key = mix(0, (uint64_t)S.J);
   for (const MatDesc& D : S.mats)
     key = mix(key, (uint64_t)D.n | (uint64_t)D.p << 8 | (uint64_t)D.n_src << 16 | (uint64_t)D.layout << 28 |
-                       (uint64_t)(D.modes != nullptr) << 29 | (uint64_t)D.real << 30);
+                       (uint64_t)(D.modes != nullptr) << 29 | (uint64_t)D.real << 30 | (uint64_t)D.ext << 33);
   for (const MatDesc& D : S.mats) key = mix(key, (uint64_t)D.red_lo << 8 ^ (uint64_t)D.red_log2);
   key = mix(key, (uint64_t)S.o_elems);
   key = mix(key, (uint64_t)S.mode_elems);
@@ -587,8 +602,8 @@ static tor_status slot_finish(Slot& S, tor_result* out, double* unit_partials, d
     r.hi = q.hi;
     r.lo = q.lo;
     r.abs_sum = q.abs_sum;
-    r.err_est = 8.0 * r.n * std::ldexp(1.0, -53) * q.abs_sum;
-    r.path = (q.flags & FLAG_REAL) ? 1 : 0;
+    r.err_est = 8.0 * r.n * std::ldexp(1.0, S.mats[j].ext ? -104 : -53) * q.abs_sum;
+    r.path = ((q.flags & FLAG_REAL) ? 1 : 0) | (S.mats[j].ext ? 2 : 0);
     if (q.flags & FLAG_NONFINITE) r.status = TOR_EINVAL;
     else if (q.flags & FLAG_NOTHERM) r.status = TOR_ENOTHERM;
     else if (abort_word & ABORT_CANCEL) r.status = TOR_ECANCELED;
@@ -977,7 +992,8 @@ tor_status tor_create(const tor_config* cfg, tor_ctx** out) {
   if ((e = cudaSetDevice(c.device)) != cudaSuccess) return fail(e, "cudaSetDevice");
   if ((e = cudaDeviceGetAttribute(&ctx->sms, cudaDevAttrMultiProcessorCount, c.device)) != cudaSuccess)
     return fail(e, "attribute");
-  if ((e = units_blocks_per_sm(&ctx->blocks_per_sm)) != cudaSuccess) return fail(e, "occupancy");
+  if ((e = units_blocks_per_sm(&ctx->blocks_per_sm, (c.flags & TOR_EXTENDED) ? 1 : 0)) != cudaSuccess)
+    return fail(e, "occupancy");
   ctx->blocks_per_sm = std::max(1, ctx->blocks_per_sm);
   ctx->grid = ctx->sms * ctx->blocks_per_sm;
   ctx->nwarps = ctx->grid * (units_block_threads() / 32);

@@ -15,12 +15,14 @@ struct MatDesc {
   const double2* O;     // source matrix on the device (row-major, leading dimension ld)
   const int* modes;     // device list of the n source modes to keep, or null (modes 0..n-1)
   double2* B;           // packed lower triangle of B = I - O in pairs order, n(2n+1) entries
+                        // (twice as many double2 when ext)
   long long part_off;   // first of this matrix's 2^p unit partials
   long long red_off;    // first of this matrix's reduction leaves (task partials if p >= 5, else unit partials)
   int red_log2;         // log2 of the number of reduction leaves: p - 5 if p >= 5, else p
   int n, p, ld, layout;
   int n_src;            // modes of the source matrix (n unless `modes` selects a submatrix)
   int real;             // -1: let k_intake detect the structure; 0: complex; 1: real (x, p) path
+  int ext;              // 1: double-double arithmetic (B holds ddc_t / dd_t entries), k_units_ext
   long long red_lo;     // first reduction leaf this job evaluates (tor_eval_range); 0 otherwise
 };
 
@@ -33,6 +35,13 @@ struct TaskDesc {
 };
 
 enum { FLAG_NOTPD = 1, FLAG_NOTHERM = 2, FLAG_NONFINITE = 4, FLAG_REAL = 8 };
+
+// Scratch bytes per counted element.  Lane scratch: a warp's region holds a
+// real-entry area and a complex-entry area (float64 + complex128, or their
+// double-double forms), since the lanes of one task may take either; warp
+// (task-node) scratch: one complex entry.
+constexpr int kLaneEntryBytes = 8 + 16, kLaneEntryBytesExt = 16 + 32;
+constexpr int kWarpEntryBytes = 16, kWarpEntryBytesExt = 32;
 enum { ABORT_TIMEOUT = 1, ABORT_CANCEL = 2 };
 
 struct UnitsParams {
@@ -43,9 +52,9 @@ struct UnitsParams {
   Part* partials;              // (hi, lo, abs_sum, 0) per unit
   Part* red_leaves;            // per warp task (p >= 5: its 32 units summed by a fixed lane tree) or per unit
   int* mat_flags;              // FLAG_* per matrix
-  double2* lane_scratch;       // per warp: 32 * lane_elems, lane-interleaved
+  double2* lane_scratch;       // per warp: 32 * lane_elems * kLaneEntryBytes(Ext) bytes, lane-interleaved
   long long lane_elems;
-  double2* warp_scratch;       // per warp: warp_elems, contiguous
+  double2* warp_scratch;       // per warp: warp_elems * kWarpEntryBytes(Ext) bytes, contiguous
   long long warp_elems;
   const volatile int* cancel;  // host-mapped cancel counter
   int cancel_epoch;            // its value when the job started; a change = stop
@@ -53,6 +62,7 @@ struct UnitsParams {
   long long slice_ns;          // > 0: warps stop taking tasks after this long (no abort); the host
                                // relaunches the kernel, which continues from the ticket
   int* abort_word;             // ABORT_* bits set by the kernel
+  int ext;                     // 1: launch k_units_ext (double-double entries)
 };
 
 struct ResultRec {
@@ -69,7 +79,7 @@ cudaError_t launch_units(const UnitsParams& prm, int grid, cudaStream_t s);
 cudaError_t launch_reduce(const MatDesc* d_mats, int nmats, const Part* partials, const int* flags,
                           ResultRec* out, cudaStream_t s);
 int units_block_threads();
-cudaError_t units_blocks_per_sm(int* blocks);
+cudaError_t units_blocks_per_sm(int* blocks, int ext);
 cudaError_t run_probe_fp64(double seconds, double* dfma_per_s);
 
 }  // namespace tor

@@ -5,9 +5,11 @@
 //               for structured O; Hermitian / finite checks.
 //   k_units   : persistent warps; each warp task evaluates 32 units (prefix
 //               subtrees) of the tree of Algorithm 2, one unit per lane.
+//   k_units_ext : the same in double-double arithmetic (extended precision).
 //   k_reduce  : fixed-shape binary tree over each matrix's task partials (each
 //               already a fixed lane tree over 32 units), in double-double.
 //   k_probe   : FP64 FMA throughput probe (the roofline's denominator).
+#include "tor_dd.cuh"
 #include "tor_device.cuh"
 #include "tor_internal.h"
 
@@ -51,8 +53,8 @@ __device__ __forceinline__ unsigned long long global_ns() {
 // child (m-1 modes) to (dst, dst_o).  In place when dst == src and
 // dst_o == o + 2.  xs/ys: scratch of 2(m-1) elements each.  Returns rho.
 template <class S>
-__device__ __noinline__ double lane_include_mem(const LaneMem<S> L, int src, int o, int m, int dst, int dst_o,
-                                                int xs, int ys, bool& bad) {
+__device__ __noinline__ typename S::Re lane_include_mem(const LaneMem<S> L, int src, int o, int m, int dst,
+                                                        int dst_o, int xs, int ys, bool& bad) {
   using T = typename S::T;
   const Pivot<S> pv = make_pivot<S>(L.ldd(src + P(o, o)), L.ld(src + P(o + 1, o)), L.ldd(src + P(o + 1, o + 1)));
   bad |= !pv.ok;
@@ -79,8 +81,8 @@ __device__ __noinline__ double lane_include_mem(const LaneMem<S> L, int src, int
 // part of the tree, where nodes are large.  All lanes compute the pivot; the
 // call ends with __syncwarp so the child is visible to every lane.
 template <class S>
-__device__ __noinline__ double coop_include(const typename S::T* src, int o, int m, typename S::T* dst, int dst_o,
-                                            typename S::T* xs, typename S::T* ys, bool& bad) {
+__device__ __noinline__ typename S::Re coop_include(const typename S::T* src, int o, int m, typename S::T* dst,
+                                                    int dst_o, typename S::T* xs, typename S::T* ys, bool& bad) {
   using T = typename S::T;
   const int lane = threadIdx.x & (kWarp - 1);
   const Pivot<S> pv = make_pivot<S>(S::re(src[P(o, o)]), src[P(o + 1, o)], S::re(src[P(o + 1, o + 1)]));
@@ -135,11 +137,14 @@ __device__ __noinline__ double coop_include(const typename S::T* src, int o, int
 // overwritten while a pending include still needs it.  The 3-mode nodes and
 // everything below them live in registers.
 template <class S>
-__device__ __noinline__ void lane_dfs(const LaneMem<S> L, int root, int root_o, int M, int n, double phi_root,
-                                      int incl_root, int buf4, int xs, int ys, DD& acc, double& ab, bool& bad) {
+__device__ __noinline__ void lane_dfs(const LaneMem<S> L, int root, int root_o, int M, int n,
+                                      typename S::Re phi_root, int incl_root, int buf4, int xs, int ys,
+                                      typename S::Acc& acc, double& ab, bool& bad) {
+  using Re = typename S::Re;
   if (M <= 3) {
     const int excl_above = (n - M) - incl_root;
-    double v = 0.0, a = 0.0;
+    Re v{};
+    double a = 0.0;
     if (M == 1) {
       HM<S, 2> R2;
       lane_load_node<S, 2>(L, root, root_o, R2);
@@ -153,13 +158,13 @@ __device__ __noinline__ void lane_dfs(const LaneMem<S> L, int root, int root_o, 
       lane_load_node<S, 6>(L, root, root_o, R6);
       Subtree<S, 6>::run(R6, phi_root, v, a, bad);
     }
-    if (excl_above & 1) v = -v;
+    if (excl_above & 1) v = S::neg(v);
     acc.add(v);
     ab += a;
     return;
   }
   int nb[65], nof[65];
-  double ph[65];
+  Re ph[65];
   nb[M] = root;
   nof[M] = root_o;
   ph[M] = phi_root;
@@ -173,10 +178,10 @@ __device__ __noinline__ void lane_dfs(const LaneMem<S> L, int root, int root_o, 
     if (c != 0 && (c & 1ull) == 0) {
       const int mi = 4 + __ffsll((long long)c) - 1;
       const int dst = buf4 + stack_off(mi - 1);
-      const double rho = lane_include_mem<S>(L, nb[mi], nof[mi], mi, dst, 0, xs, ys, bad);
+      const Re rho = lane_include_mem<S>(L, nb[mi], nof[mi], mi, dst, 0, xs, ys, bad);
       nb[mi - 1] = dst;
       nof[mi - 1] = 0;
-      ph[mi - 1] = ph[mi] * rho;
+      ph[mi - 1] = S::mul(ph[mi], rho);
       for (int m = mi - 2; m >= 4; --m) {
         nb[m] = nb[m + 1];
         nof[m] = nof[m + 1] + 2;
@@ -184,17 +189,18 @@ __device__ __noinline__ void lane_dfs(const LaneMem<S> L, int root, int root_o, 
       }
     }
     HM<S, 6> R3;
-    double phi3;
+    Re phi3;
     if (c & 1ull) {
-      phi3 = ph[4] * lane_include4<S>(L, nb[4], nof[4], R3, bad);
+      phi3 = S::mul(ph[4], lane_include4<S>(L, nb[4], nof[4], R3, bad));
     } else {
       lane_load_trail4<S>(L, nb[4], nof[4], R3);
       phi3 = ph[4];
     }
-    double v, a;
+    Re v;
+    double a;
     Subtree<S, 6>::run(R3, phi3, v, a, bad);
     const int excl_above = (n - 3) - (incl_root + __popcll(c));
-    if (excl_above & 1) v = -v;
+    if (excl_above & 1) v = S::neg(v);
     acc.add(v);
     ab += a;
   }
@@ -212,14 +218,15 @@ __device__ __forceinline__ int src_row(const MatDesc& D, int t, int c) {
 // max |O_rs - conj(O_sr)| <= 1e-12 max |O|; and structured,
 // O(a_j^dag, a_k^dag) = conj O(a_j, a_k), O(a_j^dag, a_k) = conj O(a_j, a_k^dag)
 // within the same tolerance (the form of every physical Gaussian state), all
-// in the max(|Re|, |Im|) norm of each entry.  Pass 2 writes, in packed lower
+// in the max(|Re|, |Im|) norm of each entry (exactly, with D.ext).  Pass 2 writes, in packed lower
 // triangle, either the complex B = I - O in pairs order or, for a structured
 // O (unless D.real == 0), the real V = U^H B U in (x_1, p_1, x_2, p_2, ...)
 // order:
 //   V(x_j, x_k) = Re A + Re C,  V(x_j, p_k) = Im C - Im A,
 //   V(p_j, x_k) = Im A + Im C,  V(p_j, p_k) = Re A - Re C,
 // with A = B(a_j, a_k) and C = B(a_j, a_k^dag).  flags gets FLAG_REAL when V
-// was written.
+// was written.  With D.ext the entries are written as double-doubles (ddc_t or
+// dd_t): 1 - O_ii exactly, and each entry of V to within 3 u^2.
 __global__ void __launch_bounds__(256) k_intake(const MatDesc* __restrict__ mats, int check, int* __restrict__ flags) {
   const MatDesc D = mats[blockIdx.x];
   const int n = D.n, tot = n * (2 * n + 1);
@@ -257,7 +264,13 @@ __global__ void __launch_bounds__(256) k_intake(const MatDesc* __restrict__ mats
     int f = 0;
     if (s_bad) f |= FLAG_NONFINITE;
     if (check && !(gdev <= 1e-12 * gmax)) f |= FLAG_NOTHERM;
-    const int real = D.real >= 0 ? D.real : (!s_bad && gsdev <= 1e-12 * gmax);
+    // FP64 arithmetic takes structure within 1e-12 max|O| (the real form uses
+    // one half of the blocks, a change far below its rounding); double-double
+    // arithmetic only exact structure, and ignores a caller's hint.
+    int real;
+    if (D.real == 0) real = 0;
+    else if (D.ext) real = !s_bad && gsdev == 0.0;
+    else real = D.real == 1 ? 1 : (!s_bad && gsdev <= 1e-12 * gmax);
     if (real) f |= FLAG_REAL;
     s_real = real;
     flags[blockIdx.x] = f;
@@ -271,25 +284,45 @@ __global__ void __launch_bounds__(256) k_intake(const MatDesc* __restrict__ mats
     const int s = e - P(r, 0);
     if (!real) {
       const double2 a = D.O[(size_t)src_row(D, r >> 1, r & 1) * D.ld + src_row(D, s >> 1, s & 1)];
-      D.B[e] = r == s ? make_double2(1.0 - a.x, 0.0) : make_double2(-a.x, -a.y);
+      if (!D.ext) {
+        D.B[e] = r == s ? make_double2(1.0 - a.x, 0.0) : make_double2(-a.x, -a.y);
+      } else {
+        ddc_t v{dd_t{-a.x, 0.0}, dd_t{-a.y, 0.0}};
+        if (r == s) {
+          two_sum(1.0, -a.x, v.x.h, v.x.l);
+          v.y = dd_t{0.0, 0.0};
+        }
+        ((ddc_t*)D.B)[e] = v;
+      }
     } else {
       const int j = r >> 1, k = s >> 1;
       const double2 oa = D.O[(size_t)src_row(D, j, 0) * D.ld + src_row(D, k, 0)];
       const double2 oc = D.O[(size_t)src_row(D, j, 0) * D.ld + src_row(D, k, 1)];
-      const double Are = (j == k ? 1.0 : 0.0) - oa.x, Aim = -oa.y, Cre = -oc.x, Cim = -oc.y;
-      double v;
-      if ((r & 1) == 0) v = (s & 1) == 0 ? Are + Cre : Cim - Aim;
-      else v = (s & 1) == 0 ? Aim + Cim : Are - Cre;
-      ((double*)D.B)[e] = v;
+      if (!D.ext) {
+        const double Are = (j == k ? 1.0 : 0.0) - oa.x, Aim = -oa.y, Cre = -oc.x, Cim = -oc.y;
+        double v;
+        if ((r & 1) == 0) v = (s & 1) == 0 ? Are + Cre : Cim - Aim;
+        else v = (s & 1) == 0 ? Aim + Cim : Are - Cre;
+        ((double*)D.B)[e] = v;
+      } else {
+        dd_t Are{-oa.x, 0.0};
+        if (j == k) two_sum(1.0, -oa.x, Are.h, Are.l);
+        const dd_t Aim{-oa.y, 0.0}, Cre{-oc.x, 0.0}, Cim{-oc.y, 0.0};
+        dd_t v;
+        if ((r & 1) == 0) v = (s & 1) == 0 ? dd_add(Are, Cre) : dd_add(Cim, dd_neg(Aim));
+        else v = (s & 1) == 0 ? dd_add(Aim, Cim) : dd_add(Are, dd_neg(Cre));
+        ((dd_t*)D.B)[e] = v;
+      }
     }
   }
 }
 
 // Unit partial (hi, lo, abs).  For p < 5 the unit partials are the reduction leaves.
+template <class S>
 __device__ __forceinline__ Part write_partial(const UnitsParams& prm, const MatDesc& D, int mat, long long u,
-                                              DD acc, double ab, bool bad) {
+                                              const typename S::Acc& acc, double ab, bool bad) {
   double hi, lo;
-  fast_two_sum(acc.s, acc.c, hi, lo);
+  S::acc_out(acc, hi, lo);
   const Part v{hi, lo, ab, 0.0};
   prm.partials[D.part_off + u] = v;
   if (D.p < 5) prm.red_leaves[D.red_off + u] = v;
@@ -318,10 +351,11 @@ __device__ __forceinline__ void write_task_partial(const UnitsParams& prm, const
 // out breadth-first over 5 more levels into 32 unit roots, one per lane, and
 // each lane walks its own subtree.
 template <class S>
-__device__ void run_task_shared(const UnitsParams& prm, const TaskDesc T, int lane, long long gw) {
+__device__ void run_task_shared(const UnitsParams& prm, const TaskDesc T, int lane, char* lreg, char* wreg) {
   using E = typename S::T;
-  const LaneMem<S> L{(E*)prm.lane_scratch + gw * kWarp * prm.lane_elems + lane};
-  E* WS = (E*)prm.warp_scratch + gw * prm.warp_elems;
+  using Re = typename S::Re;
+  const LaneMem<S> L{(E*)lreg + lane};
+  E* WS = (E*)wreg;
   const MatDesc D = prm.mats[T.mat];
   const int n = D.n, p = D.p, M = n - p, m0 = M + 5;
   E* SB = WS;
@@ -332,11 +366,11 @@ __device__ void run_task_shared(const UnitsParams& prm, const TaskDesc T, int la
   // 1. task node: decisions on modes 0..p-6 are the bits of T.sub (same for all lanes)
   const E* src = (const E*)D.B;
   int o = 0, incl = 0;
-  double phi = 1.0;
+  Re phi = S::one();
   bool own = false;
   for (int j = 0; j < p - 5; ++j) {
     if ((T.sub >> j) & 1) {
-      double rho;
+      Re rho;
       if (!own) {
         rho = coop_include<S>(src, o, n - j, SB, 0, xsw, ysw, bad);
         src = SB;
@@ -346,7 +380,7 @@ __device__ void run_task_shared(const UnitsParams& prm, const TaskDesc T, int la
         rho = coop_include<S>(SB, o, n - j, SB, o + 2, xsw, ysw, bad);
         o += 2;
       }
-      phi *= rho;
+      phi = S::mul(phi, rho);
       ++incl;
     } else {
       o += 2;
@@ -355,20 +389,20 @@ __device__ void run_task_shared(const UnitsParams& prm, const TaskDesc T, int la
   // 2. breadth-first fan-out: lane q holds level-d node q (bit e of q = decision on mode p-5+e)
   const E* nptr = src;
   int no = o, nincl = incl;
-  double nphi = phi;
+  Re nphi = phi;
   for (int d = 0; d < 5; ++d) {
     const int nodes = 1 << d, m = m0 - d;
     for (int q = 0; q < nodes; ++q) {
       const E* qp = (const E*)__shfl_sync(0xffffffffu, (unsigned long long)nptr, q);
       const int qo = __shfl_sync(0xffffffffu, no, q);
-      const double qphi = __shfl_sync(0xffffffffu, nphi, q);
+      const Re qphi = S::shfl(nphi, q);
       const int qincl = __shfl_sync(0xffffffffu, nincl, q);
       E* dst = arena + arena_off(m0, d) + q * tri_size(m - 1);
-      const double rho = coop_include<S>(qp, qo, m, dst, 0, xsw, ysw, bad);
+      const Re rho = coop_include<S>(qp, qo, m, dst, 0, xsw, ysw, bad);
       if (lane == (q | nodes)) {
         nptr = dst;
         no = 0;
-        nphi = qphi * rho;
+        nphi = S::mul(qphi, rho);
         nincl = qincl + 1;
       }
     }
@@ -380,20 +414,20 @@ __device__ void run_task_shared(const UnitsParams& prm, const TaskDesc T, int la
     for (int k = 0; k <= i; ++k) L.st(P(i, k), nptr[P(i + no, k + no)]);
   const int root_sz = tri_size(M);
   const int xs = root_sz + stack_off(M), ys = xs + 2 * n;
-  DD acc{0.0, 0.0};
+  typename S::Acc acc = S::acc0();
   double ab = 0.0;
   lane_dfs<S>(L, 0, 0, M, n, nphi, nincl, root_sz, xs, ys, acc, ab, bad);
   const long long u = (long long)T.sub | ((long long)lane << (p - 5));
-  const Part v = write_partial(prm, D, T.mat, u, acc, ab, bad);
+  const Part v = write_partial<S>(prm, D, T.mat, u, acc, ab, bad);
   write_task_partial(prm, D, T.sub, v, lane);
 }
 
 // p < 5: lanes take units of up to 32 small matrices of one size and type;
 // each lane builds its own root from B by in-place includes.
 template <class S>
-__device__ void run_task_lanes(const UnitsParams& prm, const TaskDesc T, int lane, long long gw) {
+__device__ void run_task_lanes(const UnitsParams& prm, const TaskDesc T, int lane, char* lreg) {
   using E = typename S::T;
-  const LaneMem<S> L{(E*)prm.lane_scratch + gw * kWarp * prm.lane_elems + lane};
+  const LaneMem<S> L{(E*)lreg + lane};
   const int p = prm.mats[T.mat].p;
   const long long q = (long long)T.sub * kWarp + lane;
   if (q >= ((long long)T.nmat << p)) return;
@@ -409,36 +443,49 @@ __device__ void run_task_lanes(const UnitsParams& prm, const TaskDesc T, int lan
   const int xs = root_sz + stack_off(M), ys = xs + 2 * n;
   bool bad = false;
   int o = 0, incl = 0;
-  double phi = 1.0;
+  typename S::Re phi = S::one();
   for (int j = 0; j < p; ++j) {
     if ((u >> j) & 1) {
-      phi *= lane_include_mem<S>(L, 0, o, n - j, 0, o + 2, xs, ys, bad);
+      phi = S::mul(phi, lane_include_mem<S>(L, 0, o, n - j, 0, o + 2, xs, ys, bad));
       ++incl;
     }
     o += 2;
   }
-  DD acc{0.0, 0.0};
+  typename S::Acc acc = S::acc0();
   double ab = 0.0;
   lane_dfs<S>(L, 0, o, M, n, phi, incl, root_sz, xs, ys, acc, ab, bad);
-  write_partial(prm, D, mat, u, acc, ab, bad);
+  write_partial<S>(prm, D, mat, u, acc, ab, bad);
 }
 
 // p < 5: each lane takes the arithmetic of its own matrix (the lanes of a task
 // share n and p; they diverge only if the batch mixes structured and general inputs).
-__device__ __forceinline__ void run_task_lanes_any(const UnitsParams& prm, const TaskDesc T, int lane, long long gw) {
+template <class SR, class SC>
+__device__ __forceinline__ void run_task_lanes_any(const UnitsParams& prm, const TaskDesc T, int lane, char* lreg_r,
+                                                   char* lreg_c) {
   const int p = prm.mats[T.mat].p;
   const long long q = (long long)T.sub * kWarp + lane;
   if (q >= ((long long)T.nmat << p)) return;
   const int mat = T.mat + (int)(q >> p);
-  if (prm.mat_flags[mat] & FLAG_REAL) run_task_lanes<Real>(prm, T, lane, gw);
-  else run_task_lanes<Cplx>(prm, T, lane, gw);
+  if (prm.mat_flags[mat] & FLAG_REAL) run_task_lanes<SR>(prm, T, lane, lreg_r);
+  else run_task_lanes<SC>(prm, T, lane, lreg_c);
 }
 
 constexpr int kUnitsThreads = 128;
 
-__global__ void __launch_bounds__(kUnitsThreads, 4) k_units(const UnitsParams prm) {
+// The persistent task loop, in the arithmetic of SR (structured inputs, real
+// (x, p) basis) and SC (general inputs).  A warp's lane scratch holds an SR
+// area and an SC area side by side, each lane-interleaved in its own entry
+// size, because the lanes of one task (p < 5) may take different arithmetic;
+// its task-node scratch (p >= 5: one matrix, one arithmetic) is sized for SC.
+template <class SR, class SC>
+__device__ __forceinline__ void units_loop(const UnitsParams& prm) {
+  using TR = typename SR::T;
+  using TC = typename SC::T;
   const int lane = threadIdx.x & (kWarp - 1);
   const long long gw = (long long)blockIdx.x * (blockDim.x / kWarp) + threadIdx.x / kWarp;
+  char* lreg_r = (char*)prm.lane_scratch + gw * kWarp * prm.lane_elems * (long long)(sizeof(TR) + sizeof(TC));
+  char* lreg_c = lreg_r + (long long)kWarp * prm.lane_elems * (long long)sizeof(TR);
+  char* wreg = (char*)prm.warp_scratch + gw * prm.warp_elems * (long long)sizeof(TC);
   const unsigned long long t0 = global_ns();
   for (;;) {
     unsigned t = 0xffffffffu;
@@ -455,13 +502,27 @@ __global__ void __launch_bounds__(kUnitsThreads, 4) k_units(const UnitsParams pr
     if (t >= (unsigned)prm.ntasks) break;
     const TaskDesc T = prm.tasks[t];
     if (prm.mats[T.mat].p >= 5) {  // one matrix per task: the whole warp takes its arithmetic
-      if (prm.mat_flags[T.mat] & FLAG_REAL) run_task_shared<Real>(prm, T, lane, gw);
-      else run_task_shared<Cplx>(prm, T, lane, gw);
+      if (prm.mat_flags[T.mat] & FLAG_REAL) run_task_shared<SR>(prm, T, lane, lreg_r, wreg);
+      else run_task_shared<SC>(prm, T, lane, lreg_c, wreg);
     } else {
-      run_task_lanes_any(prm, T, lane, gw);
+      run_task_lanes_any<SR, SC>(prm, T, lane, lreg_r, lreg_c);
     }
     __syncwarp();
   }
+}
+
+static_assert(sizeof(Real::T) + sizeof(Cplx::T) == kLaneEntryBytes, "lane scratch layout");
+static_assert(sizeof(Cplx::T) == kWarpEntryBytes, "warp scratch layout");
+static_assert(sizeof(RealX::T) + sizeof(CplxX::T) == kLaneEntryBytesExt, "lane scratch layout (ext)");
+static_assert(sizeof(CplxX::T) == kWarpEntryBytesExt, "warp scratch layout (ext)");
+
+__global__ void __launch_bounds__(kUnitsThreads, 4) k_units(const UnitsParams prm) { units_loop<Real, Cplx>(prm); }
+
+// Extended precision: double-double entries need about twice the registers,
+// so two blocks of 128 threads per SM.
+constexpr int kExtBlocksPerSm = 2;
+__global__ void __launch_bounds__(kUnitsThreads, kExtBlocksPerSm) k_units_ext(const UnitsParams prm) {
+  units_loop<RealX, CplxX>(prm);
 }
 
 // Binary tree over the 2^p partials of each matrix: thread t reduces an
@@ -542,7 +603,8 @@ cudaError_t launch_intake(const MatDesc* d_mats, int nmats, int check, int* d_fl
 }
 cudaError_t launch_units(const UnitsParams& prm, int grid, cudaStream_t s) {
   if (prm.ntasks <= 0) return cudaSuccess;
-  k_units<<<grid, kUnitsThreads, 0, s>>>(prm);
+  if (prm.ext) k_units_ext<<<grid, kUnitsThreads, 0, s>>>(prm);
+  else k_units<<<grid, kUnitsThreads, 0, s>>>(prm);
   return cudaGetLastError();
 }
 cudaError_t launch_reduce(const MatDesc* d_mats, int nmats, const Part* partials, const int* flags,
@@ -552,8 +614,9 @@ cudaError_t launch_reduce(const MatDesc* d_mats, int nmats, const Part* partials
   return cudaGetLastError();
 }
 int units_block_threads() { return kUnitsThreads; }
-cudaError_t units_blocks_per_sm(int* blocks) {
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, k_units, kUnitsThreads, 0);
+cudaError_t units_blocks_per_sm(int* blocks, int ext) {
+  return ext ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, k_units_ext, kUnitsThreads, 0)
+             : cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, k_units, kUnitsThreads, 0);
 }
 
 cudaError_t run_probe_fp64(double seconds, double* dfma_per_s) {

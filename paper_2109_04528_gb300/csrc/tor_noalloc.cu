@@ -10,7 +10,7 @@
 // the unit partials, the lane and warp stacks, the control words) lives in one
 // file-scope device array that the library image carries.
 //
-// The array is g_noalloc_scratch below (8 MiB).  Every device that loads the
+// The array is g_noalloc_scratch below (12 MiB).  Every device that loads the
 // library keeps it until the process exits.  All calls share it and it keeps
 // whatever the last call left there; the set-up kernel clears the words that
 // must start at zero (task ticket, abort word, cancel word, status flags) at the
@@ -32,7 +32,7 @@
 namespace tor {
 namespace {
 
-constexpr size_t kNoallocBytes = 8u << 20;
+constexpr size_t kNoallocBytes = 12u << 20;
 constexpr int kNoallocMaxN = TOR_NOALLOC_MAX_N;
 constexpr int kNoallocMmax = 6;       // unit subtrees over at most 6 modes
 constexpr int kNoallocBlocks = 8;     // 8 blocks x 4 warps = 32 persistent warps
@@ -85,8 +85,8 @@ constexpr size_t OFF_B = align256(OFF_RES + sizeof(ResultRec));
 constexpr size_t OFF_PARTS = align256(OFF_B + sizeof(double2) * tri_c(kNoallocMaxN));
 constexpr size_t OFF_REDS = align256(OFF_PARTS + sizeof(Part) * kMaxUnits);
 constexpr size_t OFF_LANE = align256(OFF_REDS + sizeof(Part) * kMaxUnits);
-constexpr size_t OFF_WARP = align256(OFF_LANE + sizeof(double2) * kLanes * max_lane_elems() * kWarps);
-constexpr size_t END = align256(OFF_WARP + sizeof(double2) * max_warp_elems() * kWarps);
+constexpr size_t OFF_WARP = align256(OFF_LANE + (size_t)kLaneEntryBytes * kLanes * max_lane_elems() * kWarps);
+constexpr size_t END = align256(OFF_WARP + (size_t)kWarpEntryBytes * max_warp_elems() * kWarps);
 static_assert(END <= kNoallocBytes, "no-alloc scratch layout does not fit the static array");
 
 // Fills the job descriptors and clears the control words, writing the array directly.
@@ -102,6 +102,7 @@ __global__ void k_noalloc_setup(const double2* O, int n, int ld, int layout) {
     D->modes = nullptr;
     D->n_src = n;
     D->real = 0;
+    D->ext = 0;
     D->B = (double2*)(base + OFF_B);
     D->part_off = 0;
     D->red_off = 0;
@@ -178,7 +179,7 @@ extern "C" tor_status tor_eval_noalloc(int device, int n, const tor_c128* O, int
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess) e = launch_intake((const MatDesc*)(base + OFF_MATS), 1, 1, (int*)(base + OFF_FLAGS), s);
     if (e == cudaSuccess) {
-      UnitsParams prm;
+      UnitsParams prm{};
       prm.mats = (const MatDesc*)(base + OFF_MATS);
       prm.tasks = (const TaskDesc*)(base + OFF_TASKS);
       prm.ntasks = p >= 5 ? (1 << (p - 5)) : 1;

@@ -67,11 +67,25 @@ def husimi_covariance(r: np.ndarray, T: np.ndarray) -> np.ndarray:
 
 
 def sampling_matrix(sigma: np.ndarray) -> np.ndarray:
-    """O = I - Sigma^{-1} (Eq. A), rounded once to complex128."""
+    """O = I - Sigma^{-1} (Eq. A) in complex128, projected exactly onto the form
+    every Gaussian state's O has in block layout,
+        O = [[P, Q], [conj(Q), conj(P)]],  P Hermitian, Q symmetric,
+    which also makes O exactly Hermitian.  The projection moves O by about the
+    rounding of the inverse; it removes that rounding's asymmetry so that the
+    structure (and with it the real (x, p) form) holds exactly."""
     m = sigma.shape[0]
+    n = m // 2
     O = np.eye(m) - np.linalg.inv(sigma)
-    # Hermitian part only: removes the inverse's rounding asymmetry.
-    return 0.5 * (O + O.conj().T)
+    W = O[:n, :n] + O[n:, n:].conj()  # ~ 2 P
+    S = O[:n, n:] + O[n:, :n].conj()  # ~ 2 Q
+    P = 0.25 * (W + W.conj().T)       # exactly Hermitian (sums commute, 0.25 is exact)
+    Q = 0.25 * (S + S.T)              # exactly symmetric
+    out = np.empty_like(O)
+    out[:n, :n] = P
+    out[:n, n:] = Q
+    out[n:, :n] = Q.conj()
+    out[n:, n:] = P.conj()
+    return out
 
 
 @dataclass

@@ -23,12 +23,20 @@ def two_sum(a: float, b: float):
     return s, (a - (s - bb)) + (b - bb)
 
 
+def fast_two_sum(a: float, b: float):
+    s = a + b
+    return s, b - (s - a)
+
+
 def dd_add(x, y):
-    """(hi, lo, abs) + (hi, lo, abs): TwoSum of the highs, lows folded in, FastTwoSum."""
+    """(hi, lo, abs) + (hi, lo, abs).  The double-double sum is the accurate
+    double-word addition (Joldes, Muller, Popescu, ACM TOMS 44 (2017),
+    AccurateDWPlusDW), the same operations in the same order as the device."""
     s, e = two_sum(x[0], y[0])
-    e = e + (x[1] + y[1])
-    h = s + e
-    return (h, e - (h - s), x[2] + y[2])
+    t, f = two_sum(x[1], y[1])
+    s, e = fast_two_sum(s, e + t)
+    h, lo = fast_two_sum(s, e + f)
+    return (h, lo, x[2] + y[2])
 
 
 def tree_merge(parts):

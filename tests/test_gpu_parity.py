@@ -237,3 +237,21 @@ def test_structure_detection_follows_the_input():
             r = binding.tor_eval(a, O)
         ref = oracle.tor_brute(O)
         assert gpu_err(r, ref) <= TOL * ref.abs_sum
+
+
+def test_mixed_batch_structured_and_general(ctx, oracle_mod):
+    # structured (real (x, p) arithmetic) and general (complex) matrices of the
+    # same sizes in one batch: the lanes of one task (p < 5) and concurrently
+    # running warps take different arithmetic and must not share scratch
+    mats = []
+    for i in range(48):
+        n = (3, 6, 8, 12)[i % 4]
+        mats.append(inputs.lossy_squeezed(n, 1300 + i).O if i % 3
+                    else inputs.random_hermitian_contraction(n, 1300 + i, 0.8).O)
+    batch = binding.tor_eval_batch(ctx, mats)
+    for O, b in zip(mats, batch):
+        s = binding.tor_eval(ctx, O)
+        assert (s.hi, s.lo, s.abs_sum, s.path) == (b.hi, b.lo, b.abs_sum, b.path)
+    for O, b in list(zip(mats, batch))[:8]:
+        ref = oracle_mod.tor_brute(O)
+        assert gpu_err(b, ref) <= TOL * ref.abs_sum

@@ -159,7 +159,8 @@ def test_admission_by_memory_budget():
 
 
 def test_cancel_stops_a_running_evaluation():
-    inst = inputs.config_single(32)
+    # n = 36: ~4.5 s of work on the real path, so the cancel lands mid-run
+    inst = inputs.config_single(36)
     with binding.Context(device=0) as c:
         out = {}
 

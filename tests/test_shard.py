@@ -49,11 +49,22 @@ def test_tree_merge_is_binary_and_ordered():
         shard.shard_range(4, 3, 0)
 
 
-def test_dd_add_is_error_free_on_cancelling_terms():
-    a = (1.0, 1e-17, 1.0)
-    b = (-1.0, 2e-17, 1.0)
-    h, lo, ab = shard.dd_add(a, b)
-    assert h == 3e-17 and lo == 0.0 and ab == 2.0
+def test_dd_add_is_accurate_on_cancelling_terms():
+    # relative error <= 3 u^2 of the exact sum (u = 2^-53), also when the highs cancel
+    from fractions import Fraction
+    rng = np.random.default_rng(5)
+    cases = [((1.0, 1e-17, 1.0), (-1.0, 2e-17, 1.0))]
+    for _ in range(2000):
+        ah = rng.uniform(-1, 1)
+        al = ah * rng.uniform(-1, 1) * 2.0 ** -53
+        bh = -ah * (1 + rng.uniform(-1, 1) * 2.0 ** -rng.integers(1, 60))
+        bl = bh * rng.uniform(-1, 1) * 2.0 ** -53
+        cases.append(((ah, al, 1.0), (bh, bl, 1.0)))
+    for a, b in cases:
+        h, lo, ab = shard.dd_add(a, b)
+        exact = sum(Fraction(v) for v in (a[0], a[1], b[0], b[1]))
+        assert abs(Fraction(h) + Fraction(lo) - exact) <= 3 * Fraction(2) ** -106 * abs(exact)
+        assert abs(lo) <= abs(h) * 2.0 ** -53 and ab == 2.0
 
 
 def test_two_ranks_gloo_match_single_process(oracle_mod, tmp_path):
