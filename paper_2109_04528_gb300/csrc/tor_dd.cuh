@@ -18,7 +18,8 @@
 //   dd_mul     7  double-word product (the same paper's DWTimesDW with the
 //                 lo * lo term dropped): relative error <= ~5 u^2
 //   ProdAcc       s + sum_i (+-) b_i c_i with one normalisation at the end:
-//                 12 per product + 6; absolute error ~ u^2 (|s| + sum |b_i c_i|)
+//                 12 per product + 6 (a sum that starts from a product: 5 for
+//                 it); absolute error ~ u^2 (|s| + sum |b_i c_i|)
 //   dd_rcp    13  Newton step for 1/a from the FP64 reciprocal, evaluated in
 //                 double-double: 1/a = y (1 + e + e^2 + ...), e = 1 - a y
 //   dd_rsqrt  19  the same for a^{-1/2}: y (1 + e/2 + 3e^2/8 + ...), e = 1 - a y^2
@@ -58,6 +59,12 @@ __device__ __forceinline__ dd_t dd_mul(dd_t a, dd_t b) {
 struct ProdAcc {
   double h, t;
   __device__ __forceinline__ explicit ProdAcc(dd_t s) : h(s.h), t(s.l) {}
+  // start from the product b c (7 operations): h + t = b c to ~u^2
+  __device__ __forceinline__ ProdAcc(dd_t b, dd_t c) {
+    two_prod(b.h, c.h, h, t);
+    t = __fma_rn(b.h, c.l, t);
+    t = __fma_rn(b.l, c.h, t);
+  }
   __device__ __forceinline__ void add(dd_t b, dd_t c) {  // += b c
     double p, e, s, r;
     two_prod(b.h, c.h, p, e);
@@ -130,8 +137,7 @@ struct RealX : XRe {
   static __device__ __forceinline__ dd_t re(T v) { return v; }
   static __device__ __forceinline__ T diag(dd_t d) { return d; }
   static __device__ __forceinline__ dd_t det2(dd_t a, T b, dd_t e) {
-    ProdAcc s(dd_t{0.0, 0.0});
-    s.add(a, e);
+    ProdAcc s(a, e);
     s.sub(b, b);
     return s.out();
   }
@@ -160,8 +166,7 @@ struct CplxX : XRe {
   static __device__ __forceinline__ dd_t re(T v) { return v.x; }
   static __device__ __forceinline__ T diag(dd_t d) { return ddc_t{d, dd_t{0.0, 0.0}}; }
   static __device__ __forceinline__ dd_t det2(dd_t a, T b, dd_t e) {  // a e - |b|^2
-    ProdAcc s(dd_t{0.0, 0.0});
-    s.add(a, e);
+    ProdAcc s(a, e);
     s.sub(b.x, b.x);
     s.sub(b.y, b.y);
     return s.out();

@@ -79,27 +79,37 @@ def path_flops(n: int, path: int = 0) -> float:
     """FP64 flops of the GPU walk over all 2^n subsets in the arithmetic it
     took (tor_result.path: bit 0 real (x, p) basis, bit 1 double-double).
 
-    FP64 factor, per include at m trailing modes / per leaf:
-      complex  32 m^2 + 40 m + 10 / 10  (= rank2_flops; complex MAC 8 flops,
+    FP64 factor: the fixed figure of the hot-path contract, per include at m
+    trailing modes plus 10 per leaf,
+      complex  32 m^2 + 40 m + 10   (= rank2_flops; complex MAC 8 flops,
                complex x real 2, sqrt / rsqrt / div 1)
-      real      8 m^2 + 12 m + 10 / 10  (real FMA 2: update of the 2m x 2m
-               lower triangle 8 m^2 + 4 m, pivot columns 8 m, pivot 10)
+      real      8 m^2 + 12 m + 10   (real FMA 2: update of the 2m x 2m lower
+               triangle 8 m^2 + 4 m, pivot columns 8 m, pivot 10)
     Double-double factor: every FP64 operation of the double-word algorithms
     (add / mul 1, FMA 2; two_sum 6, fast_two_sum 3, two_prod 3; a product
-    accumulated into a sum 15, its final normalisation 6; dd_mul 10, dd_add
-    20, reciprocal 18 and reciprocal square root 26 with their Newton steps):
-      real     72 m^2 + 118 m + 120 / 57   (an entry of the update: two
-               accumulated products + normalisation = 36; a pivot column row
-               41; pivot 110 and the phi product 10; a leaf pair 93 plus the
-               subtree sums 10.5 per leaf)
-      complex 264 m^2 + 224 m + 145 / 64.5 (off-diagonal entry 8 products =
-               132, diagonal 66; pivot column row 112; pivot 135 + 10; leaf
-               pair 108 plus 10.5 per leaf)"""
+    accumulated into a sum 15, a sum started from a product 7, its final
+    normalisation 6; dd_mul 10, dd_add 20, reciprocal 18 and reciprocal
+    square root 26 with their Newton steps).  Includes at m >= 1 trailing
+    modes; the last level (m = 0) is a leaf pair, which needs only the
+    determinant factor and the signed pair sum; every leaf carries 10.5 of
+    subtree and accumulator sums:
+      real     72 m^2 + 118 m + 112 per include, 85 per leaf pair
+               (an update entry: two accumulated products + normalisation 36;
+               a pivot-column row 41; pivot 102 and the phi product 10)
+      complex 264 m^2 + 224 m + 137 per include, 100 per leaf pair
+               (off-diagonal entry 8 products 132, diagonal 66; pivot-column
+               row 112; pivot 127 + 10)"""
     real, ext = bool(path & 1), bool(path & 2)
-    a, b, c, leaf = {(False, False): (32, 40, 10, 10.0), (True, False): (8, 12, 10, 10.0),
-                     (True, True): (72, 118, 120, 57.0), (False, True): (264, 224, 145, 64.5)}[(real, ext)]
-    f = leaf * 2.0 ** n
-    for j in range(n):
+    if not ext:
+        a, b, c = (8, 12, 10) if real else (32, 40, 10)
+        f = 10.0 * 2.0 ** n
+        for j in range(n):
+            m = n - 1 - j
+            f += 2.0 ** j * (a * m * m + b * m + c)
+        return f
+    a, b, c, pair = (72, 118, 112, 85.0) if real else (264, 224, 137, 100.0)
+    f = 10.5 * 2.0 ** n + pair * 2.0 ** (n - 1)
+    for j in range(n - 1):
         m = n - 1 - j
         f += 2.0 ** j * (a * m * m + b * m + c)
     return f
