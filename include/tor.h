@@ -72,13 +72,14 @@ enum { TOR_LAYOUT_BLOCK = 0, TOR_LAYOUT_PAIRS = 1 };
  *                  map from (a, a^dag) to the quadratures (x, p): every principal
  *                  block of V has the determinant of the matching block of I - O,
  *                  and the update costs a quarter of the complex multiply-adds.
- *   TOR_EXTENDED   extended-precision factor (paper Sec. 4, "X = extended"): B = I - O,
+ *   TOR_EXTENDED   extended-precision factor (paper Sec. 5, "X = extended"): B = I - O,
  *                  every pivot, Schur-complement entry, determinant factor and term
  *                  in double-double arithmetic (about 106-bit significands; the FP64
  *                  path carries only the sum in double-double).  For weakly squeezed
  *                  states, whose terms cancel almost completely, the error falls from
- *                  ~1e-16 sum|term| to ~1e-30 sum|term|, at about 6x (real basis) to
- *                  13x (complex) the FP64 instructions per term. */
+ *                  ~1e-16 sum|term| to ~1e-30 sum|term|, at about 12x (real basis) to
+ *                  19x (complex) the time per term.  The real basis is taken only for
+ *                  exactly structured O here (the FP64 path accepts 1e-12 max|O|). */
 enum { TOR_IN_DEVICE = 1u, TOR_NO_CHECK = 2u, TOR_GRAPHS = 4u, TOR_COMPLEX_PATH = 8u, TOR_EXTENDED = 16u };
 
 /* tor_session_create kinds */

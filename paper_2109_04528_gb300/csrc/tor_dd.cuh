@@ -1,7 +1,7 @@
 // tor_dd.cuh -- double-double arithmetic and the extended-precision scalar
 // types RealX and CplxX.
 //
-// Sec. 4 shows the Torontonian of weakly squeezed states to be a sum of 2^n
+// Sec. 5 shows the Torontonian of weakly squeezed states to be a sum of 2^n
 // terms close to +-1 that cancel almost completely, so the error of each term
 // (relative to the term) decides the accuracy of the result; there the factor
 // arithmetic has to run in more than double precision.  These types carry
@@ -110,6 +110,7 @@ __device__ __forceinline__ dd_t dd_rsqrt(dd_t a) {
 // ---------------------------------------------------------------------------
 struct XRe {
   using Re = dd_t;
+  static constexpr int kUnrollK = 2;
   struct Acc {
     dd_t s;
     __device__ __forceinline__ void add(dd_t v) { s = dd_add(s, v); }

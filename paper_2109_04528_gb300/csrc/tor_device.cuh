@@ -24,7 +24,7 @@
 //         (|det U| = 1), so the whole tree can run in real arithmetic at a
 //         quarter of the multiply-adds.
 //   CplxX, RealX  the same two in double-double arithmetic (about 106-bit
-//         significands): the extended-precision factor of Sec. 4, where the
+//         significands): the extended-precision factor of Sec. 5, where the
 //         pivots, the Schur updates, phi and every term are carried in
 //         double-double (tor_dd.cuh).
 // Each type names its real scalar Re (double or dd_t) and its accumulator Acc.
@@ -129,6 +129,7 @@ __device__ __forceinline__ void dd_add(double ah, double al, double bh, double b
 struct Fp64Re {  // real scalar operations of the two FP64 types
   using Re = double;
   using Acc = DD;
+  static constexpr int kUnrollK = 2;  // unroll of the entry loop of an include from memory
   static __device__ __forceinline__ double mul(double a, double b) { return a * b; }
   static __device__ __forceinline__ double sub(double a, double b) { return a - b; }
   static __device__ __forceinline__ double neg(double a) { return -a; }

@@ -69,7 +69,7 @@ __device__ __noinline__ typename S::Re lane_include_mem(const LaneMem<S> L, int 
     const T xt = S::scale(xi, pv.ia), yt = S::scale(yi, pv.id2);
     const int srow = src + P(o + 2 + i, o + 2);
     const int drow = dst + P(dst_o + i, dst_o);
-#pragma unroll 2
+#pragma unroll(S::kUnrollK)
     for (int k = 0; k < i; ++k) L.st(drow + k, S::rank2_off(L.ld(srow + k), xt, L.ld(xs + k), yt, L.ld(ys + k)));
     L.st(drow + i, S::diag(S::rank2_diag(L.ldd(srow + i), xt, xi, yt, yi)));
   }

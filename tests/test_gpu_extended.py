@@ -1,4 +1,4 @@
-"""GPU parity of the extended-precision factor (TOR_EXTENDED; Sec. 4, "X =
+"""GPU parity of the extended-precision factor (TOR_EXTENDED; Sec. 5, "X =
 extended": the Cholesky / Schur arithmetic in more than double precision)
 against the binary128 oracle, through the C ABI.
 
@@ -103,7 +103,7 @@ def test_product_state_exact_product(xctx, oracle_mod):
 
 
 def test_low_squeezing_relative_accuracy(xctx, oracle_mod):
-    # Sec. 4: weak squeezing, terms near +-1 cancelling to Tor ~ 1e-15
+    # Sec. 5: weak squeezing, terms near +-1 cancelling to Tor ~ 1e-15
     # (kappa = sum|term| / |Tor| ~ 1e19).  Double-double keeps ~10 digits of
     # Tor; the FP64 factor keeps none.
     inst = inputs.lossy_squeezed(14, 4256, (0.1, 0.2), 1.0)
