@@ -186,6 +186,31 @@ tor_status tor_eval_marginal(tor_ctx* ctx, tor_session* s, int j, int k, const i
 tor_status tor_submit_marginal(tor_ctx* ctx, tor_session* s, int j, int k, const int* modes,
                                uint64_t* ticket);
 
+/* Draws click patterns of threshold detectors on the first n_modes modes of
+ * the session's state by the chain rule -- the use of the Torontonian as the
+ * probability of a threshold-detection outcome (Sec. 1).  For each sample,
+ * modes j = 0, 1, ... are decided in order: with S the clicks so far,
+ *   t0 = Tor(O^(j+1)_S),  t1 = Tor(O^(j+1)_{S u {j}}),
+ *   P(click at j | S) = t1 / (t0 + t1),
+ * and mode j clicks iff uniforms[i * n_modes + j] < P(click at j | S).
+ *   uniforms  count x n_modes doubles in [0, 1), sample-major: the random
+ *             numbers, drawn by the caller (the call itself draws none).
+ *   patterns  out: count x n_modes bytes, 1 = click.
+ *   prob      out (may be NULL): P(pattern) = Tor(O^(n_modes)_S) / sqrt(det
+ *             Sigma_[n_modes]), the probability of each drawn pattern.
+ *   max_dev   out (may be NULL): the largest |(t0 + t1) / sqrt(det Sigma_[j+1])
+ *             - P(S on the first j modes)| / P(...) over samples and steps --
+ *             the chain rule's consistency, a rounding-level number.
+ * All samples' requests of one step go to the serving loop together (2 count
+ * per step).  Each evaluation is exact and costs 2^|S|; patterns with more
+ * than 64 clicks return TOR_ETOOBIG.  Under TOR_EXTENDED the t's carry ~106
+ * bits, for weakly squeezed states whose Torontonians cancel (Sec. 5).
+ * Returns TOR_EINVAL for bad arguments (n_modes > the session's modes, a
+ * uniform outside [0, 1)), else the first failing status of an evaluation;
+ * blocking; patterns and prob are valid only on TOR_OK. */
+tor_status tor_sample(tor_ctx* ctx, tor_session* s, int count, int n_modes, const double* uniforms,
+                      unsigned char* patterns, double* prob, double* max_dev);
+
 /* Asks the kernels running for this context to stop at their next unit
  * boundary; the affected results get TOR_ECANCELED.  Thread-safe. */
 tor_status tor_cancel(tor_ctx* ctx);

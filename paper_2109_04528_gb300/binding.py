@@ -28,7 +28,7 @@ EXPORTS = ["tor_config_default", "tor_create", "tor_destroy", "tor_eval", "tor_e
            "tor_set_prefix_depth", "tor_eval_units", "tor_last_times", "tor_probe_fp64",
            "tor_eval_noalloc", "tor_autotune", "tor_plan_save", "tor_plan_load", "tor_serving_stats",
            "tor_session_create", "tor_session_destroy", "tor_eval_marginal", "tor_submit_marginal",
-           "tor_plan_leaves", "tor_eval_range"]
+           "tor_plan_leaves", "tor_eval_range", "tor_sample"]
 TOR_NOALLOC_MAX_N = 16
 
 
@@ -119,6 +119,7 @@ def load_library():
     lib.tor_session_destroy.restype = None
     lib.tor_eval_marginal.argtypes = [c_void_p, c_void_p, c_int, c_int, P(c_int), P(tor_result)]
     lib.tor_submit_marginal.argtypes = [c_void_p, c_void_p, c_int, c_int, P(c_int), P(ctypes.c_uint64)]
+    lib.tor_sample.argtypes = [c_void_p, c_void_p, c_int, c_int, P(c_double), c_void_p, P(c_double), P(c_double)]
     lib.tor_plan_leaves.argtypes = [c_void_p, c_int]
     lib.tor_plan_leaves.restype = LL
     lib.tor_eval_range.argtypes = [c_void_p, c_int, c_void_p, c_int, LL, LL, P(tor_result)]
@@ -382,6 +383,25 @@ def tor_eval_marginal(ctx: Context, session: Session, j: int, modes, check: bool
     if check and st != TOR_OK:
         raise TorError(st, ctx.last_error() or "tor_eval_marginal")
     return TorResult.of(res)
+
+
+def tor_sample(ctx: Context, session: Session, uniforms):
+    """Chain-rule threshold-detector samples (tor_sample).  uniforms: (count,
+    n_modes) array in [0, 1).  Returns (patterns uint8 (count, n_modes),
+    probability of each pattern, chain-rule consistency max_dev)."""
+    u = np.ascontiguousarray(uniforms, dtype=np.float64)
+    if u.ndim != 2:
+        raise ValueError("uniforms must be (count, n_modes)")
+    count, n_modes = u.shape
+    pat = np.zeros((count, n_modes), dtype=np.uint8)
+    prob = np.zeros(count, dtype=np.float64)
+    dev = ctypes.c_double()
+    dp = ctypes.POINTER(ctypes.c_double)
+    st = ctx._lib.tor_sample(ctx.handle, session._h, count, n_modes, u.ctypes.data_as(dp),
+                             ctypes.c_void_p(pat.ctypes.data), prob.ctypes.data_as(dp), ctypes.byref(dev))
+    if st != TOR_OK:
+        raise TorError(st, ctx.last_error() or "tor_sample")
+    return pat, prob, dev.value
 
 
 def tor_submit_marginal(ctx: Context, session: Session, j: int, modes) -> int:

@@ -170,6 +170,7 @@ struct tor_session {
   bool closing = false;
   DevBuf d_O;                  // O^(j) for j = 1..N, pairs layout, 2j x 2j row-major each
   std::vector<long long> off;  // element offset of O^(j)
+  std::vector<long double> logdet_sigma;  // log det Sigma_[j], j = 0..N (0 for j = 0)
   uint64_t gen = 0;
 };
 
@@ -1237,6 +1238,9 @@ tor_status tor_session_create(tor_ctx* ctx, int n_total, const tor_c128* M, int 
     tot += 4ll * j * j;
   }
   std::vector<tor_c128> host((size_t)tot);
+  // det K^(j) = det(K_bb) det K^(j-1) (Schur complement of mode j-1's 2x2 block K_bb), so
+  // log det Sigma_[j] = -sum_{i <= j} log det(K_bb at step i)
+  std::vector<long double> logd(N + 1, 0.0L);
   for (int j = N; j >= 1; --j) {
     const int mj = 2 * j;
     tor_c128* Oj = host.data() + s->off[j];
@@ -1245,17 +1249,26 @@ tor_status tor_session_create(tor_ctx* ctx, int n_total, const tor_c128* M, int 
         const CL k = K[(size_t)a * m + b];
         Oj[(size_t)a * mj + b] = tor_c128{(double)((a == b ? 1.0L : 0.0L) - k.re), (double)(-k.im)};
       }
-    if (j == 1) break;
+    if (j == 1) {
+      const long double d1 = K[0].re * K[(size_t)m + 1].re - (K[1].re * K[1].re + K[1].im * K[1].im);
+      if (!(d1 > 0)) {
+        delete s;
+        return TOR_ENOTPD;
+      }
+      logd[1] = logl(d1);
+      break;
+    }
     // remove mode j-1 (rows/cols b0, b0+1): K <- K_aa - K_ab K_bb^{-1} K_ba
     const int b0 = mj - 2;
     const CL p = K[(size_t)b0 * m + b0], q = K[(size_t)b0 * m + b0 + 1], r = K[(size_t)(b0 + 1) * m + b0],
              t = K[(size_t)(b0 + 1) * m + b0 + 1];
     const CL det = csub(cmul(p, t), cmul(q, r));
     const long double dd = det.re * det.re + det.im * det.im;
-    if (!(dd > 0)) {
+    if (!(dd > 0) || !(det.re > 0)) {
       delete s;
       return TOR_ENOTPD;
     }
+    logd[j] = logl(det.re);
     const CL idet{det.re / dd, -det.im / dd};
     const CL i00 = cmul(t, idet), i01 = cmul(CL{-q.re, -q.im}, idet), i10 = cmul(CL{-r.re, -r.im}, idet),
              i11 = cmul(p, idet);
@@ -1268,6 +1281,8 @@ tor_status tor_session_create(tor_ctx* ctx, int n_total, const tor_c128* M, int 
       }
     }
   }
+  s->logdet_sigma.assign(N + 1, 0.0L);
+  for (int j = 1; j <= N; ++j) s->logdet_sigma[j] = s->logdet_sigma[j - 1] - logd[j];
   cudaSetDevice(ctx->cfg.device);
   cudaError_t e = s->d_O.ensure((size_t)tot * 16, &s->gen);
   if (e == cudaSuccess) e = cudaMemcpy(s->d_O.p, host.data(), (size_t)tot * 16, cudaMemcpyHostToDevice);
@@ -1376,6 +1391,63 @@ tor_status tor_submit_marginal(tor_ctx* ctx, tor_session* s, int j, int k, const
     }
   }
   return enqueue_request(ctx, r, ticket);
+}
+
+// Threshold-detector sampling by the chain rule: for every sample, mode j is
+// decided from the two continuations of its clicks S so far on the first
+// j + 1 modes, t0 = Tor(O^(j+1)_S) and t1 = Tor(O^(j+1)_{S u {j}}).  All
+// samples' requests of one step go to the serving loop together.
+tor_status tor_sample(tor_ctx* ctx, tor_session* s, int count, int n_modes, const double* uniforms,
+                      unsigned char* patterns, double* prob, double* max_dev) {
+  if (!ctx || !s || s->ctx != ctx || count < 0 || n_modes < 1 || n_modes > s->N) return TOR_EINVAL;
+  if (count > 0 && (!uniforms || !patterns)) return TOR_EINVAL;
+  for (long long i = 0; i < (long long)count * n_modes; ++i)
+    if (!(uniforms[i] >= 0.0 && uniforms[i] < 1.0)) return TOR_EINVAL;
+  std::vector<std::vector<int>> S(count);
+  std::vector<long double> pprev(count, 1.0L);  // P(clicks S on the modes decided so far)
+  std::vector<uint64_t> t0(count), t1(count);
+  std::vector<char> sub0(count), sub1(count);
+  long double dev = 0.0L;
+  tor_status first = TOR_OK;
+  for (int j = 0; j < n_modes && first == TOR_OK; ++j) {
+    for (int i = 0; i < count; ++i) {
+      std::vector<int>& c = S[i];
+      tor_status st = tor_submit_marginal(ctx, s, j + 1, (int)c.size(), c.data(), &t0[i]);
+      sub0[i] = st == TOR_OK;
+      c.push_back(j);
+      tor_status st1 = st == TOR_OK ? tor_submit_marginal(ctx, s, j + 1, (int)c.size(), c.data(), &t1[i]) : st;
+      c.pop_back();
+      sub1[i] = st == TOR_OK && st1 == TOR_OK;
+      if (first == TOR_OK && st1 != TOR_OK) first = st1;
+      if (first != TOR_OK) {  // stop submitting; what was submitted is still collected below
+        for (int k = i + 1; k < count; ++k) sub0[k] = sub1[k] = 0;
+        break;
+      }
+    }
+    const long double norm = expl(-0.5L * s->logdet_sigma[j + 1]);  // 1 / sqrt(det Sigma_[j+1])
+    for (int i = 0; i < count; ++i) {
+      tor_result r0{}, r1{};
+      tor_status a0 = sub0[i] ? tor_poll(ctx, t0[i], &r0, -1.0) : TOR_EINVAL;
+      tor_status a1 = sub1[i] ? tor_poll(ctx, t1[i], &r1, -1.0) : TOR_EINVAL;
+      if (!sub0[i] || !sub1[i]) continue;
+      if (first == TOR_OK && a0 != TOR_OK) first = a0;
+      if (first == TOR_OK && a1 != TOR_OK) first = a1;
+      if (first != TOR_OK) continue;
+      const long double a = ((long double)r0.hi + (long double)r0.lo) * norm;
+      const long double b = ((long double)r1.hi + (long double)r1.lo) * norm;
+      if (pprev[i] > 0) dev = std::max(dev, fabsl(a + b - pprev[i]) / pprev[i]);
+      const long double p1 = b / (a + b);
+      const bool click = (long double)uniforms[(size_t)i * n_modes + j] < p1;
+      patterns[(size_t)i * n_modes + j] = click ? 1 : 0;
+      if (click) S[i].push_back(j);
+      pprev[i] = click ? b : a;
+    }
+  }
+  if (first != TOR_OK) return first;
+  if (prob)
+    for (int i = 0; i < count; ++i) prob[i] = (double)pprev[i];
+  if (max_dev) *max_dev = (double)dev;
+  return TOR_OK;
 }
 
 }  // extern "C"
