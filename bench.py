@@ -8,6 +8,8 @@ reduce: every step of the hot path).  Workloads (seeded synthetic inputs):
                               plus a product state at n = 24
   single_n30 / single_n34 / single_n38   one lossy squeezed state of that size
   batch4096                   4096 click patterns k ~ U{4..24} of one 100-mode state
+  serve                       chain-rule marginal requests on a 144-mode state (p50/p99)
+  sample                      threshold-detector patterns drawn by tor_sample on a 40-mode state
 
 Metric: subset terms per second (sum of 2^n over the step's matrices / time).
 `value` times the device-resident path (inputs already on the GPU), `e2e` the
@@ -342,6 +344,42 @@ def run_serve(args, world, rank, local):
     return 0
 
 
+def run_sample(args, world, rank, local):
+    """Chain-rule threshold-detector sampling (tor_sample) on a 40-mode lossy
+    squeezed state (r ~ U[0.5,1.2], eta = 0.5; ~14 clicks per pattern on average)."""
+    if rank != 0:
+        return 0
+    from paper_2109_04528_gb300 import binding, build
+    build.build()
+    n = 40
+    inst = inputs.lossy_squeezed(n, inputs.SEED_BASE + 9, (0.5, 1.2), 0.5)
+    u = inputs.rng_for(inputs.SEED_BASE + 21).uniform(0.0, 1.0, size=(args.sample_count, n))
+    flags = binding.TOR_EXTENDED if args.extended else 0
+    ctx = binding.Context(device=local, flags=flags)
+    sess = binding.Session(ctx, inst.sigma)
+    binding.tor_sample(ctx, sess, u[:16])  # warm-up
+    t0 = time.perf_counter()
+    pat, prob, dev = binding.tor_sample(ctx, sess, u)
+    el = time.perf_counter() - t0
+    # subset terms of the two evaluations per step: 2^|S| + 2^(|S|+1), S = clicks before the step
+    before = np.cumsum(pat, axis=1) - pat
+    terms = float((3.0 * np.exp2(before)).sum())
+    k = pat.sum(axis=1)
+    out = {"metric": "samples/s", "value": len(u) / el, "unit": "samples/s", "n_gpus": 1,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f64x2" if args.extended else "f64", "data": "synthetic",
+           "config": {"workload": "sample", "state": f"{n}-mode lossy squeezed, r~U[0.5,1.2], eta=0.5",
+                      "samples": len(u), "modes": n,
+                      "per_step": "Tor(O^(j+1)_S) and Tor(O^(j+1)_{S u {j}}) through the serving loop"},
+           "seconds": el, "terms_per_s": terms / el, "tor_per_s": 2.0 * len(u) * n / el,
+           "mean_clicks": float(k.mean()), "max_clicks": int(k.max()),
+           "min_log10_prob": float(np.log10(prob.min())), "chain_rule_max_dev": dev}
+    ctx.close()
+    sess.close()
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -357,6 +395,7 @@ def main():
                     help="double-double factor arithmetic (TOR_EXTENDED)")
     ap.add_argument("--autotune", type=float, default=0.0,
                     help="seconds for the prefix-depth autotuner before timing (0 = built-in plan)")
+    ap.add_argument("--sample-count", type=int, default=1000, help="sample: patterns to draw")
     ap.add_argument("--serve-window", type=float, default=2.0, help="serve: seconds of the overload window")
     ap.add_argument("--serve-rate", type=float, default=2000.0, help="serve: offered requests/s")
     ap.add_argument("--serve-sustain-rate", type=float, default=40.0, help="serve: sustainable requests/s")
@@ -370,6 +409,8 @@ def main():
         return run_reference(args, world, rank)
     if args.workload == "serve":
         return run_serve(args, world, rank, local)
+    if args.workload == "sample":
+        return run_sample(args, world, rank, local)
 
     import torch
 

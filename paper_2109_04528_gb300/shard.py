@@ -1,4 +1,5 @@
-"""Sharding one Torontonian across processes (one per GPU).
+"""Sharding across processes (one per GPU): one Torontonian by leaf ranges,
+or a batch of Torontonians by matrices.
 
 The final reduction of tor_eval is a fixed binary tree over the matrix's
 reduction leaves (its warp tasks).  A shard evaluates an aligned power-of-two
@@ -49,6 +50,41 @@ def tree_merge(parts):
     return parts[0]
 
 
+def partition_batch(ns, world: int):
+    """Splits a batch of matrices with n_i modes over `world` ranks by cost
+    2^n_i: largest first, each to the rank with the least work so far (lowest
+    rank on ties).  Returns one list of batch indices per rank, each in
+    ascending order.  Deterministic, so every rank computes the same split."""
+    if world < 1:
+        raise ValueError("world must be >= 1")
+    load = [0] * world
+    parts = [[] for _ in range(world)]
+    for i in sorted(range(len(ns)), key=lambda i: (-ns[i], i)):
+        r = min(range(world), key=lambda q: (load[q], q))
+        parts[r].append(i)
+        load[r] += 1 << ns[i]
+    return [sorted(p) for p in parts]
+
+
+def distributed_batch(evaluate, ns, group=None):
+    """Evaluates a batch split by partition_batch: `evaluate(indices)` returns
+    this rank's (hi, lo, abs) per index; one all-gather returns every rank the
+    whole batch's results in batch order.  A matrix's result does not depend
+    on the batch it is evaluated in, so this equals one rank's tor_eval_batch."""
+    import torch.distributed as dist
+    world, rank = dist.get_world_size(group), dist.get_rank(group)
+    mine = partition_batch(ns, world)[rank]
+    got = evaluate(mine)
+    rows = [(i, tuple(float(v) for v in r)) for i, r in zip(mine, got)]
+    allr = [None] * world
+    dist.all_gather_object(allr, rows, group=group)
+    out = [None] * len(ns)
+    for rows_r in allr:
+        for i, r in rows_r:
+            out[i] = r
+    return out
+
+
 def gather_merge(partial, group=None):
     """All-gather each rank's (hi, lo, abs) (torch.distributed) and merge in rank order."""
     import torch.distributed as dist
@@ -56,6 +92,17 @@ def gather_merge(partial, group=None):
     got = [None] * world
     dist.all_gather_object(got, tuple(float(v) for v in partial), group=group)
     return tree_merge(got)
+
+
+def distributed_tor_batch(ctx, mats, group=None):
+    """tor_eval_batch of `mats` with the matrices split over the ranks of `group`."""
+    from . import binding
+    ns = [m.shape[0] // 2 for m in mats]
+
+    def evaluate(idx):
+        res = binding.tor_eval_batch(ctx, [mats[i] for i in idx]) if idx else []
+        return [(r.hi, r.lo, r.abs_sum) for r in res]
+    return distributed_batch(evaluate, ns, group)
 
 
 def distributed_tor(ctx, O, group=None):

@@ -1,6 +1,7 @@
 """GPU side of sharding: the leaves of one matrix split into 1, 2, 4, 8 aligned
 ranges (as 1..8 GPUs would take them), each evaluated with tor_eval_range,
 merged on the host, reproduce tor_eval bitwise."""
+import numpy as np
 import pytest
 
 from paper_2109_04528_gb300 import binding, inputs, shard
@@ -25,3 +26,18 @@ def test_ranges_merge_to_tor_eval_bitwise():
             assert merged == (full.hi, full.lo, full.abs_sum), world
         with pytest.raises(binding.TorError):
             binding.tor_eval_range(c, inst.O, 1, 2)  # not aligned
+
+
+def test_batch_partition_merges_to_tor_eval_batch_bitwise():
+    # each rank's share of a batch, evaluated as its own batch, gives the same
+    # bits as the whole batch in one call
+    rng = np.random.default_rng(4)
+    ns = [int(k) for k in rng.integers(3, 21, size=30)]
+    mats = [inputs.lossy_squeezed(n, 3100 + i, (0.5, 1.2), 0.4).O for i, n in enumerate(ns)]
+    with binding.Context(device=0) as c:
+        whole = binding.tor_eval_batch(c, mats)
+        for world in (2, 4):
+            for part in shard.partition_batch(ns, world):
+                got = binding.tor_eval_batch(c, [mats[i] for i in part]) if part else []
+                for i, r in zip(part, got):
+                    assert (r.hi, r.lo, r.abs_sum) == (whole[i].hi, whole[i].lo, whole[i].abs_sum)

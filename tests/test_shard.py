@@ -84,3 +84,48 @@ def test_two_ranks_gloo_match_single_process(oracle_mod, tmp_path):
     assert r0 == tuple(single)
     full = oracle_mod.tor_brute(O)
     assert abs((r0[0] - full.hi) + (r0[1] - full.lo)) <= 1e-25 * full.abs_sum
+
+
+def test_partition_batch_balances_cost():
+    ns = [20, 3, 18, 18, 12, 20, 5, 19]
+    parts = shard.partition_batch(ns, 3)
+    assert sorted(i for p in parts for i in p) == list(range(len(ns)))
+    loads = [sum(1 << ns[i] for i in p) for p in parts]
+    assert max(loads) <= 2 ** 20 + 2 ** 19  # LPT: the two n=20 on different ranks
+    assert shard.partition_batch(ns, 3) == parts  # deterministic
+    assert shard.partition_batch(ns, 1) == [list(range(len(ns)))]
+
+
+def _batch_rank_main(rank, world, port, out_dir):
+    import torch.distributed as dist
+
+    import oracle
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    mats = [inputs.lossy_squeezed(n, 300 + i, (0.5, 1.2), 0.4).O for i, n in enumerate(BATCH_NS)]
+
+    def evaluate(idx):
+        return [(r.hi, r.lo, r.abs_sum) for r in (oracle.tor_brute(mats[i], threads=1) for i in idx)]
+    out = shard.distributed_batch(evaluate, BATCH_NS)
+    np.save(os.path.join(out_dir, f"b{rank}.npy"), np.array(out))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+BATCH_NS = [6, 2, 7, 4, 7, 1, 5]
+
+
+def test_batch_two_ranks_gloo_match_single_process(oracle_mod, tmp_path):
+    import socket
+
+    import torch.multiprocessing as mp
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    port = s.getsockname()[1]
+    s.close()
+    mp.start_processes(_batch_rank_main, args=(2, port, str(tmp_path)), nprocs=2, join=True, start_method="spawn")
+    b0, b1 = np.load(tmp_path / "b0.npy"), np.load(tmp_path / "b1.npy")
+    assert np.array_equal(b0, b1)
+    for i, n in enumerate(BATCH_NS):
+        r = oracle_mod.tor_brute(inputs.lossy_squeezed(n, 300 + i, (0.5, 1.2), 0.4).O, threads=1)
+        assert tuple(b0[i]) == (r.hi, r.lo, r.abs_sum)
