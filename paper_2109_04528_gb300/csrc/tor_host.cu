@@ -369,11 +369,30 @@ static tor_status slot_prepare(tor_ctx* ctx, Slot& S, const std::vector<MatIn>& 
     S.lane_e = std::max(S.lane_e, lane_elems_for(m.n, p));
     S.warp_e = std::max(S.warp_e, warp_elems_for(m.n, p));
   }
-  // warp tasks, largest subtrees first
+  // warp tasks, largest subtrees first.  All tasks of one size group (equal n,
+  // adjacent after the sort above) share M, so ordering the groups stably by M
+  // and emitting their tasks in order is a stable sort of the tasks by M.
+  struct Group {
+    int j, k, M;
+  };
+  std::vector<Group> groups;
+  long long ntasks = 0;
   for (int j = 0; j < J;) {
     int k = j;
     while (k < J && S.mats[k].n == S.mats[j].n) ++k;
-    const int p = S.mats[j].p, M = S.mats[j].n - p;
+    const int p = S.mats[j].p;
+    groups.push_back({j, k, S.mats[j].n - p});
+    for (int a = j; a < k && p >= 5; ++a) {
+      const MatIn& m = ins[S.act[a]];
+      ntasks += m.leaf_count > 0 ? m.leaf_count : (1ll << (p - 5));
+    }
+    if (p < 5) ntasks += ((((long long)(k - j)) << p) + 31) / 32;
+    j = k;
+  }
+  std::stable_sort(groups.begin(), groups.end(), [](const Group& a, const Group& b) { return a.M > b.M; });
+  S.tasks.reserve((size_t)ntasks);
+  for (const Group& g : groups) {
+    const int j = g.j, k = g.k, p = S.mats[j].p, M = g.M;
     if (p >= 5) {
       for (int a = j; a < k; ++a) {
         const MatIn& m = ins[S.act[a]];
@@ -385,9 +404,7 @@ static tor_status slot_prepare(tor_ctx* ctx, Slot& S, const std::vector<MatIn>& 
       const long long units = (long long)(k - j) << p;
       for (long long t = 0; t * 32 < units; ++t) S.tasks.push_back({j, (int)t, k - j, M});
     }
-    j = k;
   }
-  std::stable_sort(S.tasks.begin(), S.tasks.end(), [](const TaskDesc& a, const TaskDesc& b) { return a.M > b.M; });
   S.want_parts = want_parts;
   // buffers
   const size_t eb = entry_bytes(ctx);
@@ -1244,11 +1261,39 @@ tor_status tor_session_create(tor_ctx* ctx, int n_total, const tor_c128* M, int 
   for (int j = N; j >= 1; --j) {
     const int mj = 2 * j;
     tor_c128* Oj = host.data() + s->off[j];
-    for (int a = 0; a < mj; ++a)
-      for (int b = 0; b < mj; ++b) {
+    if (!s->real) {
+      for (int a = 0; a < mj; ++a)
+        for (int b = 0; b < mj; ++b) {
+          const CL k = K[(size_t)a * m + b];
+          Oj[(size_t)a * mj + b] = tor_c128{(double)((a == b ? 1.0L : 0.0L) - k.re), (double)(-k.im)};
+        }
+    } else {
+      // A physical state: write O^(j) exactly Hermitian and exactly of the form
+      // O(a_u^dag, a_v^dag) = conj O(a_u, a_v), O(a_u^dag, a_v) = conj O(a_u, a_v^dag),
+      // from the average of the (rounding-level different) entries that the
+      // structure identifies, each rounded once.
+      auto o = [&](int a, int b) {
         const CL k = K[(size_t)a * m + b];
-        Oj[(size_t)a * mj + b] = tor_c128{(double)((a == b ? 1.0L : 0.0L) - k.re), (double)(-k.im)};
-      }
+        return CL{(a == b ? 1.0L : 0.0L) - k.re, -k.im};
+      };
+      for (int u = 0; u < j; ++u)
+        for (int v = 0; v <= u; ++v) {
+          const CL x1 = o(2 * u, 2 * v), y1 = o(2 * u + 1, 2 * v + 1), x2 = o(2 * v, 2 * u), y2 = o(2 * v + 1, 2 * u + 1);
+          const CL z1 = o(2 * u, 2 * v + 1), w1 = o(2 * u + 1, 2 * v), z2 = o(2 * v, 2 * u + 1), w2 = o(2 * v + 1, 2 * u);
+          // P(u, v) ~ x1 ~ conj y1 ~ conj x2 ~ y2;  Q(u, v) = Q(v, u) ~ z1 ~ conj w1 ~ z2 ~ conj w2
+          const tor_c128 P{(double)((x1.re + y1.re + x2.re + y2.re) / 4), (double)((x1.im - y1.im - x2.im + y2.im) / 4)};
+          const tor_c128 Q{(double)((z1.re + w1.re + z2.re + w2.re) / 4), (double)((z1.im - w1.im + z2.im - w2.im) / 4)};
+          const tor_c128 Pc{P.re, -P.im}, Qc{Q.re, -Q.im};
+          Oj[(size_t)(2 * u) * mj + 2 * v] = P;
+          Oj[(size_t)(2 * u + 1) * mj + 2 * v + 1] = Pc;
+          Oj[(size_t)(2 * v) * mj + 2 * u] = Pc;
+          Oj[(size_t)(2 * v + 1) * mj + 2 * u + 1] = P;
+          Oj[(size_t)(2 * u) * mj + 2 * v + 1] = Q;
+          Oj[(size_t)(2 * u + 1) * mj + 2 * v] = Qc;
+          Oj[(size_t)(2 * v) * mj + 2 * u + 1] = Q;
+          Oj[(size_t)(2 * v + 1) * mj + 2 * u] = Qc;
+        }
+    }
     if (j == 1) {
       const long double d1 = K[0].re * K[(size_t)m + 1].re - (K[1].re * K[1].re + K[1].im * K[1].im);
       if (!(d1 > 0)) {
