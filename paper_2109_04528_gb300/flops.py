@@ -115,6 +115,27 @@ def path_flops(n: int, path: int = 0) -> float:
     return f
 
 
+def path_ops(n: int, path: int) -> float:
+    """FP64 instructions (add, mul and FMA one each) of the double-double walk
+    (path bit 1), counted like path_flops: two_sum 6, fast_two_sum 3, two_prod
+    2, an accumulated product 12, a sum started from a product 4, its
+    normalisation 6, dd_mul 7, dd_add 20, reciprocal 13, reciprocal square
+    root 19 (each with its hardware estimate):
+      real     60 m^2 + 94 m + 82 per include, 69 per leaf pair
+      complex 216 m^2 + 176 m + 101 per include, 81 per leaf pair
+    plus 10.5 per leaf.  The FP64 pipe issues one of these per slot whatever
+    its kind, so ops / (the measured DFMA rate) is the pipe's busy fraction
+    in algorithmic work."""
+    if not path & 2:
+        raise ValueError("path_ops counts the double-double walk (path bit 1)")
+    a, b, c, pair = (60, 94, 82, 69.0) if path & 1 else (216, 176, 101, 81.0)
+    f = 10.5 * 2.0 ** n + pair * 2.0 ** (n - 1)
+    for j in range(n - 1):
+        m = n - 1 - j
+        f += 2.0 ** j * (a * m * m + b * m + c)
+    return f
+
+
 def fit_omega(counts: dict[int, int]) -> tuple[float, float]:
     """Least-squares fit of Eq. (linear_fit): ln F - (N/2) ln 2 = omega ln N + C
     over the given {N: FLOs}.  Returns (omega, C)."""

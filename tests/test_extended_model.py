@@ -23,7 +23,12 @@ from paper_2109_04528_gb300 import flops, inputs
 
 class Ops:
     def __init__(self):
-        self.f = 0
+        self.f = 0    # flops (FMA 2)
+        self.fmas = 0
+
+    @property
+    def ops(self):  # FP64 instructions (FMA 1)
+        return self.f - self.fmas
 
     def add(self, a, b):
         self.f += 1
@@ -39,6 +44,7 @@ class Ops:
 
     def fma(self, a, b, c):
         self.f += 2
+        self.fmas += 1
         return float(Fraction(a) * Fraction(b) + Fraction(c))
 
     # error-free transformations
@@ -297,6 +303,7 @@ def model_tor(O, real):
     acc = [(0.0, 0.0)]
     walk(A, S, n, (1.0, 0.0), 0, acc, o)
     h, l = acc[0]
+    model_tor.ops = o.ops
     return Fraction(h) + Fraction(l), o.f
 
 
@@ -306,6 +313,7 @@ def test_count_equals_path_flops(n, real):
     O = inputs.lossy_squeezed(n, 31 + n, (0.3, 0.8), 0.5).O
     _, f = model_tor(O, real)
     assert f == flops.path_flops(n, 2 | (1 if real else 0))
+    assert model_tor.ops == flops.path_ops(n, 2 | (1 if real else 0))
 
 
 @pytest.mark.parametrize("real", [True, False])
