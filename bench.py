@@ -71,7 +71,7 @@ def profiled_traffic(workload_name: str, kernel: str = "k_units"):
     """DRAM bytes per launch of `kernel` from the committed ncu capture, if it
     was taken of that kernel on this workload and on the sources as they are now."""
     try:
-        with open(os.path.join(ROOT, "profiles", "k_units_traffic.json")) as f:
+        with open(os.path.join(ROOT, "profiles", f"{kernel}_traffic.json")) as f:
             t = json.load(f)
     except (OSError, ValueError):
         return None
