@@ -27,6 +27,7 @@ def ctx(request):
     build.build()
     flags = binding.TOR_COMPLEX_PATH if request.param == "complex" else 0
     c = binding.Context(device=0, flags=flags)
+    c.kind = request.param
     yield c
     c.close()
 
@@ -87,8 +88,10 @@ def test_every_prefix_depth_agrees(ctx, oracle_mod):
         ctx.set_prefix_depth(n, old)
 
 
-@pytest.mark.parametrize("n", [6, 13, 20, 24])
+@pytest.mark.parametrize("n", [6, 13, 20, 24, 30, 34, 38])
 def test_product_state_closed_form(ctx, n):
+    if n > 30 and ctx.kind == "complex":
+        pytest.skip("n = 34, 38 on the real path only (the complex path takes ~2.5x as long)")
     inst = inputs.product_state(n, 700 + n)
     want, absum = closed_product(inst)
     r = binding.tor_eval(ctx, inst.O)
@@ -103,6 +106,21 @@ def test_high_squeezing_product_relative(ctx):
     want, absum = closed_product(inst)
     r = binding.tor_eval(ctx, inst.O)
     assert abs(r.tor - want) <= 1e-9 * abs(want)
+
+
+@pytest.mark.parametrize("n", [30, 38])
+def test_high_squeezing_product_within_err_est(ctx, n):
+    # kappa = prod (x+1)/(x-1) stays moderate (~1e8 at n = 38), so the library's
+    # stated a-priori bound err_est = 8 n u sum|term| is a real test of Tor itself
+    if n > 30 and ctx.kind == "complex":
+        pytest.skip("n = 38 on the real path only")
+    inst = inputs.product_state(n, 91 + n, (1.5, 2.5), (0.8, 1.0))
+    want, absum = closed_product(inst)
+    r = binding.tor_eval(ctx, inst.O)
+    assert r.status == 0
+    assert absum / abs(want) < 1e12
+    assert abs(r.tor - want) <= r.err_est, (r.tor, want, r.err_est)
+    assert abs(r.abs_sum - absum) <= 1e-11 * absum
 
 
 def test_vacuum_is_exactly_zero(ctx):
@@ -170,11 +188,12 @@ def test_deterministic_repeat(ctx):
     assert (a.hi, a.lo, a.abs_sum) == (b.hi, b.lo, b.abs_sum)
 
 
-def test_units_at_full_size_sampled(ctx, oracle_mod):
-    # n = 24 (the largest single size of the n=16/20/24 workload) in the launch
-    # configuration the benchmark uses: sampled unit partials vs the oracle,
-    # the total vs the sum of the partials.
-    inst = inputs.config_single(24)
+@pytest.mark.parametrize("n", [24, 30])
+def test_units_at_full_size_sampled(ctx, oracle_mod, n):
+    # n = 24 (the largest single size of the n=16/20/24 workload) and n = 30 (the
+    # single_n30 workload) in the launch configuration the benchmark uses: sampled
+    # unit partials vs the oracle, the total vs the sum of the partials.
+    inst = inputs.config_single(n)
     res, p, parts = binding.tor_eval_units(ctx, inst.O)
     assert res.status == 0 and p >= 5
     rng = np.random.default_rng(2)
