@@ -70,9 +70,42 @@ struct ResultRec {
   int flags, pad;
 };
 
-// Element counts of the scratch a task needs (complex128 elements).
-long long lane_elems_for(int n, int p);
-long long warp_elems_for(int n, int p);
+// ---- scratch sizes, in entries of the arithmetic's own type (one definition
+// for the kernels, the host runtime and the allocation-free entry point) ----
+__host__ __device__ constexpr int tri_size(int m) { return m * (2 * m + 1); }  // packed entries, m modes
+// sum_{k=4}^{m-1} k(2k+1): offset of the lane stack buffer for m modes past the root
+__host__ __device__ constexpr int stack_off(int m) {
+  int s = 0;
+  for (int k = 4; k < m; ++k) s += tri_size(k);
+  return s;
+}
+// breadth-first fan-out arena of a task: level d's include children (2^d nodes of m0 - d - 1 modes)
+__host__ __device__ constexpr int arena_off(int m0, int d) {
+  int s = 0;
+  for (int e = 0; e < d; ++e) s += (1 << e) * tri_size(m0 - e - 1);
+  return s;
+}
+// pivot-column scratch (one of the two arrays) of a task-node build: 2R entries
+// per node being included, R = 2(m - 1) rows; the prefix includes take one node
+// of up to n modes, fan-out level d takes its 2^d nodes of m0 - d modes at once
+__host__ __device__ constexpr int pivot_cols(int n, int m0) {
+  int c = 4 * n;
+  for (int d = 0; d < 5; ++d) {
+    const int v = (1 << d) * 4 * (m0 - d - 1);
+    c = v > c ? v : c;
+  }
+  return c;
+}
+// per lane (interleaved by lane): unit root, stack buffers, pivot columns
+__host__ __device__ constexpr long long lane_elems_c(int n, int p) {
+  return (long long)(p >= 5 ? tri_size(n - p) : tri_size(n)) + stack_off(n - p) + 4LL * n;
+}
+// per warp (p >= 5 only): task node, fan-out arena, two pivot-column arrays
+__host__ __device__ constexpr long long warp_elems_c(int n, int p) {
+  return p < 5 ? 0 : (long long)tri_size(n) + arena_off(n - p + 5, 5) + 2LL * pivot_cols(n, n - p + 5);
+}
+inline long long lane_elems_for(int n, int p) { return lane_elems_c(n, p); }
+inline long long warp_elems_for(int n, int p) { return warp_elems_c(n, p); }
 
 cudaError_t launch_intake(const MatDesc* d_mats, int nmats, int check, int* d_flags, cudaStream_t s);
 cudaError_t launch_units(const UnitsParams& prm, int grid, cudaStream_t s);

@@ -16,30 +16,7 @@
 namespace tor {
 
 // ------------------------------------------------------------------ helpers
-
-__host__ __device__ __forceinline__ int tri_size(int m) { return m * (2 * m + 1); }  // packed entries, m modes
-// sum_{k=4}^{m-1} k(2k+1): offset of the lane stack buffer for m modes past the root
-__host__ __device__ __forceinline__ int stack_off(int m) {
-  int s = 0;
-  for (int k = 4; k < m; ++k) s += tri_size(k);
-  return s;
-}
-__host__ __device__ __forceinline__ int arena_off(int m0, int d) {  // BFS arena: level d's include children
-  int s = 0;
-  for (int e = 0; e < d; ++e) s += (1 << e) * tri_size(m0 - e - 1);
-  return s;
-}
-
-long long lane_elems_for(int n, int p) {
-  int M = n - p;
-  long long root = p >= 5 ? tri_size(M) : tri_size(n);
-  return root + stack_off(M) + 4LL * n;
-}
-long long warp_elems_for(int n, int p) {
-  if (p < 5) return 0;
-  int m0 = n - p + 5;
-  return (long long)tri_size(n) + arena_off(m0, 5) + 8LL * n;
-}
+// (scratch sizes: tri_size, stack_off, arena_off, pivot_cols in tor_internal.h)
 
 __device__ __forceinline__ unsigned long long global_ns() {
   unsigned long long t;
@@ -76,20 +53,26 @@ __device__ __noinline__ typename S::Re lane_include_mem(const LaneMem<S> L, int 
   return pv.rho;
 }
 
-// Cooperative include: the 32 lanes of a warp split the entries of one node
-// stored contiguously (packed, not interleaved).  Used for the shared upper
-// part of the tree, where nodes are large.  All lanes compute the pivot; the
-// call ends with __syncwarp so the child is visible to every lane.
+// Cooperative include: the lanes of a warp split the entries of nodes stored
+// contiguously (packed, not interleaved).  Used for the shared upper part of
+// the tree, where nodes are large.  The warp is divided into groups of gs
+// lanes (gs = 32 >> d, li = lane within its group); every group includes the
+// first mode of its own node (src, o) with m modes -- all nodes of one
+// breadth-first level at once, so the pivot costs one pass per level, not one
+// per node.  All lanes of a group compute its pivot; xs / ys are the group's
+// pivot-column scratch (2R entries each); the call ends with __syncwarp so the
+// children are visible to every lane.  In place when dst == src and
+// dst_o == o + 2.  Each entry gets the same arithmetic whatever the grouping.
 template <class S>
 __device__ __noinline__ typename S::Re coop_include(const typename S::T* src, int o, int m, typename S::T* dst,
-                                                    int dst_o, typename S::T* xs, typename S::T* ys, bool& bad) {
+                                                    int dst_o, typename S::T* xs, typename S::T* ys, int gs, int li,
+                                                    bool& bad) {
   using T = typename S::T;
-  const int lane = threadIdx.x & (kWarp - 1);
   const Pivot<S> pv = make_pivot<S>(S::re(src[P(o, o)]), src[P(o + 1, o)], S::re(src[P(o + 1, o + 1)]));
   bad |= !pv.ok;
   const int R = 2 * (m - 1);
   // xs[0..R) = x, xs[R..2R) = x / d1; ys[0..R) = y', ys[R..2R) = y' / d2
-  for (int r = lane; r < R; r += kWarp) {
+  for (int r = li; r < R; r += gs) {
     const T x = src[P(o + 2 + r, o)];
     const T y = S::reduce_col(x, src[P(o + 2 + r, o + 1)], pv.cl);
     xs[r] = x;
@@ -99,19 +82,19 @@ __device__ __noinline__ typename S::Re coop_include(const typename S::T* src, in
   }
   __syncwarp();
   const int tot = (R * (R + 1)) / 2;
-  int i = 0, k = lane;
+  int i = 0, k = li;
   while (k > i) {
     k -= i + 1;
     ++i;
   }
-  for (int e = lane; e < tot; e += kWarp) {
+  for (int e = li; e < tot; e += gs) {
     const T xt = xs[R + i], yt = ys[R + i];
     const T sv = src[P(o + 2 + i, o + 2 + k)];
     T out;
     if (k < i) out = S::rank2_off(sv, xt, xs[k], yt, ys[k]);
     else out = S::diag(S::rank2_diag(S::re(sv), xt, xs[i], yt, ys[i]));
     dst[P(dst_o + i, dst_o + k)] = out;
-    k += kWarp;
+    k += gs;
     while (k > i) {
       k -= i + 1;
       ++i;
@@ -361,7 +344,7 @@ __device__ void run_task_shared(const UnitsParams& prm, const TaskDesc T, int la
   E* SB = WS;
   E* arena = WS + tri_size(n);
   E* xsw = arena + arena_off(m0, 5);
-  E* ysw = xsw + 4 * n;
+  E* ysw = xsw + pivot_cols(n, m0);
   bool bad = false;
   // 1. task node: decisions on modes 0..p-6 are the bits of T.sub (same for all lanes)
   const E* src = (const E*)D.B;
@@ -372,12 +355,12 @@ __device__ void run_task_shared(const UnitsParams& prm, const TaskDesc T, int la
     if ((T.sub >> j) & 1) {
       Re rho;
       if (!own) {
-        rho = coop_include<S>(src, o, n - j, SB, 0, xsw, ysw, bad);
+        rho = coop_include<S>(src, o, n - j, SB, 0, xsw, ysw, kWarp, lane, bad);
         src = SB;
         o = 0;
         own = true;
       } else {
-        rho = coop_include<S>(SB, o, n - j, SB, o + 2, xsw, ysw, bad);
+        rho = coop_include<S>(SB, o, n - j, SB, o + 2, xsw, ysw, kWarp, lane, bad);
         o += 2;
       }
       phi = S::mul(phi, rho);
@@ -386,25 +369,29 @@ __device__ void run_task_shared(const UnitsParams& prm, const TaskDesc T, int la
       o += 2;
     }
   }
-  // 2. breadth-first fan-out: lane q holds level-d node q (bit e of q = decision on mode p-5+e)
+  // 2. breadth-first fan-out: lane q holds level-d node q (bit e of q = decision on mode p-5+e).
+  //    Level d includes all its 2^d nodes at once: lane group g (gs = 32 >> d lanes) takes node g,
+  //    writes its include child to the arena, and lane nodes + g takes that child.
   const E* nptr = src;
   int no = o, nincl = incl;
   Re nphi = phi;
   for (int d = 0; d < 5; ++d) {
-    const int nodes = 1 << d, m = m0 - d;
-    for (int q = 0; q < nodes; ++q) {
-      const E* qp = (const E*)__shfl_sync(0xffffffffu, (unsigned long long)nptr, q);
-      const int qo = __shfl_sync(0xffffffffu, no, q);
-      const Re qphi = S::shfl(nphi, q);
-      const int qincl = __shfl_sync(0xffffffffu, nincl, q);
-      E* dst = arena + arena_off(m0, d) + q * tri_size(m - 1);
-      const Re rho = coop_include<S>(qp, qo, m, dst, 0, xsw, ysw, bad);
-      if (lane == (q | nodes)) {
-        nptr = dst;
-        no = 0;
-        nphi = S::mul(qphi, rho);
-        nincl = qincl + 1;
-      }
+    const int nodes = 1 << d, m = m0 - d, gs = kWarp >> d, R = 2 * (m - 1);
+    const int g = lane / gs, li = lane % gs;
+    const E* gp = (const E*)__shfl_sync(0xffffffffu, (unsigned long long)nptr, g);
+    const int go = __shfl_sync(0xffffffffu, no, g);
+    const Re rho = coop_include<S>(gp, go, m, arena + arena_off(m0, d) + g * tri_size(m - 1), 0, xsw + g * 2 * R,
+                                   ysw + g * 2 * R, gs, li, bad);
+    // the lane taking node q's include child reads q's phi, its count and rho (held by group q)
+    const int q = lane >= nodes && lane < 2 * nodes ? lane - nodes : 0;
+    const Re qphi = S::shfl(nphi, q);
+    const int qincl = __shfl_sync(0xffffffffu, nincl, q);
+    const Re qrho = S::shfl(rho, q * gs);
+    if (lane >= nodes && lane < 2 * nodes) {
+      nptr = arena + arena_off(m0, d) + q * tri_size(m - 1);
+      no = 0;
+      nphi = S::mul(qphi, qrho);
+      nincl = qincl + 1;
     }
     if (lane < nodes) no += 2;
   }

@@ -42,34 +42,15 @@ constexpr int kLanes = 32;           // lanes per warp (lane stacks are interlea
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocBytes];
 
 __host__ __device__ constexpr size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
-constexpr int tri_c(int m) { return m * (2 * m + 1); }
 __host__ __device__ constexpr int plan_p(int n) { return n > kNoallocMmax ? n - kNoallocMmax : 0; }
-constexpr int stack_c(int M) {
-  int s = 0;
-  for (int k = 4; k < M; ++k) s += tri_c(k);
-  return s;
-}
-constexpr long long lane_elems_c(int n) {
-  // same layout as lane_elems_for(n, plan_p(n)) in tor_kernels.cu
-  return (plan_p(n) >= 5 ? tri_c(n - plan_p(n)) : tri_c(n)) + stack_c(n - plan_p(n)) + 4LL * n;
-}
 constexpr long long max_lane_elems() {
   long long m = 0;
-  for (int n = 1; n <= kNoallocMaxN; ++n) m = lane_elems_c(n) > m ? lane_elems_c(n) : m;
+  for (int n = 1; n <= kNoallocMaxN; ++n) m = lane_elems_c(n, plan_p(n)) > m ? lane_elems_c(n, plan_p(n)) : m;
   return m;
 }
 constexpr long long max_warp_elems() {
-  // warp_elems_for(n, p) for p >= 5: tri(n) + arena(m0 = n - p + 5, 5 levels) + 8n
   long long m = 0;
-  for (int n = 1; n <= kNoallocMaxN; ++n) {
-    const int p = plan_p(n);
-    if (p < 5) continue;
-    const int m0 = n - p + 5;
-    long long a = 0;
-    for (int e = 0; e < 5; ++e) a += (1LL << e) * tri_c(m0 - e - 1);
-    const long long w = tri_c(n) + a + 8LL * n;
-    m = w > m ? w : m;
-  }
+  for (int n = 1; n <= kNoallocMaxN; ++n) m = warp_elems_c(n, plan_p(n)) > m ? warp_elems_c(n, plan_p(n)) : m;
   return m;
 }
 constexpr int kWarps = kNoallocBlocks * 4;
@@ -82,7 +63,7 @@ constexpr size_t OFF_MATS = align256(OFF_FLAGS + sizeof(int));           // one 
 constexpr size_t OFF_TASKS = align256(OFF_MATS + sizeof(MatDesc));      // <= 32 TaskDesc
 constexpr size_t OFF_RES = align256(OFF_TASKS + 64 * sizeof(TaskDesc));  // one ResultRec
 constexpr size_t OFF_B = align256(OFF_RES + sizeof(ResultRec));
-constexpr size_t OFF_PARTS = align256(OFF_B + sizeof(double2) * tri_c(kNoallocMaxN));
+constexpr size_t OFF_PARTS = align256(OFF_B + sizeof(double2) * tri_size(kNoallocMaxN));
 constexpr size_t OFF_REDS = align256(OFF_PARTS + sizeof(Part) * kMaxUnits);
 constexpr size_t OFF_LANE = align256(OFF_REDS + sizeof(Part) * kMaxUnits);
 constexpr size_t OFF_WARP = align256(OFF_LANE + (size_t)kLaneEntryBytes * kLanes * max_lane_elems() * kWarps);
