@@ -249,8 +249,10 @@ static int default_prefix_depth(int n, int nwarps) {
   while ((2ll << lw) <= std::max(nwarps, 1)) ++lw;
   int p;
   if (n <= lw + 9) p = n - 4;
-  else if (n <= lw + 15) p = lw + 5;
-  else p = lw + 8;
+  else if (n <= lw + 13) p = lw + 5;
+  else if (n <= lw + 15) p = lw + 6;
+  else if (n <= lw + 20) p = lw + 8;
+  else p = lw + 9;
   return std::max(0, std::min(p, n - 1));
 }
 
