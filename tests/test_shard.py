@@ -129,3 +129,37 @@ def test_batch_two_ranks_gloo_match_single_process(oracle_mod, tmp_path):
     for i, n in enumerate(BATCH_NS):
         r = oracle_mod.tor_brute(inputs.lossy_squeezed(n, 300 + i, (0.5, 1.2), 0.4).O, threads=1)
         assert tuple(b0[i]) == (r.hi, r.lo, r.abs_sum)
+
+
+def _bench_rank_main(rank, world, port, out_dir):
+    import sys
+
+    import torch.distributed as dist
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    import bench
+
+    class Args:
+        impl = "reference"  # the reference arm's rendezvous uses gloo
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), WORLD_SIZE=str(world), RANK=str(rank),
+                      LOCAL_RANK=str(rank))
+    w, r, local = bench.dist_setup(Args())
+    bench.barrier(w)
+    got = bench.max_over_ranks(w, 10.0 + r, "cpu")  # each rank's time; the job's is the slowest
+    np.save(os.path.join(out_dir, f"m{rank}.npy"), np.array([w, r, local, got]))
+    bench.barrier(w)
+    dist.destroy_process_group()
+
+
+def test_bench_rank_helpers_gloo(tmp_path):
+    # the bench's multi-rank plumbing (rendezvous, barrier, max over ranks) on two CPU ranks
+    import socket
+
+    import torch.multiprocessing as mp
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    port = s.getsockname()[1]
+    s.close()
+    mp.start_processes(_bench_rank_main, args=(2, port, str(tmp_path)), nprocs=2, join=True, start_method="spawn")
+    for rank in range(2):
+        w, r, local, got = np.load(tmp_path / f"m{rank}.npy")
+        assert (w, r, local, got) == (2, rank, rank, 11.0)
