@@ -175,30 +175,63 @@ def max_over_ranks(world, x: float, device) -> float:
     return float(t.item())
 
 
+def spread_sample(n: int, count: int):
+    """(stride, count) of a sample of the 2^n subset masks, k * stride for k < count, spread over
+    the whole range with an odd stride, so that it has the subset-size mix of the full sum (the
+    first masks alone hold only the low modes: small, cheap determinants)."""
+    count = max(1, min(int(count), 1 << n))
+    if count >= (1 << n) or count == 1:
+        return 1, count
+    stride = ((1 << n) - 1) // (count - 1)
+    stride -= 1 - stride % 2
+    return max(stride, 1), count
+
+
+def cpu_model() -> str:
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith(("model name", "cpu model")):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    import platform
+    return platform.machine()
+
+
+def timed_oracle(O, cores: int, count: int):
+    import oracle
+    n = O.shape[0] // 2
+    stride, count = spread_sample(n, count)
+    t0 = time.perf_counter()
+    oracle.tor_brute(O, threads=cores, stride=stride, count=count)
+    return time.perf_counter() - t0, stride, count
+
+
 def cpu_baseline(mats, budget_s: float):
-    """The oracle (binary128 brute force) on a bounded sample: the first `count`
-    subsets of the workload's largest matrix, on all host cores."""
+    """The oracle (binary128 brute force) on a bounded sample of the workload's
+    largest matrix -- subsets spread over all 2^n masks -- on all host cores."""
     import oracle
     oracle.build()
     O = max(mats, key=lambda a: a.shape[0])
     n = O.shape[0] // 2
     cores = os.cpu_count() or 1
     count = 1 << min(n, 10)
-    t0 = time.perf_counter()
-    oracle.tor_brute(O, threads=cores, count=count)
-    dt = time.perf_counter() - t0
+    dt, _, count = timed_oracle(O, cores, count)
     while dt < 0.5 and count < (1 << n):  # calibrate
-        count = min(1 << n, count * 4)
-        t0 = time.perf_counter()
-        oracle.tor_brute(O, threads=cores, count=count)
-        dt = time.perf_counter() - t0
+        dt, _, count = timed_oracle(O, cores, min(1 << n, count * 4))
     count = int(min(1 << n, max(count, count * budget_s / max(dt, 1e-3))))
-    t0 = time.perf_counter()
-    oracle.tor_brute(O, threads=cores, count=count)
-    dt = time.perf_counter() - t0
-    return {"value": count / dt, "unit": "subset terms/s", "cores": cores, "kind": "oracle",
-            "sample": f"first {count} of the 2^{n} subsets of the n={n} matrix, binary128 LU per subset, "
-                      f"{dt:.1f} s"}
+    dt, stride, count = timed_oracle(O, cores, count)
+    return {"value": count / dt, "unit": "subset terms/s", "cores": cores, "cpu": cpu_model(), "kind": "oracle",
+            "sample": f"{count} of the 2^{n} subsets of the n={n} matrix (masks k*{stride}, spread over all), "
+                      f"binary128 LU per subset, {dt:.1f} s"}
 
 
 def run_reference(args, world, rank):
@@ -210,27 +243,25 @@ def run_reference(args, world, rank):
     cores = os.cpu_count() or 1
     O = max(mats, key=lambda a: a.shape[0])
     n = O.shape[0] // 2
-    # size one step to ~2 s of CPU work
-    count = 1 << min(n, 8)
-    t0 = time.perf_counter()
-    oracle.tor_brute(O, threads=cores, count=count)
-    dt = time.perf_counter() - t0
+    # size one step to ~2 s of CPU work, subsets spread over all 2^n masks
+    dt, _, count = timed_oracle(O, cores, 1 << min(n, 8))
     count = int(min(1 << n, max(count, count * 2.0 / max(dt, 1e-3))))
     for _ in range(args.warmup):
-        oracle.tor_brute(O, threads=cores, count=count)
+        timed_oracle(O, cores, count)
     times = []
     for _ in range(args.steps):
-        t0 = time.perf_counter()
-        oracle.tor_brute(O, threads=cores, count=count)
-        times.append(time.perf_counter() - t0)
+        dt, stride, count = timed_oracle(O, cores, count)
+        times.append(dt)
     tot = sum(times)
     value = count * args.steps / tot
     line = {"impl": "reference", "metric": "subset terms/s", "value": value, "unit": "subset terms/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f128",
             "data": "synthetic", "config": {"workload": args.workload, "desc": desc},
-            "cpu_baseline": {"value": value, "unit": "subset terms/s", "cores": cores, "kind": "oracle",
-                             "sample": f"each step: first {count} of the 2^{n} subsets of the n={n} matrix"},
+            "cpu_baseline": {"value": value, "unit": "subset terms/s", "cores": cores, "cpu": cpu_model(),
+                             "kind": "oracle",
+                             "sample": f"each step: {count} of the 2^{n} subsets of the n={n} matrix "
+                                       f"(masks k*{stride}, spread over all)"},
             "e2e": {"value": value, "unit": "subset terms/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
