@@ -567,6 +567,7 @@ def main():
     line = {
         "metric": "subset terms/s", "value": value, "unit": "subset terms/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": tot_ms / args.steps,
+        "ms_per_step_median": statistics.median(ms),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64x2" if ext else "f64",
         "data": "synthetic",
         "config": {"workload": args.workload, "desc": desc, "n": ns, "terms_per_step": terms,

@@ -180,3 +180,20 @@ def test_inexact_structure_takes_complex_path(xctx, oracle_mod):
     o = oracle_mod.tor_brute(O)
     assert r.path == 2
     assert err(r, o) <= TOL_X * o.abs_sum
+
+
+def test_graph_replay_and_served_equal_plain(xctx):
+    # the same matrices through a CUDA-graph context and through the serving loop:
+    # bitwise the plain extended result
+    rng = np.random.default_rng(21)
+    mats = [inputs.lossy_squeezed(int(k), 1500 + i, (0.5, 1.2), 0.4).O for i, k in enumerate(rng.integers(4, 15, 8))]
+    plain = binding.tor_eval_batch(xctx, mats)
+    flags = binding.TOR_EXTENDED | binding.TOR_GRAPHS | (binding.TOR_COMPLEX_PATH if xctx.kind == "complex" else 0)
+    with binding.Context(device=0, flags=flags) as g:
+        for _ in range(2):  # capture, then replay
+            got = binding.tor_eval_batch(g, mats)
+            assert [(r.hi, r.lo, r.abs_sum, r.path) for r in got] == [(r.hi, r.lo, r.abs_sum, r.path) for r in plain]
+    tickets = [binding.tor_submit(xctx, O) for O in mats]
+    for t, p in zip(tickets, plain):
+        st, r = binding.tor_poll(xctx, t, 60.0)
+        assert st == 0 and (r.hi, r.lo, r.abs_sum) == (p.hi, p.lo, p.abs_sum)
