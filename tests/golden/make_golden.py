@@ -2,7 +2,7 @@
 seeded input generator that produces the matrices, which it stores verbatim so
 that every machine reads the same complex128 entries).
 
-Usage: python tests/golden/make_golden.py
+Usage: python tests/golden/make_golden.py [fixture names]  (default: all)
 """
 import json
 import os
@@ -17,7 +17,7 @@ import oracle  # noqa: E402
 from paper_2109_04528_gb300 import inputs  # noqa: E402
 
 
-def write(name, inst, note):
+def write(name, inst, note, units=()):
     r = oracle.tor_brute(inst.O)
     rec = {
         "citation": "Eq. (tor), Sec. 1 (definition); values from the binary128 brute-force oracle",
@@ -26,13 +26,34 @@ def write(name, inst, note):
         "O_re": np.real(inst.O).tolist(), "O_im": np.imag(inst.O).tolist(),
         "tor_hi": r.hi, "tor_lo": r.lo, "abs_sum": r.abs_sum,
     }
+    if units:
+        # prefix units (bit j of u = mode j in Z, j < p): each sums the terms whose first p decisions are u
+        p = units[0]
+        rec["unit_p"] = p
+        rec["units"] = []
+        for u in units[1]:
+            q = oracle.tor_unit(inst.O, p, u)
+            rec["units"].append({"u": u, "hi": q.hi, "lo": q.lo, "abs_sum": q.abs_sum})
     with open(os.path.join(HERE, name), "w") as f:
         json.dump(rec, f, indent=0)
         f.write("\n")
 
 
+FIXTURES = {
+    "lossy_n8.json": (inputs.config_n8, "n=8 squeezed vacua r~U[0.3,0.8], Haar U, eta=0.5 (256 subsets)", ()),
+    "lossy_n4_hi.json": (lambda: inputs.lossy_squeezed(4, 99, (1.0, 1.5), 0.7),
+                         "n=4, higher squeezing r~U[1.0,1.5], eta=0.7", ()),
+    "lossy_n20.json": (lambda: inputs.config_single(20),
+                       "n=20 lossy squeezed state of the benchmark's kind (r~U[0.3,0.8], eta_j~U[0.3,0.7]); "
+                       "full brute force over 2^20 subsets", (8, [0, 37, 255])),
+    "lossy_n22.json": (lambda: inputs.config_single(22),
+                       "n=22 lossy squeezed state of the benchmark's kind (r~U[0.3,0.8], eta_j~U[0.3,0.7]); "
+                       "full brute force over 2^22 subsets", (8, [0, 37, 255])),
+}
+
+
 if __name__ == "__main__":
-    write("lossy_n8.json", inputs.config_n8(),
-          "n=8 squeezed vacua r~U[0.3,0.8], Haar U, eta=0.5 (256 subsets)")
-    write("lossy_n4_hi.json", inputs.lossy_squeezed(4, 99, (1.0, 1.5), 0.7),
-          "n=4, higher squeezing r~U[1.0,1.5], eta=0.7")
+    # python tests/golden/make_golden.py [NAME ...]   (default: every fixture)
+    for name in sys.argv[1:] or FIXTURES:
+        make, note, units = FIXTURES[name]
+        write(name, make(), note, units)

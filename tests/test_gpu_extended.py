@@ -197,3 +197,16 @@ def test_graph_replay_and_served_equal_plain(xctx):
     for t, p in zip(tickets, plain):
         st, r = binding.tor_poll(xctx, t, 60.0)
         assert st == 0 and (r.hi, r.lo, r.abs_sum) == (p.hi, p.lo, p.abs_sum)
+
+
+@pytest.mark.parametrize("name", ["lossy_n20.json", "lossy_n22.json"])
+def test_golden_full_brute_force(xctx, name):
+    # n = 20 and 22 against the oracle's stored full brute force, at the double-double bound
+    import json
+    import os
+    with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", name)) as f:
+        g = json.load(f)
+    O = np.array(g["O_re"]) + 1j * np.array(g["O_im"])
+    r = binding.tor_eval(xctx, O)
+    assert r.status == 0
+    assert abs((r.hi - g["tor_hi"]) + (r.lo - g["tor_lo"])) <= TOL_X * g["abs_sum"]

@@ -54,6 +54,30 @@ def test_golden_fixture(ctx):
     assert abs(r.abs_sum - g["abs_sum"]) <= 1e-12 * g["abs_sum"]
 
 
+@pytest.mark.parametrize("name", ["lossy_n20.json", "lossy_n22.json"])
+def test_golden_full_brute_force(ctx, name):
+    # n = 20 and 22 against the oracle's full brute force (stored: minutes of binary128 CPU work),
+    # and prefix units at p = 8 against the stored unit sums
+    with open(os.path.join(HERE, "golden", name)) as f:
+        g = json.load(f)
+    O = np.array(g["O_re"]) + 1j * np.array(g["O_im"])
+    n = g["n"]
+    r = binding.tor_eval(ctx, O)
+    assert r.status == 0
+    assert abs((r.hi - g["tor_hi"]) + (r.lo - g["tor_lo"])) <= TOL * g["abs_sum"]
+    assert abs(r.abs_sum - g["abs_sum"]) <= 1e-12 * g["abs_sum"]
+    old = ctx.plan_prefix_depth(n)
+    try:
+        ctx.set_prefix_depth(n, g["unit_p"])
+        res, p, parts = binding.tor_eval_units(ctx, O)
+        assert p == g["unit_p"]
+        for unit in g["units"]:
+            got_hi, got_lo, got_abs = parts[unit["u"]]
+            assert abs((got_hi - unit["hi"]) + (got_lo - unit["lo"])) <= TOL * unit["abs_sum"]
+    finally:
+        ctx.set_prefix_depth(n, old)
+
+
 @pytest.mark.parametrize("n", [1, 2, 3, 4, 5, 6, 7, 9, 11, 12, 13, 14, 15, 16])
 def test_random_lossy_vs_oracle(ctx, oracle_mod, n):
     inst = inputs.lossy_squeezed(n, 500 + n, (0.3, 0.8), (0.3, 0.7))

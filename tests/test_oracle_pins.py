@@ -161,3 +161,16 @@ def test_golden_fixture_reproduces(oracle_mod, name):
     g, O = load_golden(name)
     r = oracle_mod.tor_brute(O)
     assert r.hi == g["tor_hi"] and abs(r.lo - g["tor_lo"]) <= 1e-30 * g["abs_sum"]
+
+
+@pytest.mark.parametrize("name", ["lossy_n20.json", "lossy_n22.json"])
+def test_large_golden_units_reproduce(oracle_mod, name):
+    # the full brute force over 2^20 / 2^22 subsets takes minutes; its stored prefix
+    # units (2^12 / 2^14 subsets each) are recomputed here
+    g, O = load_golden(name)
+    assert O.shape == (2 * g["n"], 2 * g["n"]) and g["abs_sum"] > 0
+    for unit in g["units"]:
+        r = oracle_mod.tor_unit(O, g["unit_p"], unit["u"])
+        assert r.hi == unit["hi"] and abs(r.lo - unit["lo"]) <= 1e-30 * unit["abs_sum"]
+        assert abs(r.abs_sum - unit["abs_sum"]) <= 1e-15 * unit["abs_sum"]
+        assert unit["abs_sum"] < g["abs_sum"]
