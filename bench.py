@@ -56,26 +56,34 @@ def workload(name: str, rank: int = 0):
     raise SystemExit(f"unknown workload {name}")
 
 
-def csrc_hash() -> str:
+KERNEL_SOURCES = ("tor_device.cuh", "tor_dd.cuh", "tor_internal.h", "tor_kernels.cu")
+
+
+def kernel_hash() -> str:
+    """Hash of the device code (the kernels and the structures they read); the
+    host runtime and the allocation-free entry point are not part of it."""
     import hashlib
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_2109_04528_gb300", "csrc")
-    for f in sorted(os.listdir(d)):
+    for f in KERNEL_SOURCES:
         h.update(f.encode())
         with open(os.path.join(d, f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(workload_name: str, kernel: str = "k_units"):
+def profiled_traffic(workload_name: str, kernel: str = "k_units", prefix_depth=None):
     """DRAM bytes per launch of `kernel` from the committed ncu capture, if it
-    was taken of that kernel on this workload and on the sources as they are now."""
+    was taken of that kernel on this workload, on the kernel sources as they are
+    now and with the same prefix depths (the launch's task decomposition)."""
     try:
         with open(os.path.join(ROOT, "profiles", f"{kernel}_traffic.json")) as f:
             t = json.load(f)
     except (OSError, ValueError):
         return None
-    if t.get("workload") != workload_name or t.get("kernel") != kernel or t.get("csrc_hash") != csrc_hash():
+    if t.get("workload") != workload_name or t.get("kernel") != kernel or t.get("kernel_hash") != kernel_hash():
+        return None
+    if prefix_depth is not None and t.get("prefix_depth") != prefix_depth:
         return None
     return t.get("dram_bytes_per_launch")
 
@@ -579,7 +587,8 @@ def main():
                 "d2h_bytes_per_step": int(32 * len(mats))},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": fp64_tflops, "unit": "TFLOP/s",
                      "frac": achieved / fp64_tflops,
-                     "traffic": profiled_traffic(args.workload, "k_units_ext" if ext else "k_units"),
+                     "traffic": profiled_traffic(args.workload, "k_units_ext" if ext else "k_units",
+                                                 {str(n): ctx_dev.plan_prefix_depth(n) for n in sorted(set(ns))}),
                      "kernel": "k_units_ext" if ext else "k_units",
                      "peak_source": "FP64 DFMA probe (tor_probe_fp64), measured in this run",
                      "flops_per_launch": flops, "units_ms_avg": units_avg,

@@ -20,6 +20,7 @@
 #include <cstring>
 #include <deque>
 #include <map>
+#include <new>
 #include <memory>
 #include <mutex>
 #include <string>
@@ -256,12 +257,15 @@ static int default_prefix_depth(int n, int nwarps) {
   return std::max(0, std::min(p, n - 1));
 }
 
+// Largest prefix depth: 2^30 unit partials (32 GB) and 2^25 warp tasks.
+constexpr int kMaxPrefixDepth = 30;
+
 static int plan_p(tor_ctx* ctx, int n) {
   int p;
   if (ctx->plan[n] >= 0) p = ctx->plan[n];
   else if (ctx->cfg.prefix_depth >= 0) p = ctx->cfg.prefix_depth;
   else p = default_prefix_depth(n, ctx->nwarps);
-  return std::max(0, std::min(p, n - 1));
+  return std::max(0, std::min(std::min(p, n - 1), kMaxPrefixDepth));
 }
 
 // priority: 0 = default; < 0 = the device's highest; > 0 = its lowest
@@ -823,7 +827,18 @@ static void server_loop(tor_ctx* ctx) {
       }
       std::vector<tor_result> res(ins.size());
       bool any = false;
-      tor_status st = slot_prepare(ctx, S, ins, res.data(), false, &any);
+      tor_status st;
+      try {
+        st = slot_prepare(ctx, S, ins, res.data(), false, &any);
+      } catch (const std::bad_alloc&) {
+        any = false;
+        st = TOR_ENOMEM;
+        for (size_t k = 0; k < res.size(); ++k) {
+          res[k] = tor_result{};
+          res[k].n = ins[k].n;
+          res[k].status = TOR_ENOMEM;
+        }
+      }
       if (any) {
         S.cancel_epoch = __atomic_load_n(ctx->h_cancel, __ATOMIC_SEQ_CST);
         S.graphed = false;
@@ -955,6 +970,19 @@ bool hpd_inverse(std::vector<CL>& A, int m) {
 }
 }  // namespace
 
+// Nothing throws across the C ABI: an allocation failure inside an entry point
+// becomes TOR_ENOMEM (locks are scoped, so they are released on the way out).
+template <class F>
+static tor_status guarded(F&& f) {
+  try {
+    return f();
+  } catch (const std::bad_alloc&) {
+    return TOR_ENOMEM;
+  } catch (...) {
+    return TOR_EINVAL;
+  }
+}
+
 extern "C" {
 
 void tor_config_default(tor_config* cfg) {
@@ -989,7 +1017,7 @@ const char* tor_last_error(tor_ctx* ctx) { return ctx ? ctx->last_error.c_str() 
 
 tor_status tor_plan_load(tor_ctx* ctx, const char* path);
 
-tor_status tor_create(const tor_config* cfg, tor_ctx** out) {
+static tor_status tor_create_impl(const tor_config* cfg, tor_ctx** out) {
   if (!out) return TOR_EINVAL;
   *out = nullptr;
   tor_config c;
@@ -1029,6 +1057,10 @@ tor_status tor_create(const tor_config* cfg, tor_ctx** out) {
   }
   *out = ctx;
   return TOR_OK;
+}
+
+tor_status tor_create(const tor_config* cfg, tor_ctx** out) {
+  return guarded([&] { return tor_create_impl(cfg, out); });
 }
 
 void tor_destroy(tor_ctx* ctx) {
@@ -1074,7 +1106,7 @@ int tor_plan_prefix_depth(tor_ctx* ctx, int n) {
 }
 
 tor_status tor_set_prefix_depth(tor_ctx* ctx, int n, int p) {
-  if (!ctx || n < 1 || n > 64 || p < -1 || p > n - 1) return TOR_EINVAL;
+  if (!ctx || n < 1 || n > 64 || p < -1 || p > n - 1 || p > kMaxPrefixDepth) return TOR_EINVAL;
   std::lock_guard<std::mutex> lk(ctx->run_mu);
   ctx->plan[n] = p;
   return TOR_OK;
@@ -1109,7 +1141,7 @@ tor_status tor_probe_fp64(int device, double seconds, double* dfma_per_s, double
   return TOR_OK;
 }
 
-tor_status tor_eval_batch(tor_ctx* ctx, int count, const int* n, const tor_c128* const* O, const int* ld,
+static tor_status tor_eval_batch_impl(tor_ctx* ctx, int count, const int* n, const tor_c128* const* O, const int* ld,
                           tor_result* out) {
   if (!ctx || count < 0 || (count > 0 && (!n || !O || !out))) return TOR_EINVAL;
   std::vector<MatIn> ins(count);
@@ -1126,14 +1158,23 @@ tor_status tor_eval_batch(tor_ctx* ctx, int count, const int* n, const tor_c128*
   return run_blocking(ctx, ins, out, nullptr, 0);
 }
 
-tor_status tor_eval(tor_ctx* ctx, int n, const tor_c128* O, int ld, tor_result* out) {
+tor_status tor_eval_batch(tor_ctx* ctx, int count, const int* n, const tor_c128* const* O, const int* ld,
+                          tor_result* out) {
+  return guarded([&] { return tor_eval_batch_impl(ctx, count, n, O, ld, out); });
+}
+
+static tor_status tor_eval_impl(tor_ctx* ctx, int n, const tor_c128* O, int ld, tor_result* out) {
   if (!ctx || !out) return TOR_EINVAL;
   const tor_c128* Op[1] = {O};
   int lds[1] = {ld};
   return tor_eval_batch(ctx, 1, &n, Op, lds, out);
 }
 
-tor_status tor_eval_units(tor_ctx* ctx, int n, const tor_c128* O, int ld, double* partials, size_t partials_len,
+tor_status tor_eval(tor_ctx* ctx, int n, const tor_c128* O, int ld, tor_result* out) {
+  return guarded([&] { return tor_eval_impl(ctx, n, O, ld, out); });
+}
+
+static tor_status tor_eval_units_impl(tor_ctx* ctx, int n, const tor_c128* O, int ld, double* partials, size_t partials_len,
                           tor_result* out) {
   if (!ctx || !out || !partials || n < 1 || n > 64) return TOR_EINVAL;
   std::vector<MatIn> ins(1);
@@ -1147,13 +1188,18 @@ tor_status tor_eval_units(tor_ctx* ctx, int n, const tor_c128* O, int ld, double
   return run_blocking(ctx, ins, out, partials, partials_len);
 }
 
+tor_status tor_eval_units(tor_ctx* ctx, int n, const tor_c128* O, int ld, double* partials, size_t partials_len,
+                          tor_result* out) {
+  return guarded([&] { return tor_eval_units_impl(ctx, n, O, ld, partials, partials_len, out); });
+}
+
 long long tor_plan_leaves(tor_ctx* ctx, int n) {
   if (!ctx || n < 1 || n > 64) return -1;
   const int p = plan_p(ctx, n);
   return 1ll << (p >= 5 ? p - 5 : p);
 }
 
-tor_status tor_eval_range(tor_ctx* ctx, int n, const tor_c128* O, int ld, long long leaf_lo, long long leaf_count,
+static tor_status tor_eval_range_impl(tor_ctx* ctx, int n, const tor_c128* O, int ld, long long leaf_lo, long long leaf_count,
                           tor_result* out) {
   if (!ctx || !out || n < 1 || n > 64) return TOR_EINVAL;
   const int p = plan_p(ctx, n);
@@ -1175,7 +1221,12 @@ tor_status tor_eval_range(tor_ctx* ctx, int n, const tor_c128* O, int ld, long l
   return run_blocking(ctx, ins, out, nullptr, 0);
 }
 
-tor_status tor_submit(tor_ctx* ctx, int n, const tor_c128* O, int ld, uint64_t* ticket) {
+tor_status tor_eval_range(tor_ctx* ctx, int n, const tor_c128* O, int ld, long long leaf_lo, long long leaf_count,
+                          tor_result* out) {
+  return guarded([&] { return tor_eval_range_impl(ctx, n, O, ld, leaf_lo, leaf_count, out); });
+}
+
+static tor_status tor_submit_impl(tor_ctx* ctx, int n, const tor_c128* O, int ld, uint64_t* ticket) {
   if (!ctx || !ticket || n < 0 || (n > 0 && !O) || ld < 2 * n) return TOR_EINVAL;
   if (n > 64) return TOR_ETOOBIG;
   if (ctx->cfg.flags & TOR_IN_DEVICE) return TOR_EINVAL;  // the queue copies host inputs only
@@ -1189,6 +1240,10 @@ tor_status tor_submit(tor_ctx* ctx, int n, const tor_c128* O, int ld, uint64_t* 
   r->in.n_src = n;
   r->in.layout = ctx->cfg.layout;
   return enqueue_request(ctx, r, ticket);
+}
+
+tor_status tor_submit(tor_ctx* ctx, int n, const tor_c128* O, int ld, uint64_t* ticket) {
+  return guarded([&] { return tor_submit_impl(ctx, n, O, ld, ticket); });
 }
 
 tor_status tor_poll(tor_ctx* ctx, uint64_t ticket, tor_result* out, double timeout_s) {
@@ -1218,7 +1273,7 @@ tor_status tor_serving_stats(tor_ctx* ctx, long long* served, long long* batches
   return TOR_OK;
 }
 
-tor_status tor_session_create(tor_ctx* ctx, int n_total, const tor_c128* M, int ld, int kind,
+static tor_status tor_session_create_impl(tor_ctx* ctx, int n_total, const tor_c128* M, int ld, int kind,
                               tor_session** out) {
   if (!ctx || !out || !M || n_total < 1 || n_total > 1024 || ld < 2 * n_total) return TOR_EINVAL;
   if (kind != TOR_SESSION_SIGMA && kind != TOR_SESSION_O) return TOR_EINVAL;
@@ -1347,6 +1402,11 @@ tor_status tor_session_create(tor_ctx* ctx, int n_total, const tor_c128* M, int 
   return TOR_OK;
 }
 
+tor_status tor_session_create(tor_ctx* ctx, int n_total, const tor_c128* M, int ld, int kind,
+                              tor_session** out) {
+  return guarded([&] { return tor_session_create_impl(ctx, n_total, M, ld, kind, out); });
+}
+
 void tor_session_destroy(tor_session* s) {
   if (!s) return;
   if (tor_ctx* ctx = s->ctx) {
@@ -1408,9 +1468,11 @@ tor_status tor_eval_marginal(tor_ctx* ctx, tor_session* s, int j, int k, const i
     if (s->closing) return TOR_EINVAL;
     ++s->blocking;
   }
-  {
+  try {
     std::lock_guard<std::mutex> lk(ctx->run_mu);
     st = run_blocking(ctx, ins, out, nullptr, 0);
+  } catch (const std::bad_alloc&) {
+    st = TOR_ENOMEM;
   }
   {
     std::lock_guard<std::mutex> lq(ctx->q_mu);
@@ -1420,7 +1482,7 @@ tor_status tor_eval_marginal(tor_ctx* ctx, tor_session* s, int j, int k, const i
   return st;
 }
 
-tor_status tor_submit_marginal(tor_ctx* ctx, tor_session* s, int j, int k, const int* modes, uint64_t* ticket) {
+static tor_status tor_submit_marginal_impl(tor_ctx* ctx, tor_session* s, int j, int k, const int* modes, uint64_t* ticket) {
   if (!ctx || !ticket || !s || s->ctx != ctx) return TOR_EINVAL;
   Request* r = new Request();
   tor_status st = marginal_in(s, j, k, modes, r->in, r->modes);
@@ -1440,11 +1502,15 @@ tor_status tor_submit_marginal(tor_ctx* ctx, tor_session* s, int j, int k, const
   return enqueue_request(ctx, r, ticket);
 }
 
+tor_status tor_submit_marginal(tor_ctx* ctx, tor_session* s, int j, int k, const int* modes, uint64_t* ticket) {
+  return guarded([&] { return tor_submit_marginal_impl(ctx, s, j, k, modes, ticket); });
+}
+
 // Threshold-detector sampling by the chain rule: for every sample, mode j is
 // decided from the two continuations of its clicks S so far on the first
 // j + 1 modes, t0 = Tor(O^(j+1)_S) and t1 = Tor(O^(j+1)_{S u {j}}).  All
 // samples' requests of one step go to the serving loop together.
-tor_status tor_sample(tor_ctx* ctx, tor_session* s, int count, int n_modes, const double* uniforms,
+static tor_status tor_sample_impl(tor_ctx* ctx, tor_session* s, int count, int n_modes, const double* uniforms,
                       unsigned char* patterns, double* prob, double* max_dev) {
   if (!ctx || !s || s->ctx != ctx || count < 0 || n_modes < 1 || n_modes > s->N) return TOR_EINVAL;
   if (count > 0 && (!uniforms || !patterns)) return TOR_EINVAL;
@@ -1497,6 +1563,11 @@ tor_status tor_sample(tor_ctx* ctx, tor_session* s, int count, int n_modes, cons
   return TOR_OK;
 }
 
+tor_status tor_sample(tor_ctx* ctx, tor_session* s, int count, int n_modes, const double* uniforms,
+                      unsigned char* patterns, double* prob, double* max_dev) {
+  return guarded([&] { return tor_sample_impl(ctx, s, count, n_modes, uniforms, patterns, prob, max_dev); });
+}
+
 }  // extern "C"
 
 // ---------------------------------------------------------------------------
@@ -1545,7 +1616,7 @@ static void synthetic_matrix(int n, std::vector<tor_c128>& O, bool structured, i
 
 extern "C" {
 
-tor_status tor_autotune(tor_ctx* ctx, int n_lo, int n_hi, double budget_s, int* chosen) {
+static tor_status tor_autotune_impl(tor_ctx* ctx, int n_lo, int n_hi, double budget_s, int* chosen) {
   if (!ctx || n_lo < 1 || n_hi > 64 || n_lo > n_hi || budget_s <= 0) return TOR_EINVAL;
   if (ctx->cfg.flags & TOR_IN_DEVICE) return TOR_EINVAL;  // times host inputs
   const double per_n = budget_s / (n_hi - n_lo + 1);
@@ -1597,7 +1668,11 @@ tor_status tor_autotune(tor_ctx* ctx, int n_lo, int n_hi, double budget_s, int* 
   return TOR_OK;
 }
 
-tor_status tor_plan_save(tor_ctx* ctx, const char* path) {
+tor_status tor_autotune(tor_ctx* ctx, int n_lo, int n_hi, double budget_s, int* chosen) {
+  return guarded([&] { return tor_autotune_impl(ctx, n_lo, n_hi, budget_s, chosen); });
+}
+
+static tor_status tor_plan_save_impl(tor_ctx* ctx, const char* path) {
   if (!ctx || !path) return TOR_EINVAL;
   FILE* f = fopen(path, "w");
   if (!f) return TOR_EINVAL;
@@ -1617,7 +1692,11 @@ tor_status tor_plan_save(tor_ctx* ctx, const char* path) {
   return TOR_OK;
 }
 
-tor_status tor_plan_load(tor_ctx* ctx, const char* path) {
+tor_status tor_plan_save(tor_ctx* ctx, const char* path) {
+  return guarded([&] { return tor_plan_save_impl(ctx, path); });
+}
+
+static tor_status tor_plan_load_impl(tor_ctx* ctx, const char* path) {
   if (!ctx || !path) return TOR_EINVAL;
   FILE* f = fopen(path, "r");
   if (!f) return TOR_EINVAL;
@@ -1638,6 +1717,10 @@ tor_status tor_plan_load(tor_ctx* ctx, const char* path) {
   std::lock_guard<std::mutex> lk(ctx->run_mu);
   for (auto& r : rows) ctx->plan[r.first] = r.second;
   return TOR_OK;
+}
+
+tor_status tor_plan_load(tor_ctx* ctx, const char* path) {
+  return guarded([&] { return tor_plan_load_impl(ctx, path); });
 }
 
 }  // extern "C"
