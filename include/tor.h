@@ -16,7 +16,8 @@
  *
  * Conventions for every call:
  *   - Every function returns a tor_status; nothing aborts or throws across this
- *     ABI.  Per-matrix failures are reported in tor_result.status.
+ *     ABI (a host allocation that fails inside a call gives TOR_ENOMEM).
+ *     Per-matrix failures are reported in tor_result.status.
  *   - Matrices are row-major complex128 (tor_c128 == numpy complex128 ==
  *     torch.cdouble) with leading dimension `ld` >= 2n, in complex elements.
  *   - Row order is TOR_LAYOUT_BLOCK (a_1..a_n, a_1^dag..a_n^dag) unless the
@@ -229,8 +230,9 @@ const char* tor_last_error(tor_ctx* ctx);
 int tor_plan_prefix_depth(tor_ctx* ctx, int n);
 
 /* Sets the prefix depth used for n modes from now on (the autotuner's entry
- * point).  p in [0, n-1].  Changing it changes the summation order, so
- * results before and after differ in rounding. */
+ * point).  p in [0, min(n-1, 30)] (2^30 unit partials take 32 GB), or -1 for
+ * the built-in plan.  Changing it changes the summation order, so results
+ * before and after differ in rounding. */
 tor_status tor_set_prefix_depth(tor_ctx* ctx, int n, int p);
 
 /* Like tor_eval, but also copies the 2^p per-unit partial sums to the host:
