@@ -111,6 +111,7 @@ __device__ __forceinline__ dd_t dd_rsqrt(dd_t a) {
 struct XRe {
   using Re = dd_t;
   static constexpr int kUnrollK = 2;
+  static constexpr int kRegModes = 3;  // modes of the register-resident subtrees of the lane walk
   struct Acc {
     dd_t s;
     __device__ __forceinline__ void add(dd_t v) { s = dd_add(s, v); }

@@ -144,6 +144,7 @@ struct Fp64Re {  // real scalar operations of the two FP64 types
 };
 struct Cplx : Fp64Re {
   using T = double2;
+  static constexpr int kRegModes = 3;
   static __device__ __forceinline__ double re(T v) { return v.x; }
   static __device__ __forceinline__ T diag(double d) { return make_double2(d, 0.0); }
   static __device__ __forceinline__ double abs2(T b) { return fma(b.x, b.x, b.y * b.y); }
@@ -179,6 +180,7 @@ struct Cplx : Fp64Re {
 };
 struct Real : Fp64Re {
   using T = double;
+  static constexpr int kRegModes = 4;  // modes of the register-resident subtrees of the lane walk
   static __device__ __forceinline__ double re(T v) { return v; }
   static __device__ __forceinline__ T diag(double d) { return d; }
   static __device__ __forceinline__ double abs2(T b) { return b * b; }
@@ -325,30 +327,30 @@ struct LaneMem {
   __device__ __forceinline__ typename S::Re ldd(int e) const { return S::re(ld(e)); }
 };
 
-// Load the trailing 6 x 6 block of a node with 4 modes (exclude its first mode).
-template <class S>
-__device__ __forceinline__ void lane_load_trail4(const LaneMem<S> L, int src, int o, HM<S, 6>& C) {
+// Load the trailing R x R block of a node with R/2 + 1 modes (exclude its first mode).
+template <class S, int R>
+__device__ __forceinline__ void lane_load_trail(const LaneMem<S> L, int src, int o, HM<S, R>& C) {
 #pragma unroll
-  for (int i = 0; i < 6; ++i) {
+  for (int i = 0; i < R; ++i) {
     C.d[i] = L.ldd(src + P(o + 2 + i, o + 2 + i));
 #pragma unroll
     for (int k = 0; k < i; ++k) C.o[TI(i, k)] = L.ld(src + P(o + 2 + i, o + 2 + k));
   }
 }
-// Include the first mode of a 4-mode node in memory; child (3 modes) in registers.
-template <class S>
-__device__ __forceinline__ typename S::Re lane_include4(const LaneMem<S> L, int src, int o, HM<S, 6>& C, bool& bad) {
+// Include the first mode of a node with R/2 + 1 modes in memory; the child (R/2 modes) in registers.
+template <class S, int R>
+__device__ __forceinline__ typename S::Re lane_include_reg(const LaneMem<S> L, int src, int o, HM<S, R>& C, bool& bad) {
   using T = typename S::T;
   const Pivot<S> pv = make_pivot<S>(L.ldd(src + P(o, o)), L.ld(src + P(o + 1, o)), L.ldd(src + P(o + 1, o + 1)));
   bad |= !pv.ok;
-  T x[6], yp[6];
+  T x[R], yp[R];
 #pragma unroll
-  for (int r = 0; r < 6; ++r) {
+  for (int r = 0; r < R; ++r) {
     x[r] = L.ld(src + P(o + 2 + r, o));
     yp[r] = S::reduce_col(x[r], L.ld(src + P(o + 2 + r, o + 1)), pv.cl);
   }
 #pragma unroll
-  for (int i = 0; i < 6; ++i) {
+  for (int i = 0; i < R; ++i) {
     const T xt = S::scale(x[i], pv.ia), yt = S::scale(yp[i], pv.id2);
 #pragma unroll
     for (int k = 0; k < i; ++k)
@@ -357,7 +359,7 @@ __device__ __forceinline__ typename S::Re lane_include4(const LaneMem<S> L, int 
   }
   return pv.rho;
 }
-// Load a whole node with R/2 modes (R <= 6) from memory into registers.
+// Load a whole node with R/2 modes from memory into registers.
 template <class S, int R>
 __device__ __forceinline__ void lane_load_node(const LaneMem<S> L, int src, int o, HM<S, R>& C) {
 #pragma unroll

@@ -110,21 +110,24 @@ __device__ __noinline__ typename S::Re coop_include(const typename S::T* src, in
 // modes, phi_root, incl_root modes included so far out of n - M decided) and
 // adds its 2^M signed terms to acc, their magnitudes to ab.
 //
-// Levels are indexed by the number of modes m of the node.  The binary
-// counter c enumerates the 3-mode nodes in depth-first order: bit t of c is
-// the decision (1 = include) taken at the level with 4 + t modes.  Going
-// from c-1 to c flips bit t = ctz(c) from 0 to 1 and every lower bit back to
-// 0: one include at level 4 + t, then excludes.  Included children are
+// Levels are indexed by the number of modes m of the node.  With K =
+// S::kRegModes, the binary counter c enumerates the K-mode nodes in
+// depth-first order: bit t of c is the decision (1 = include) taken at the
+// level with K + 1 + t modes.  Going from c-1 to c flips bit t = ctz(c) from
+// 0 to 1 and every lower bit back to 0: one include at level K + 1 + t, then
+// excludes.  Included children are
 // written to the buffer of their own size (buffer m holds an m-mode matrix),
 // excluded children are views of their parent, so a node is never
-// overwritten while a pending include still needs it.  The 3-mode nodes and
-// everything below them live in registers.
+// overwritten while a pending include still needs it.  The nodes of
+// K = S::kRegModes modes (3, or 4 for the FP64 real type) and everything
+// below them live in registers.
 template <class S>
 __device__ __noinline__ void lane_dfs(const LaneMem<S> L, int root, int root_o, int M, int n,
                                       typename S::Re phi_root, int incl_root, int buf4, int xs, int ys,
                                       typename S::Acc& acc, double& ab, bool& bad) {
   using Re = typename S::Re;
-  if (M <= 3) {
+  constexpr int K = S::kRegModes;  // register-resident subtree: K modes, 2K x 2K
+  if (M <= K) {
     const int excl_above = (n - M) - incl_root;
     Re v{};
     double a = 0.0;
@@ -136,10 +139,16 @@ __device__ __noinline__ void lane_dfs(const LaneMem<S> L, int root, int root_o, 
       HM<S, 4> R4;
       lane_load_node<S, 4>(L, root, root_o, R4);
       Subtree<S, 4>::run(R4, phi_root, v, a, bad);
-    } else {
+    } else if (M == 3) {
       HM<S, 6> R6;
       lane_load_node<S, 6>(L, root, root_o, R6);
       Subtree<S, 6>::run(R6, phi_root, v, a, bad);
+    } else {
+      if constexpr (K >= 4) {
+        HM<S, 8> R8;
+        lane_load_node<S, 8>(L, root, root_o, R8);
+        Subtree<S, 8>::run(R8, phi_root, v, a, bad);
+      }
     }
     if (excl_above & 1) v = S::neg(v);
     acc.add(v);
@@ -151,38 +160,38 @@ __device__ __noinline__ void lane_dfs(const LaneMem<S> L, int root, int root_o, 
   nb[M] = root;
   nof[M] = root_o;
   ph[M] = phi_root;
-  for (int m = M - 1; m >= 4; --m) {
+  for (int m = M - 1; m > K; --m) {
     nb[m] = nb[m + 1];
     nof[m] = nof[m + 1] + 2;
     ph[m] = ph[m + 1];
   }
-  const unsigned long long count = 1ull << (M - 3);
+  const unsigned long long count = 1ull << (M - K);
   for (unsigned long long c = 0; c < count; ++c) {
     if (c != 0 && (c & 1ull) == 0) {
-      const int mi = 4 + __ffsll((long long)c) - 1;
+      const int mi = K + 1 + __ffsll((long long)c) - 1;
       const int dst = buf4 + stack_off(mi - 1);
       const Re rho = lane_include_mem<S>(L, nb[mi], nof[mi], mi, dst, 0, xs, ys, bad);
       nb[mi - 1] = dst;
       nof[mi - 1] = 0;
       ph[mi - 1] = S::mul(ph[mi], rho);
-      for (int m = mi - 2; m >= 4; --m) {
+      for (int m = mi - 2; m > K; --m) {
         nb[m] = nb[m + 1];
         nof[m] = nof[m + 1] + 2;
         ph[m] = ph[m + 1];
       }
     }
-    HM<S, 6> R3;
-    Re phi3;
+    HM<S, 2 * K> RK;
+    Re phiK;
     if (c & 1ull) {
-      phi3 = S::mul(ph[4], lane_include4<S>(L, nb[4], nof[4], R3, bad));
+      phiK = S::mul(ph[K + 1], lane_include_reg<S, 2 * K>(L, nb[K + 1], nof[K + 1], RK, bad));
     } else {
-      lane_load_trail4<S>(L, nb[4], nof[4], R3);
-      phi3 = ph[4];
+      lane_load_trail<S, 2 * K>(L, nb[K + 1], nof[K + 1], RK);
+      phiK = ph[K + 1];
     }
     Re v;
     double a;
-    Subtree<S, 6>::run(R3, phi3, v, a, bad);
-    const int excl_above = (n - 3) - (incl_root + __popcll(c));
+    Subtree<S, 2 * K>::run(RK, phiK, v, a, bad);
+    const int excl_above = (n - K) - (incl_root + __popcll(c));
     if (excl_above & 1) v = S::neg(v);
     acc.add(v);
     ab += a;

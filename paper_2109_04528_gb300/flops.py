@@ -115,39 +115,41 @@ def path_flops(n: int, path: int = 0) -> float:
     return f
 
 
-def _leaf_sums(n: int, combine: float, acc: float) -> float:
-    """Sums above the leaf pairs: every node with 2 or 3 undecided modes (the
-    register subtree) adds its two children's signed sums and magnitudes
-    (`combine`), and every register-subtree root -- the nodes with min(n, 3)
-    undecided modes -- adds its sum to the lane's accumulator (`acc`)."""
-    top = min(n, 3)
+def _leaf_sums(n: int, combine: float, acc: float, regs: int) -> float:
+    """Sums above the leaf pairs: every node with 2..regs undecided modes (the
+    register-resident subtree) adds its two children's signed sums and
+    magnitudes (`combine`), and every register-subtree root -- the nodes with
+    min(n, regs) undecided modes -- adds its sum to the lane's accumulator (`acc`)."""
+    top = min(n, regs)
     return sum(2.0 ** (n - k) * combine for k in range(2, top + 1)) + 2.0 ** (n - top) * acc
 
 
 def path_ops(n: int, path: int) -> float:
-    """Algorithmic FP64 instructions (add, mul and FMA one each, every rcp /
-    rsqrt counted with its hardware estimate) of the GPU walk over all 2^n
-    subsets in the arithmetic `path` (tor_result.path).  The FP64 pipe issues
-    one of these per slot whatever its kind, so ops / (the measured DFMA rate)
-    is the pipe's busy fraction in algorithmic work.  Per include at m >= 1
-    trailing modes / per leaf pair, and the sums above the leaves:
-      FP64 real      4 m^2 + 8 m + 16 / 11   (2 FMA per entry; a pivot-column
-                     row 3; pivot: det 2, rsqrt 6, rcp 4, l 1, 1/d2 2, phi 1);
-                     a subtree sum 2, the lane's double-double sum 8
-      FP64 complex  16 m^2 + 16 m + 18 / 12  (8 FMA per off-diagonal entry, 4
-                     per diagonal one; a row 8; pivot 17 + phi 1)
-      double-double real     60 m^2 + 94 m + 82 / 69
-      double-double complex 216 m^2 + 176 m + 101 / 81
+    """Algorithmic FP64-pipe instructions (add, mul and FMA one each) of the GPU
+    walk over all 2^n subsets in the arithmetic `path` (tor_result.path).  The
+    FP64 pipe issues one of these per slot whatever its kind, so ops / (the
+    measured issue rate) is the pipe's busy fraction in algorithmic work.  The
+    hardware rcp / rsqrt estimates that start each reciprocal are not FP64-pipe
+    instructions and are not counted.  Per include at m >= 1 trailing modes /
+    per leaf pair, and the sums above the leaves:
+      FP64 real      4 m^2 + 8 m + 14 / 10   (2 FMA per entry; a pivot-column
+                     row 3; pivot: det 2, rsqrt 5, rcp 3, l 1, 1/d2 2, phi 1);
+                     a subtree sum 2, the lane's double-double sum 8; subtrees
+                     of 4 modes in registers
+      FP64 complex  16 m^2 + 16 m + 16 / 11  (8 FMA per off-diagonal entry, 4
+                     per diagonal one; a row 8; pivot 15 + phi 1); 3 modes
+      double-double real     60 m^2 + 94 m + 80 / 68
+      double-double complex 216 m^2 + 176 m + 99 / 80
                      (two_sum 6, fast_two_sum 3, two_prod 2, an accumulated
                      product 12, a sum started from a product 4, its
-                     normalisation 6, dd_mul 7, dd_add 20, reciprocal 13,
-                     reciprocal square root 19); a subtree sum and the lane's
-                     sum 21 each."""
+                     normalisation 6, dd_mul 7, dd_add 20, reciprocal 12,
+                     reciprocal square root 18); a subtree sum and the lane's
+                     sum 21 each; 3 modes."""
     real, ext = bool(path & 1), bool(path & 2)
-    a, b, c, pair, combine, acc = {
-        (True, False): (4, 8, 16, 11.0, 2.0, 8.0), (False, False): (16, 16, 18, 12.0, 2.0, 8.0),
-        (True, True): (60, 94, 82, 69.0, 21.0, 21.0), (False, True): (216, 176, 101, 81.0, 21.0, 21.0)}[(real, ext)]
-    f = pair * 2.0 ** (n - 1) + _leaf_sums(n, combine, acc)
+    a, b, c, pair, combine, acc, regs = {
+        (True, False): (4, 8, 14, 10.0, 2.0, 8.0, 4), (False, False): (16, 16, 16, 11.0, 2.0, 8.0, 3),
+        (True, True): (60, 94, 80, 68.0, 21.0, 21.0, 3), (False, True): (216, 176, 99, 80.0, 21.0, 21.0, 3)}[(real, ext)]
+    f = pair * 2.0 ** (n - 1) + _leaf_sums(n, combine, acc, regs)
     for j in range(n - 1):
         m = n - 1 - j
         f += 2.0 ** j * (a * m * m + b * m + c)

@@ -6,8 +6,8 @@ its reciprocal and reciprocal square root -- hardware estimate plus one cubic
 series step -- the pivot columns and the rank-2 update), the leaf pairs and the
 signed sums of Eq. (tor), with the lane's double-double accumulator.  Python
 floats are IEEE doubles rounded to nearest; an FMA is rounded once, through
-exact rationals.  Every FP64 instruction is counted (add, mul, FMA and each
-estimate one each).  Checks:
+exact rationals.  Every FP64-pipe instruction is counted (add, mul and FMA one
+each; the reciprocal estimates are not FP64-pipe instructions).  Checks:
   * the count equals paper_2109_04528_gb300.flops.path_ops for the real (x, p)
     and the complex walk -- the figure the benchmark's instruction fraction
     divides by;
@@ -40,15 +40,13 @@ class Ops:
         return float(Fraction(a) * Fraction(b) + Fraction(c))
 
     def rcp(self, x):
-        y = float(np.float32(1.0 / x))  # a coarse estimate (the hardware's is ~2^-20)
-        self.n += 1
+        y = float(np.float32(1.0 / x))  # a coarse estimate (the hardware's is ~2^-20; not an FP64-pipe op)
         e = self.fma(-x, y, 1.0)
         s = self.fma(e, e, e)
         return self.fma(y, s, y)
 
     def rsqrt(self, x):
         y = float(np.float32(1.0 / math.sqrt(x)))
-        self.n += 1
         t = self.mul(x, y)
         e = self.fma(-t, y, 1.0)
         p = self.fma(0.375, e, 0.5)
@@ -149,7 +147,7 @@ def trail(S):
 
 
 def subtree(A, S, m, phi, o):
-    """(signed sum, sum of magnitudes) below a node with m <= 3 modes."""
+    """(signed sum, sum of magnitudes) below a register-resident node of m modes."""
     if m == 1:
         det2 = A.det2(A.re(S[(0, 0)]), S[(1, 0)], A.re(S[(1, 1)]))
         pr = o.mul(phi, o.rsqrt(det2))
@@ -160,17 +158,17 @@ def subtree(A, S, m, phi, o):
     return o.add(v2, -v1), o.add(a1, a2)
 
 
-def walk(A, S, m, phi, excl, acc, o):
-    if m <= 3:
+def walk(A, S, m, phi, excl, acc, o, regs):
+    if m <= regs:
         v, a = subtree(A, S, m, phi, o)
         v = -v if excl % 2 else v  # a sign, no arithmetic
         acc[0], e = o.two_sum(acc[0], v)  # double-double accumulator (Sum2)
         acc[1] = o.add(acc[1], e)
         acc[2] = o.add(acc[2], a)
         return
-    walk(A, trail(S), m - 1, phi, excl + 1, acc, o)
+    walk(A, trail(S), m - 1, phi, excl + 1, acc, o, regs)
     C, rho = include(A, S, o)
-    walk(A, C, m - 1, o.mul(phi, rho), excl, acc, o)
+    walk(A, C, m - 1, o.mul(phi, rho), excl, acc, o, regs)
 
 
 def b_entries(O, real):
@@ -198,7 +196,8 @@ def model_tor(O, real):
     o = Ops()
     A = RealArith(o) if real else CplxArith(o)
     acc = [0.0, 0.0, 0.0]
-    walk(A, b_entries(O, real), O.shape[0] // 2, 1.0, 0, acc, o)
+    # subtrees of 4 modes stay in registers on the real path, 3 on the complex one
+    walk(A, b_entries(O, real), O.shape[0] // 2, 1.0, 0, acc, o, 4 if real else 3)
     return acc[0] + acc[1], acc[2], o.n
 
 
