@@ -119,7 +119,7 @@ struct XRe {
   static __device__ __forceinline__ dd_t mul(dd_t a, dd_t b) { return dd_mul(a, b); }
   static __device__ __forceinline__ dd_t sub(dd_t a, dd_t b) { return dd_add(a, dd_neg(b)); }
   static __device__ __forceinline__ dd_t neg(dd_t a) { return dd_neg(a); }
-  static __device__ __forceinline__ bool pos(dd_t a) { return a.h > 0.0; }
+  static __device__ __forceinline__ bool pos(dd_t a) { return pos_finite(a.h); }  // h + l > 0 iff h > 0
   static __device__ __forceinline__ dd_t rcp(dd_t a) { return dd_rcp(a); }
   static __device__ __forceinline__ dd_t rsqrt(dd_t a) { return dd_rsqrt(a); }
   static __device__ __forceinline__ double hi(dd_t a) { return a.h; }

@@ -125,6 +125,15 @@ __device__ __forceinline__ void dd_add(double ah, double al, double bh, double b
 //   re(v), diag(d)       real part; the stored form of a real diagonal entry
 // and, on its real scalar Re: mul, sub, neg, pos (> 0), rcp, rsqrt, hi (the
 // leading double), one, shfl (warp broadcast from a lane).
+// Positive and finite, decided on the bit pattern with integer operations: on
+// GB300 an FP64 comparison takes an issue slot of the FP64 pipe, like an FMA,
+// while integer operations run on another pipe.  The bit patterns of the
+// positive finite doubles are exactly 1 .. 0x7FEFFFFFFFFFFFFF; +-0, negative
+// values, infinities and NaNs fall outside.
+__device__ __forceinline__ bool pos_finite(double a) {
+  return (unsigned long long)__double_as_longlong(a) - 1ull < 0x7FEFFFFFFFFFFFFFull;
+}
+
 // ---------------------------------------------------------------------------
 struct Fp64Re {  // real scalar operations of the two FP64 types
   using Re = double;
@@ -133,7 +142,7 @@ struct Fp64Re {  // real scalar operations of the two FP64 types
   static __device__ __forceinline__ double mul(double a, double b) { return a * b; }
   static __device__ __forceinline__ double sub(double a, double b) { return a - b; }
   static __device__ __forceinline__ double neg(double a) { return -a; }
-  static __device__ __forceinline__ bool pos(double a) { return a > 0.0; }
+  static __device__ __forceinline__ bool pos(double a) { return pos_finite(a); }
   static __device__ __forceinline__ double rcp(double a) { return rcp64(a); }
   static __device__ __forceinline__ double rsqrt(double a) { return rsqrt64(a); }
   static __device__ __forceinline__ double hi(double a) { return a; }
@@ -211,14 +220,14 @@ struct Pivot {
   Re id2;            // 1 / d2 = a rho^2
   Re rho;            // (a e - |b|^2)^{-1/2}
   typename S::T cl;  // conj(l) = conj(b) / a
-  bool ok;           // d1 > 0 and d1 d2 > 0: the block is positive definite
+  bool ok;           // d1 > 0 and d1 d2 > 0, both finite: the block is positive definite
 };
 template <class S>
 __device__ __forceinline__ Pivot<S> make_pivot(typename S::Re a, typename S::T b, typename S::Re e) {
   using Re = typename S::Re;
   Pivot<S> pv;
   const Re det2 = S::det2(a, b, e);
-  pv.ok = S::pos(a) && S::pos(det2);
+  pv.ok = S::pos(a) & S::pos(det2);
   pv.rho = S::rsqrt(det2);
   pv.ia = S::rcp(a);
   pv.cl = S::cl(b, pv.ia);
@@ -279,7 +288,7 @@ __device__ __forceinline__ void leaf_pair(typename S::Re a, typename S::T b, typ
                                           typename S::Re& v, double& ab, bool& bad) {
   using Re = typename S::Re;
   const Re det2 = S::det2(a, b, e);
-  bad |= !(S::pos(a) && S::pos(det2));
+  bad |= !(S::pos(a) & S::pos(det2));
   const Re pr = S::mul(phi, S::rsqrt(det2));
   v = S::sub(pr, phi);
   ab = S::hi(pr) + S::hi(phi);

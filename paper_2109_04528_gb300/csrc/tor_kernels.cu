@@ -53,6 +53,32 @@ __device__ __noinline__ typename S::Re lane_include_mem(const LaneMem<S> L, int 
   return pv.rho;
 }
 
+// Copies the node (src, o) with m modes (packed, not interleaved) into the
+// lane's stack at element 0, 8 entries per pass: their loads are issued before
+// their stores, so they overlap.  Used for entries wider than 8 bytes (complex
+// and double-double), where it measured faster; the FP64 real path keeps the
+// plain loop, which needs fewer registers in the caller.
+template <class S>
+__device__ __noinline__ void lane_copy_node(const LaneMem<S> L, const typename S::T* src, int o, int m) {
+  using T = typename S::T;
+  const int tot = tri_size(m);
+  int i = 0, k = 0;
+  for (int e0 = 0; e0 < tot; e0 += 8) {
+    T v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      if (e0 + u < tot) v[u] = src[P(i + o, k + o)];
+      if (++k > i) {
+        k = 0;
+        ++i;
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u)
+      if (e0 + u < tot) L.st(e0 + u, v[u]);
+  }
+}
+
 // Cooperative include: the lanes of a warp split the entries of nodes stored
 // contiguously (packed, not interleaved).  Used for the shared upper part of
 // the tree, where nodes are large.  The warp is divided into groups of gs
@@ -405,10 +431,14 @@ __device__ void run_task_shared(const UnitsParams& prm, const TaskDesc T, int la
     if (lane < nodes) no += 2;
   }
   // 3. copy the lane's unit root into its private stack
-  const int RR = 2 * M;
-  for (int i = 0; i < RR; ++i)
-    for (int k = 0; k <= i; ++k) L.st(P(i, k), nptr[P(i + no, k + no)]);
   const int root_sz = tri_size(M);
+  if constexpr (sizeof(E) > 8) {
+    lane_copy_node<S>(L, nptr, no, M);
+  } else {
+    const int RR = 2 * M;
+    for (int i = 0; i < RR; ++i)
+      for (int k = 0; k <= i; ++k) L.st(P(i, k), nptr[P(i + no, k + no)]);
+  }
   const int xs = root_sz + stack_off(M), ys = xs + 2 * n;
   typename S::Acc acc = S::acc0();
   double ab = 0.0;
@@ -431,11 +461,13 @@ __device__ void run_task_lanes(const UnitsParams& prm, const TaskDesc T, int lan
   const MatDesc D = prm.mats[mat];
   const int n = D.n, M = n - p;
   const long long u = q & ((1ll << p) - 1);
-  const int RR = 2 * n;
-  const E* B = (const E*)D.B;
-  for (int i = 0; i < RR; ++i)
-    for (int k = 0; k <= i; ++k) L.st(P(i, k), B[P(i, k)]);
   const int root_sz = tri_size(n);
+  const E* B = (const E*)D.B;
+  if constexpr (sizeof(E) > 8) {
+    lane_copy_node<S>(L, B, 0, n);
+  } else {
+    for (int e = 0; e < root_sz; ++e) L.st(e, B[e]);
+  }
   const int xs = root_sz + stack_off(M), ys = xs + 2 * n;
   bool bad = false;
   int o = 0, incl = 0;
