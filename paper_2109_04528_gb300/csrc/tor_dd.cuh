@@ -124,6 +124,11 @@ struct XRe {
   static __device__ __forceinline__ dd_t rsqrt(dd_t a) { return dd_rsqrt(a); }
   static __device__ __forceinline__ double hi(dd_t a) { return a.h; }
   static __device__ __forceinline__ dd_t one() { return dd_t{1.0, 0.0}; }
+  static __device__ __forceinline__ void pair_sums(dd_t phi, dd_t r, dd_t& v, double& ab) {
+    const dd_t pr = dd_mul(phi, r);
+    v = dd_add(pr, dd_neg(phi));
+    ab = pr.h + phi.h;
+  }
   static __device__ __forceinline__ dd_t shfl(dd_t a, int q) {
     return dd_t{__shfl_sync(0xffffffffu, a.h, q), __shfl_sync(0xffffffffu, a.l, q)};
   }

@@ -146,6 +146,12 @@ struct Fp64Re {  // real scalar operations of the two FP64 types
   static __device__ __forceinline__ double rcp(double a) { return rcp64(a); }
   static __device__ __forceinline__ double rsqrt(double a) { return rsqrt64(a); }
   static __device__ __forceinline__ double hi(double a) { return a; }
+  // a leaf pair phi (exclude) and phi r (include): signed sum phi r - phi and
+  // magnitude sum phi r + phi, one FMA each
+  static __device__ __forceinline__ void pair_sums(double phi, double r, double& v, double& ab) {
+    v = fma(phi, r, -phi);
+    ab = fma(phi, r, phi);
+  }
   static __device__ __forceinline__ double one() { return 1.0; }
   static __device__ __forceinline__ double shfl(double a, int q) { return __shfl_sync(0xffffffffu, a, q); }
   static __device__ __forceinline__ Acc acc0() { return DD{0.0, 0.0}; }
@@ -289,9 +295,7 @@ __device__ __forceinline__ void leaf_pair(typename S::Re a, typename S::T b, typ
   using Re = typename S::Re;
   const Re det2 = S::det2(a, b, e);
   bad |= !(S::pos(a) & S::pos(det2));
-  const Re pr = S::mul(phi, S::rsqrt(det2));
-  v = S::sub(pr, phi);
-  ab = S::hi(pr) + S::hi(phi);
+  S::pair_sums(phi, S::rsqrt(det2), v, ab);
 }
 
 // Sum over the 2^(R/2) leaves below a register node:

@@ -132,11 +132,12 @@ def path_ops(n: int, path: int) -> float:
     hardware rcp / rsqrt estimates that start each reciprocal are not FP64-pipe
     instructions and are not counted.  Per include at m >= 1 trailing modes /
     per leaf pair, and the sums above the leaves:
-      FP64 real      4 m^2 + 8 m + 14 / 10   (2 FMA per entry; a pivot-column
-                     row 3; pivot: det 2, rsqrt 5, rcp 3, l 1, 1/d2 2, phi 1);
-                     a subtree sum 2, the lane's double-double sum 8; subtrees
-                     of 4 modes in registers
-      FP64 complex  16 m^2 + 16 m + 16 / 11  (8 FMA per off-diagonal entry, 4
+      FP64 real      4 m^2 + 8 m + 14 / 9    (2 FMA per entry; a pivot-column
+                     row 3; pivot: det 2, rsqrt 5, rcp 3, l 1, 1/d2 2, phi 1;
+                     a leaf pair: det 2, rsqrt 5, its signed and magnitude
+                     sums one FMA each); a subtree sum 2, the lane's
+                     double-double sum 8; subtrees of 4 modes in registers
+      FP64 complex  16 m^2 + 16 m + 16 / 10  (8 FMA per off-diagonal entry, 4
                      per diagonal one; a row 8; pivot 15 + phi 1); 3 modes
       double-double real     60 m^2 + 94 m + 80 / 68
       double-double complex 216 m^2 + 176 m + 99 / 80
@@ -147,7 +148,7 @@ def path_ops(n: int, path: int) -> float:
                      sum 21 each; 3 modes."""
     real, ext = bool(path & 1), bool(path & 2)
     a, b, c, pair, combine, acc, regs = {
-        (True, False): (4, 8, 14, 10.0, 2.0, 8.0, 4), (False, False): (16, 16, 16, 11.0, 2.0, 8.0, 3),
+        (True, False): (4, 8, 14, 9.0, 2.0, 8.0, 4), (False, False): (16, 16, 16, 10.0, 2.0, 8.0, 3),
         (True, True): (60, 94, 80, 68.0, 21.0, 21.0, 3), (False, True): (216, 176, 99, 80.0, 21.0, 21.0, 3)}[(real, ext)]
     f = pair * 2.0 ** (n - 1) + _leaf_sums(n, combine, acc, regs)
     for j in range(n - 1):

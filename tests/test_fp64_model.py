@@ -150,8 +150,8 @@ def subtree(A, S, m, phi, o):
     """(signed sum, sum of magnitudes) below a register-resident node of m modes."""
     if m == 1:
         det2 = A.det2(A.re(S[(0, 0)]), S[(1, 0)], A.re(S[(1, 1)]))
-        pr = o.mul(phi, o.rsqrt(det2))
-        return o.add(pr, -phi), o.add(pr, phi)
+        r = o.rsqrt(det2)
+        return o.fma(phi, r, -phi), o.fma(phi, r, phi)  # the pair's signed and magnitude sums
     v1, a1 = subtree(A, trail(S), m - 1, phi, o)
     C, rho = include(A, S, o)
     v2, a2 = subtree(A, C, m - 1, o.mul(phi, rho), o)
