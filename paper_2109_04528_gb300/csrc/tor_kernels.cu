@@ -348,7 +348,13 @@ __device__ __forceinline__ Part write_partial(const UnitsParams& prm, const MatD
   return v;
 }
 
-// Sum of the 32 lanes' unit partials of a task by a fixed binary tree over lane index.
+// Sum of the 32 lanes' unit partials of a task by a fixed binary tree over lane
+// index.  Each level adds the high parts exactly (two_sum) and the low parts
+// with the rounding error in FP64, left unnormalised; one two_sum at the end
+// normalises.  8 FP64 instructions per level instead of the 20 of a normalised
+// double-word sum, and each level costs a full warp instruction however few
+// lanes add.  Error: the low parts stay below ~5u sum|hi|, so their roundings
+// add below ~25u^2 sum|partial| (u = 2^-53), far inside both tolerances.
 __device__ __forceinline__ void write_task_partial(const UnitsParams& prm, const MatDesc& D, int sub, Part v,
                                                    int lane) {
   double h = v.hi, l = v.lo, a = v.abs_sum;
@@ -358,11 +364,18 @@ __device__ __forceinline__ void write_task_partial(const UnitsParams& prm, const
     const double l2 = __shfl_down_sync(0xffffffffu, l, off);
     const double a2 = __shfl_down_sync(0xffffffffu, a, off);
     if ((lane & (2 * off - 1)) == 0) {
-      dd_add(h, l, h2, l2, h, l);
+      double s, e;
+      two_sum(h, h2, s, e);
+      h = s;
+      l = __dadd_rn(__dadd_rn(l, l2), e);
       a = a + a2;
     }
   }
-  if (lane == 0) prm.red_leaves[D.red_off + (sub - D.red_lo)] = Part{h, l, a, 0.0};
+  if (lane == 0) {
+    double hh, ll;
+    two_sum(h, l, hh, ll);
+    prm.red_leaves[D.red_off + (sub - D.red_lo)] = Part{hh, ll, a, 0.0};
+  }
 }
 
 // p >= 5: the warp builds the task node (depth p - 5) cooperatively, fans it

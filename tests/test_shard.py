@@ -16,7 +16,8 @@ N, P = 9, 6  # 2^(P-5) = 2 leaves (warp tasks), each 32 units of 2^(N-P) subsets
 
 
 def task_partial(oracle_mod, O, t):
-    # lane l of task t takes unit u = t | (l << (P-5)); lanes merge by the same binary tree
+    # lane l of task t takes unit u = t | (l << (P-5)); lanes merge by a binary tree over lane index
+    # (the shape of the device's lane tree, which leaves low parts unnormalised between levels)
     units = []
     for lane in range(32):
         r = oracle_mod.tor_unit(O, P, t | (lane << (P - 5)), threads=1)
