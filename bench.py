@@ -244,6 +244,14 @@ def cpu_baseline(mats, budget_s: float):
                       f"binary128 LU per subset, {dt:.1f} s"}
 
 
+def launches_per_step(ctx, ns) -> int:
+    """Kernels one tor_eval_batch launches: k_intake, k_units, k_reduce, and
+    k_reduce_chunks when a matrix has more than 256 reduction leaves (2^(p-5)
+    task partials for p >= 5, 2^p unit partials below)."""
+    big = any((p - 5 if p >= 5 else p) > 8 for p in (ctx.plan_prefix_depth(n) for n in ns))
+    return 3 + (1 if big else 0)
+
+
 def cpu_alg2(mats, budget_s: float):
     """The paper's own method on the host cores: Algorithm 2 in FP64 with a
     thread pool over subtrees (oracle/tor_alg2_cpu.c), on the workload's
@@ -634,7 +642,7 @@ def main():
                      "flops_per_launch": flops, "units_ms_avg": units_avg,
                      "path": f"{n_real} of {len(ns)} matrices in the real (x,p) basis, rest complex"
                              + ("; double-double factor (every FP64 operation counted)" if ext else "")},
-        "gpu_launches": 3 * args.steps,
+        "gpu_launches": launches_per_step(ctx_dev, ns) * args.steps,
         "clocks": clocks,
     }
     line["roofline"]["fp64_instructions"] = inst

@@ -131,7 +131,7 @@ struct Slot {
   std::vector<MatDesc> mats;
   std::vector<TaskDesc> tasks;
   int J = 0;
-  long long o_elems = 0, b_elems = 0, parts = 0, reds = 0, mode_elems = 0, lane_e = 0, warp_e = 0;
+  long long o_elems = 0, b_elems = 0, parts = 0, reds = 0, red_chunks = 0, mode_elems = 0, lane_e = 0, warp_e = 0;
   bool want_parts = false;
   size_t bytes = 0;
   int cancel_epoch = 0;
@@ -345,7 +345,7 @@ static tor_status slot_prepare(tor_ctx* ctx, Slot& S, const std::vector<MatIn>& 
   const int J = (int)S.act.size();
   S.mats.assign(J, MatDesc{});
   S.tasks.clear();
-  S.o_elems = S.b_elems = S.parts = S.reds = S.mode_elems = S.lane_e = S.warp_e = 0;
+  S.o_elems = S.b_elems = S.parts = S.reds = S.red_chunks = S.mode_elems = S.lane_e = S.warp_e = 0;
   for (int j = 0; j < J; ++j) {
     const MatIn& m = ins[S.act[j]];
     const int p = plan_p(ctx, m.n);
@@ -369,6 +369,8 @@ static tor_status slot_prepare(tor_ctx* ctx, Slot& S, const std::vector<MatIn>& 
     }
     D.red_off = S.reds;
     S.reds += 1ll << D.red_log2;
+    D.red_chunk0 = (int)S.red_chunks;
+    S.red_chunks += red_chunks(D.red_log2);
     S.b_elems += tri(m.n);
     if (!m.dev && !m.modes) S.o_elems += 4ll * m.n * m.n;
     if (m.modes) S.mode_elems += m.n;
@@ -538,7 +540,7 @@ static tor_status rec_back(tor_ctx* ctx, Slot& S, bool timed) {
   cudaStream_t s = S.stream;
   const int J = S.J;
   if (timed) CK(cudaEventRecord(S.ev[3], s), "event");
-  CK(launch_reduce((const MatDesc*)S.d_mats.p, J, (const Part*)S.d_partials.p + S.parts, (const int*)S.d_flags.p,
+  CK(launch_reduce((const MatDesc*)S.d_mats.p, J, S.red_chunks, (Part*)S.d_partials.p + S.parts, (const int*)S.d_flags.p,
                    (ResultRec*)S.d_results.p, s),
      "k_reduce");
   if (timed) CK(cudaEventRecord(S.ev[4], s), "event");

@@ -19,6 +19,7 @@ struct MatDesc {
   long long part_off;   // first of this matrix's 2^p unit partials
   long long red_off;    // first of this matrix's reduction leaves (task partials if p >= 5, else unit partials)
   int red_log2;         // log2 of the number of reduction leaves: p - 5 if p >= 5, else p
+  int red_chunk0;       // first block of this matrix in the first reduction stage (red_chunk_log2 > 0)
   int n, p, ld, layout;
   int n_src;            // modes of the source matrix (n unless `modes` selects a submatrix)
   int real;             // -1: let k_intake detect the structure; 0: complex; 1: real (x, p) path
@@ -70,6 +71,16 @@ struct ResultRec {
   int flags, pad;
 };
 
+// Two-stage reduction: with more than 256 leaves, the first stage sums aligned
+// chunks of 2^red_chunk_log2 leaves (one thread block each, at most 256 chunks
+// per matrix), the second the chunk sums; one binary tree over leaf index.
+__host__ __device__ constexpr int red_chunk_log2(int red_log2) {
+  return red_log2 <= 8 ? 0 : (red_log2 - 8 > 8 ? red_log2 - 8 : 8);
+}
+__host__ __device__ constexpr long long red_chunks(int red_log2) {
+  return red_chunk_log2(red_log2) ? 1ll << (red_log2 - red_chunk_log2(red_log2)) : 0;
+}
+
 // ---- scratch sizes, in entries of the arithmetic's own type (one definition
 // for the kernels, the host runtime and the allocation-free entry point) ----
 __host__ __device__ constexpr int tri_size(int m) { return m * (2 * m + 1); }  // packed entries, m modes
@@ -109,7 +120,7 @@ inline long long warp_elems_for(int n, int p) { return warp_elems_c(n, p); }
 
 cudaError_t launch_intake(const MatDesc* d_mats, int nmats, int check, int* d_flags, cudaStream_t s);
 cudaError_t launch_units(const UnitsParams& prm, int grid, cudaStream_t s);
-cudaError_t launch_reduce(const MatDesc* d_mats, int nmats, const Part* partials, const int* flags,
+cudaError_t launch_reduce(const MatDesc* d_mats, int nmats, long long nchunks, Part* partials, const int* flags,
                           ResultRec* out, cudaStream_t s);
 int units_block_threads();
 cudaError_t units_blocks_per_sm(int* blocks, int ext);

@@ -6,8 +6,9 @@
 //   k_units   : persistent warps; each warp task evaluates 32 units (prefix
 //               subtrees) of the tree of Algorithm 2, one unit per lane.
 //   k_units_ext : the same in double-double arithmetic (extended precision).
-//   k_reduce  : fixed-shape binary tree over each matrix's task partials (each
-//               already a fixed lane tree over 32 units), in double-double.
+//   k_reduce_chunks, k_reduce : fixed-shape binary tree over each matrix's
+//               task partials (each already a fixed lane tree over 32 units), in
+//               double-double; large matrices in two stages.
 //   k_probe   : FP64 FMA throughput probe (the roofline's denominator).
 #include "tor_dd.cuh"
 #include "tor_device.cuh"
@@ -245,6 +246,17 @@ __device__ __forceinline__ int src_row(const MatDesc& D, int t, int c) {
 // with A = B(a_j, a_k) and C = B(a_j, a_k^dag).  flags gets FLAG_REAL when V
 // was written.  With D.ext the entries are written as double-doubles (ddc_t or
 // dd_t): 1 - O_ii exactly, and each entry of V to within 3 u^2.
+__device__ __forceinline__ unsigned long long abs_bits(double v) {
+  return (unsigned long long)__double_as_longlong(v) & 0x7FFFFFFFFFFFFFFFull;
+}
+constexpr unsigned long long kInfBits = 0x7FF0000000000000ull;  // |v| patterns >= this: inf or NaN
+// max of two |v| patterns that ignores NaN (patterns above infinity), as fmax does
+__device__ __forceinline__ unsigned long long umax(unsigned long long a, unsigned long long b) {
+  if (a > kInfBits) return b;
+  if (b > kInfBits) return a;
+  return a > b ? a : b;
+}
+
 __global__ void __launch_bounds__(256) k_intake(const MatDesc* __restrict__ mats, int check, int* __restrict__ flags) {
   const MatDesc D = mats[blockIdx.x];
   const int n = D.n, tot = n * (2 * n + 1);
@@ -257,23 +269,41 @@ __global__ void __launch_bounds__(256) k_intake(const MatDesc* __restrict__ mats
     s_bad = 0;
   }
   __syncthreads();
-  double mx = 0.0, dev = 0.0, sdev = 0.0;
+  // Maxima of |.| kept as bit patterns: with the sign bit cleared, doubles
+  // order like their patterns, so the comparisons run on the integer pipe, not
+  // the FP64 one; NaNs are skipped like fmax skips them (a non-finite entry is
+  // flagged on its own).  Four entries per pass, their loads issued together.
+  unsigned long long mx = 0, dev = 0, sdev = 0;
   int bad = 0;
-  for (int e = threadIdx.x; e < 4 * n * n; e += blockDim.x) {
-    const int r = e / (2 * n), s = e % (2 * n);  // full matrix, pairs order
-    const double2 a = D.O[(size_t)src_row(D, r >> 1, r & 1) * D.ld + src_row(D, s >> 1, s & 1)];
-    const double2 b = D.O[(size_t)src_row(D, s >> 1, s & 1) * D.ld + src_row(D, r >> 1, r & 1)];
-    if (!isfinite(a.x) || !isfinite(a.y)) bad = 1;
-    mx = fmax(mx, fmax(fabs(a.x), fabs(a.y)));
-    dev = fmax(dev, fmax(fabs(a.x - b.x), fabs(a.y + b.y)));
-    // structure: compare with the entry of the opposite components of the same modes
-    const double2 c = D.O[(size_t)src_row(D, r >> 1, 1 - (r & 1)) * D.ld + src_row(D, s >> 1, 1 - (s & 1))];
-    sdev = fmax(sdev, fmax(fabs(a.x - c.x), fabs(a.y + c.y)));
+  const int full = 4 * n * n;
+  constexpr int kI = 4;
+  for (int e0 = threadIdx.x; e0 < full; e0 += kI * blockDim.x) {
+    double2 a[kI], b[kI], c[kI];
+#pragma unroll
+    for (int u = 0; u < kI; ++u) {
+      const int e = e0 + u * blockDim.x;
+      if (e < full) {
+        const int r = e / (2 * n), s = e % (2 * n);  // full matrix, pairs order
+        a[u] = D.O[(size_t)src_row(D, r >> 1, r & 1) * D.ld + src_row(D, s >> 1, s & 1)];
+        b[u] = D.O[(size_t)src_row(D, s >> 1, s & 1) * D.ld + src_row(D, r >> 1, r & 1)];
+        // structure: the entry of the opposite components of the same modes
+        c[u] = D.O[(size_t)src_row(D, r >> 1, 1 - (r & 1)) * D.ld + src_row(D, s >> 1, 1 - (s & 1))];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kI; ++u) {
+      if (e0 + u * blockDim.x < full) {
+        const unsigned long long ax = abs_bits(a[u].x), ay = abs_bits(a[u].y);
+        if (ax >= kInfBits || ay >= kInfBits) bad = 1;
+        mx = umax(mx, umax(ax, ay));
+        dev = umax(dev, umax(abs_bits(a[u].x - b[u].x), abs_bits(a[u].y + b[u].y)));
+        sdev = umax(sdev, umax(abs_bits(a[u].x - c[u].x), abs_bits(a[u].y + c[u].y)));
+      }
+    }
   }
-  // non-negative doubles order like their bit patterns (NaN compares as huge: fails the tests below)
-  atomicMax(&s_max, (unsigned long long)__double_as_longlong(mx));
-  atomicMax(&s_dev, (unsigned long long)__double_as_longlong(dev));
-  atomicMax(&s_sdev, (unsigned long long)__double_as_longlong(sdev));
+  atomicMax(&s_max, mx);
+  atomicMax(&s_dev, dev);
+  atomicMax(&s_sdev, sdev);
   if (bad) atomicOr(&s_bad, 1);
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -566,56 +596,108 @@ __global__ void __launch_bounds__(kUnitsThreads, kExtBlocksPerSm) k_units_ext(co
   units_loop<RealX, CplxX>(prm);
 }
 
-// Binary tree over the 2^p partials of each matrix: thread t reduces an
-// aligned block of 2^k leaves pairwise, then the threads' results are
-// combined pairwise in shared memory.  The shape depends on p only.
+// Reduction of each matrix's 2^red_log2 leaves (task partials, or unit
+// partials for p < 5): one perfect binary tree over leaf index, left operand
+// first, in accurate double-word sums.  The tree is cut into aligned blocks
+// that separate thread blocks evaluate (k_reduce_chunks, then k_reduce); every
+// internal node gets the same operands whatever the cut, so the result does not
+// depend on it.
 constexpr int kReduceThreads = 256;
+
+// Sum of k leaves x[0], x[stride], ... (k a power of two) as a perfect binary tree.
+__device__ __forceinline__ void chunk_tree(const Part* x, long long stride, long long k, double& h, double& l,
+                                           double& a) {
+  double h_st[40], l_st[40], a_st[40];
+  int top = 0;
+  for (long long i = 0; i < k; ++i) {
+    const Part v = x[i * stride];
+    double vh = v.hi, vl = v.lo, va = v.abs_sum;
+    for (long long q = i; q & 1; q >>= 1) {
+      --top;
+      dd_add(h_st[top], l_st[top], vh, vl, vh, vl);
+      va = a_st[top] + va;
+    }
+    h_st[top] = vh;
+    l_st[top] = vl;
+    a_st[top] = va;
+    ++top;
+  }
+  h = h_st[0];
+  l = l_st[0];
+  a = a_st[0];
+}
+
+// Perfect binary tree over the values of threads 0..T-1 (T a power of two, at
+// most kReduceThreads), pairs (2i, 2i+1) at each level, the active threads
+// packed into the lowest warps.  Called by every thread; thread 0 gets the sum.
+__device__ __forceinline__ void block_tree(double& h, double& l, double& a, int T) {
+  __shared__ double sh[2][kReduceThreads], sl[2][kReduceThreads], sa[2][kReduceThreads];
+  const int t = threadIdx.x;
+  int cur = 0;
+  if (t < T) {
+    sh[0][t] = h;
+    sl[0][t] = l;
+    sa[0][t] = a;
+  }
+  __syncthreads();
+  for (int cnt = T >> 1; cnt >= 1; cnt >>= 1) {
+    if (t < cnt) {
+      double hh, ll;
+      dd_add(sh[cur][2 * t], sl[cur][2 * t], sh[cur][2 * t + 1], sl[cur][2 * t + 1], hh, ll);
+      sh[cur ^ 1][t] = hh;
+      sl[cur ^ 1][t] = ll;
+      sa[cur ^ 1][t] = sa[cur][2 * t] + sa[cur][2 * t + 1];
+    }
+    cur ^= 1;
+    __syncthreads();
+  }
+  h = sh[cur][0];
+  l = sl[cur][0];
+  a = sa[cur][0];
+}
+
+// First stage: block b sums one aligned chunk of 2^red_chunk_log2 leaves of
+// its matrix (the last matrix with red_chunk0 <= b) and writes the sum over the
+// chunk's first leaf.
+__global__ void __launch_bounds__(kReduceThreads) k_reduce_chunks(const MatDesc* __restrict__ mats, int nmats,
+                                                                  Part* partials) {
+  const int b = blockIdx.x;
+  int lo = 0, hi = nmats - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (mats[mid].red_chunk0 <= b) lo = mid;
+    else hi = mid - 1;
+  }
+  const MatDesc D = mats[lo];
+  const long long C = 1ll << red_chunk_log2(D.red_log2);
+  Part* x = partials + D.red_off + (long long)(b - D.red_chunk0) * C;
+  const long long k = C / kReduceThreads;
+  double h, l, a;
+  chunk_tree(x + threadIdx.x * k, 1, k, h, l, a);
+  block_tree(h, l, a, kReduceThreads);
+  if (threadIdx.x == 0) x[0] = Part{h, l, a, 0.0};
+}
+
+// Second stage, one block per matrix: the 2^(red_log2 - red_chunk_log2) chunk
+// sums (or all the leaves, when there was no first stage).
 __global__ void __launch_bounds__(kReduceThreads) k_reduce(const MatDesc* __restrict__ mats,
                                                            const Part* __restrict__ partials,
                                                            const int* __restrict__ flags, ResultRec* out) {
   const MatDesc D = mats[blockIdx.x];
-  const long long U = 1ll << D.red_log2;
+  const int clog = red_chunk_log2(D.red_log2);
+  const long long stride = 1ll << clog;
+  const long long U = 1ll << (D.red_log2 - clog);
   const int T = (int)(U < kReduceThreads ? U : kReduceThreads);
-  const long long chunk = U / T;
+  const long long k = U / T;
   const Part* x = partials + D.red_off;
-  __shared__ double sh[kReduceThreads], sl[kReduceThreads], sa[kReduceThreads];
-  const int t = threadIdx.x;
-  if (t < T) {
-    double h_st[40], l_st[40], a_st[40];
-    int top = 0;
-    for (long long i = 0; i < chunk; ++i) {
-      const Part v = x[(long long)t * chunk + i];
-      double h = v.hi, l = v.lo, a = v.abs_sum;
-      for (long long k = i; k & 1; k >>= 1) {
-        --top;
-        dd_add(h_st[top], l_st[top], h, l, h, l);
-        a = a_st[top] + a;
-      }
-      h_st[top] = h;
-      l_st[top] = l;
-      a_st[top] = a;
-      ++top;
-    }
-    sh[t] = h_st[0];
-    sl[t] = l_st[0];
-    sa[t] = a_st[0];
-  }
-  __syncthreads();
-  for (int s = 1; s < T; s <<= 1) {
-    if (t < T && (t % (2 * s)) == 0) {
-      double h, l;
-      dd_add(sh[t], sl[t], sh[t + s], sl[t + s], h, l);
-      sh[t] = h;
-      sl[t] = l;
-      sa[t] = sa[t] + sa[t + s];
-    }
-    __syncthreads();
-  }
-  if (t == 0) {
+  double h = 0.0, l = 0.0, a = 0.0;
+  if ((int)threadIdx.x < T) chunk_tree(x + (long long)threadIdx.x * k * stride, stride, k, h, l, a);
+  block_tree(h, l, a, T);
+  if (threadIdx.x == 0) {
     ResultRec r;
-    r.hi = sh[0];
-    r.lo = sl[0];
-    r.abs_sum = sa[0];
+    r.hi = h;
+    r.lo = l;
+    r.abs_sum = a;
     r.flags = flags[blockIdx.x];
     r.pad = 0;
     out[blockIdx.x] = r;
@@ -648,9 +730,15 @@ cudaError_t launch_units(const UnitsParams& prm, int grid, cudaStream_t s) {
   else k_units<<<grid, kUnitsThreads, 0, s>>>(prm);
   return cudaGetLastError();
 }
-cudaError_t launch_reduce(const MatDesc* d_mats, int nmats, const Part* partials, const int* flags,
+cudaError_t launch_reduce(const MatDesc* d_mats, int nmats, long long nchunks, Part* partials, const int* flags,
                           ResultRec* out, cudaStream_t s) {
   if (nmats <= 0) return cudaSuccess;
+  if (nchunks > 0) {
+    if (nchunks > 0x7fffffffll) return cudaErrorInvalidValue;
+    k_reduce_chunks<<<(unsigned)nchunks, kReduceThreads, 0, s>>>(d_mats, nmats, partials);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
   k_reduce<<<nmats, kReduceThreads, 0, s>>>(d_mats, partials, flags, out);
   return cudaGetLastError();
 }

@@ -89,6 +89,7 @@ __global__ void k_noalloc_setup(const double2* O, int n, int ld, int layout) {
     D->red_off = 0;
     D->red_lo = 0;
     D->red_log2 = p >= 5 ? p - 5 : p;
+    D->red_chunk0 = 0;
     D->n = n;
     D->p = p;
     D->ld = ld;
@@ -180,7 +181,7 @@ extern "C" tor_status tor_eval_noalloc(int device, int n, const tor_c128* O, int
       e = launch_units(prm, kNoallocBlocks, s);
     }
     if (e == cudaSuccess)
-      e = launch_reduce((const MatDesc*)(base + OFF_MATS), 1, (const Part*)(base + OFF_REDS),
+      e = launch_reduce((const MatDesc*)(base + OFF_MATS), 1, red_chunks(p >= 5 ? p - 5 : p), (Part*)(base + OFF_REDS),
                         (const int*)(base + OFF_FLAGS), (ResultRec*)(base + OFF_RES), s);
     if (e == cudaSuccess) {
       k_noalloc_finish<<<1, 1, 0, s>>>(out, n);
