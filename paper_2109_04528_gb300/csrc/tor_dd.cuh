@@ -15,6 +15,10 @@
 //   dd_add    20  accurate double-word sum (Joldes, Muller, Popescu, ACM TOMS
 //                 44 (2017), AccurateDWPlusDW): relative error <= 3 u^2, also
 //                 under cancellation
+//   dd_sum    11  sloppy double-word sum (the same paper's SloppyDWPlusDW): its
+//                 relative error is unbounded under cancellation, its absolute
+//                 error stays below ~2 u^2 (|a| + |b|); used for the sums of
+//                 terms, whose accuracy is measured against sum |term|
 //   dd_mul     7  double-word product (the same paper's DWTimesDW with the
 //                 lo * lo term dropped): relative error <= ~5 u^2
 //   ProdAcc       s + sum_i (+-) b_i c_i with one normalisation at the end:
@@ -44,6 +48,14 @@ __device__ __forceinline__ dd_t dd_add(dd_t a, dd_t b) {
   return r;
 }
 __device__ __forceinline__ dd_t dd_neg(dd_t a) { return dd_t{-a.h, -a.l}; }
+__device__ __forceinline__ dd_t dd_sum(dd_t a, dd_t b) {
+  double s, e;
+  two_sum(a.h, b.h, s, e);
+  e = __dadd_rn(e, __dadd_rn(a.l, b.l));
+  dd_t r;
+  fast_two_sum(s, e, r.h, r.l);
+  return r;
+}
 
 __device__ __forceinline__ dd_t dd_mul(dd_t a, dd_t b) {
   double p, e;
@@ -114,10 +126,10 @@ struct XRe {
   static constexpr int kRegModes = 3;  // modes of the register-resident subtrees of the lane walk
   struct Acc {
     dd_t s;
-    __device__ __forceinline__ void add(dd_t v) { s = dd_add(s, v); }
+    __device__ __forceinline__ void add(dd_t v) { s = dd_sum(s, v); }
   };
   static __device__ __forceinline__ dd_t mul(dd_t a, dd_t b) { return dd_mul(a, b); }
-  static __device__ __forceinline__ dd_t sub(dd_t a, dd_t b) { return dd_add(a, dd_neg(b)); }
+  static __device__ __forceinline__ dd_t sub(dd_t a, dd_t b) { return dd_sum(a, dd_neg(b)); }  // sums of terms only
   static __device__ __forceinline__ dd_t neg(dd_t a) { return dd_neg(a); }
   static __device__ __forceinline__ bool pos(dd_t a) { return pos_finite(a.h); }  // h + l > 0 iff h > 0
   static __device__ __forceinline__ dd_t rcp(dd_t a) { return dd_rcp(a); }
@@ -126,7 +138,7 @@ struct XRe {
   static __device__ __forceinline__ dd_t one() { return dd_t{1.0, 0.0}; }
   static __device__ __forceinline__ void pair_sums(dd_t phi, dd_t r, dd_t& v, double& ab) {
     const dd_t pr = dd_mul(phi, r);
-    v = dd_add(pr, dd_neg(phi));
+    v = dd_sum(pr, dd_neg(phi));
     ab = pr.h + phi.h;
   }
   static __device__ __forceinline__ dd_t shfl(dd_t a, int q) {

@@ -69,8 +69,13 @@ class Ops:
         s, e = self.fast_two_sum(s, self.add(e, t))
         return self.fast_two_sum(s, self.add(e, f))
 
+    def dd_sum(self, a, b):  # the sloppy double-word sum, for sums of terms
+        s, e = self.two_sum(a[0], b[0])
+        e = self.add(e, self.add(a[1], b[1]))
+        return self.fast_two_sum(s, e)
+
     def dd_sub(self, a, b):
-        return self.dd_add(a, (-b[0], -b[1]))
+        return self.dd_sum(a, (-b[0], -b[1]))
 
     def dd_mul(self, a, b):
         p, e = self.two_prod(a[0], b[0])
@@ -261,7 +266,7 @@ def walk(A, S, m, phi, excl, acc, o):
     if m <= 3:
         v = subtree(A, S, m, phi, o)  # signs of the exclusions below this node included
         sign = -1.0 if excl % 2 else 1.0  # (-1)^(modes excluded above)
-        acc[0] = o.dd_add(acc[0], (sign * v[0], sign * v[1]))
+        acc[0] = o.dd_sum(acc[0], (sign * v[0], sign * v[1]))
         o.f += 1
         return
     walk(A, trail(S), m - 1, phi, excl + 1, acc, o)
