@@ -22,8 +22,10 @@
 //   dd_mul     7  double-word product (the same paper's DWTimesDW with the
 //                 lo * lo term dropped): relative error <= ~5 u^2
 //   ProdAcc       s + sum_i (+-) b_i c_i with one normalisation at the end:
-//                 12 per product + 6 (a sum that starts from a product: 5 for
-//                 it); absolute error ~ u^2 (|s| + sum |b_i c_i|)
+//                 12 per product + 3 (a sum that starts from a product: 5 for
+//                 it); absolute error ~ u^2 (|s| + sum |b_i c_i|).  The final
+//                 fast_two_sum is exact when |h| >= |t|; when h has cancelled
+//                 below t it adds at most u |t|, inside the same bound
 //   dd_rcp    13  Newton step for 1/a from the FP64 reciprocal, evaluated in
 //                 double-double: 1/a = y (1 + e + e^2 + ...), e = 1 - a y
 //   dd_rsqrt  19  the same for a^{-1/2}: y (1 + e/2 + 3e^2/8 + ...), e = 1 - a y^2
@@ -89,7 +91,7 @@ struct ProdAcc {
   __device__ __forceinline__ void sub(dd_t b, dd_t c) { add(dd_neg(b), c); }  // -= b c
   __device__ __forceinline__ dd_t out() const {
     dd_t r;
-    two_sum(h, t, r.h, r.l);
+    fast_two_sum(h, t, r.h, r.l);
     return r;
   }
 };

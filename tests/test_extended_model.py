@@ -97,7 +97,7 @@ class Ops:
         acc[1] = self.add(acc[1], self.add(r, e))
 
     def acc_out(self, acc):
-        return self.two_sum(acc[0], acc[1])
+        return self.fast_two_sum(acc[0], acc[1])
 
     def rcp(self, a):
         x = a[0]
