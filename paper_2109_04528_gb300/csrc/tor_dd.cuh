@@ -19,8 +19,11 @@
 //                 relative error is unbounded under cancellation, its absolute
 //                 error stays below ~2 u^2 (|a| + |b|); used for the sums of
 //                 terms, whose accuracy is measured against sum |term|
-//   dd_mul     7  double-word product (the same paper's DWTimesDW with the
-//                 lo * lo term dropped): relative error <= ~5 u^2
+//   dd_mul     4  double-word product (the same paper's DWTimesDW with the
+//                 lo * lo term dropped and without its final renormalisation:
+//                 the low part, the product's rounding error plus the cross
+//                 terms, stays below ~2.5 u of the high part, so the pair is a
+//                 double word as it stands): relative error <= ~5 u^2
 //   ProdAcc       s + sum_i (+-) b_i c_i with one normalisation at the end:
 //                 12 per product + 3 (a sum that starts from a product: 5 for
 //                 it); absolute error ~ u^2 (|s| + sum |b_i c_i|).  The final
@@ -64,9 +67,7 @@ __device__ __forceinline__ dd_t dd_mul(dd_t a, dd_t b) {
   two_prod(a.h, b.h, p, e);
   e = __fma_rn(a.h, b.l, e);
   e = __fma_rn(a.l, b.h, e);
-  dd_t r;
-  fast_two_sum(p, e, r.h, r.l);
-  return r;
+  return dd_t{p, e};
 }
 
 // Sum of products, normalised once: h + t holds the running value.

@@ -88,17 +88,17 @@ def path_flops(n: int, path: int = 0) -> float:
     Double-double factor: every FP64 operation of the double-word algorithms
     (add / mul 1, FMA 2; two_sum 6, fast_two_sum 3, two_prod 3; a product
     accumulated into a sum 15, a sum started from a product 7, its final
-    normalisation 3; dd_mul 10, the sloppy double-word sum of terms 11,
+    normalisation 3; dd_mul 7, the sloppy double-word sum of terms 11,
     reciprocal 18 and reciprocal square root 26 with their Newton steps).
     Includes at m >= 1 trailing modes; the last level (m = 0) is a leaf pair,
     which needs only the determinant factor and the signed pair sum; every
     leaf carries 6 of subtree and accumulator sums:
-      real     66 m^2 + 109 m + 109 per include, 73 per leaf pair
+      real     66 m^2 + 97 m + 97 per include, 70 per leaf pair
                (an update entry: two accumulated products + normalisation 33;
-               a pivot-column row 38; pivot 99 and the phi product 10)
-      complex 252 m^2 + 212 m + 134 per include, 88 per leaf pair
+               a pivot-column row 32; pivot 90 and the phi product 7)
+      complex 252 m^2 + 188 m + 119 per include, 85 per leaf pair
                (off-diagonal entry 8 products 126, diagonal 63; pivot-column
-               row 106; pivot 124 + 10)"""
+               row 94; pivot 112 + 7)"""
     real, ext = bool(path & 1), bool(path & 2)
     if not ext:
         a, b, c = (8, 12, 10) if real else (32, 40, 10)
@@ -107,7 +107,7 @@ def path_flops(n: int, path: int = 0) -> float:
             m = n - 1 - j
             f += 2.0 ** j * (a * m * m + b * m + c)
         return f
-    a, b, c, pair = (66, 109, 109, 73.0) if real else (252, 212, 134, 88.0)
+    a, b, c, pair = (66, 97, 97, 70.0) if real else (252, 188, 119, 85.0)
     f = 6.0 * 2.0 ** n + pair * 2.0 ** (n - 1)
     for j in range(n - 1):
         m = n - 1 - j
@@ -139,17 +139,17 @@ def path_ops(n: int, path: int) -> float:
                      double-double sum 8; subtrees of 4 modes in registers
       FP64 complex  16 m^2 + 16 m + 16 / 10  (8 FMA per off-diagonal entry, 4
                      per diagonal one; a row 8; pivot 15 + phi 1); 3 modes
-      double-double real     54 m^2 + 85 m + 77 / 56
-      double-double complex 204 m^2 + 164 m + 96 / 68
+      double-double real     54 m^2 + 73 m + 65 / 53
+      double-double complex 204 m^2 + 140 m + 81 / 65
                      (two_sum 6, fast_two_sum 3, two_prod 2, an accumulated
                      product 12, a sum started from a product 4, its
-                     normalisation 3, dd_mul 7, the sloppy double-word sum of
+                     normalisation 3, dd_mul 4, the sloppy double-word sum of
                      terms 11, reciprocal 12, reciprocal square root 18); a
                      subtree sum and the lane's sum 12 each; 3 modes."""
     real, ext = bool(path & 1), bool(path & 2)
     a, b, c, pair, combine, acc, regs = {
         (True, False): (4, 8, 14, 9.0, 2.0, 8.0, 4), (False, False): (16, 16, 16, 10.0, 2.0, 8.0, 3),
-        (True, True): (54, 85, 77, 56.0, 12.0, 12.0, 3), (False, True): (204, 164, 96, 68.0, 12.0, 12.0, 3)}[(real, ext)]
+        (True, True): (54, 73, 65, 53.0, 12.0, 12.0, 3), (False, True): (204, 140, 81, 65.0, 12.0, 12.0, 3)}[(real, ext)]
     f = pair * 2.0 ** (n - 1) + _leaf_sums(n, combine, acc, regs)
     for j in range(n - 1):
         m = n - 1 - j

@@ -77,11 +77,11 @@ class Ops:
     def dd_sub(self, a, b):
         return self.dd_sum(a, (-b[0], -b[1]))
 
-    def dd_mul(self, a, b):
+    def dd_mul(self, a, b):  # not renormalised: |e| <= ~2.5 u |p|
         p, e = self.two_prod(a[0], b[0])
         e = self.fma(a[0], b[1], e)
         e = self.fma(a[1], b[0], e)
-        return self.fast_two_sum(p, e)
+        return (p, e)
 
     def acc_start(self, b, c):  # a sum that starts from the product b c
         h, t = self.two_prod(b[0], c[0])
