@@ -464,6 +464,59 @@ def run_sample(args, world, rank, local):
     return 0
 
 
+def run_sweep_n(args, world, rank, local):
+    """Subset terms/s against the mode count n, one lossy squeezed state per n
+    (r ~ U[0.3,0.8], eta_j ~ U[0.3,0.7]): the GPU (one device-resident tor_eval,
+    CUDA events, best of a few), the paper's Algorithm 2 in FP64 on all host
+    cores, and the binary128 oracle on all cores and on one.  The CPU rows stop
+    where one evaluation would take longer than a few seconds."""
+    if rank != 0:
+        return 0
+    import torch
+
+    import oracle
+    from oracle import alg2_cpu
+    from paper_2109_04528_gb300 import binding, build
+    build.build()
+    oracle.build()
+    alg2_cpu.build()
+    device = torch.device("cuda", local)
+    torch.cuda.set_device(device)
+    cores = os.cpu_count() or 1
+    rows = []
+    with binding.Context(device=local, flags=binding.TOR_IN_DEVICE) as ctx:
+        for n in range(8, 35, 2):
+            O = inputs.config_single(n, seed=inputs.SEED_BASE + 1000 + n).O
+            d = torch.from_numpy(O).to(device)
+            binding.tor_eval(ctx, d)
+            reps = 5 if n <= 28 else 2
+            best = min((binding.tor_eval(ctx, d), ctx.last_times()["total_ms"])[1] for _ in range(reps))
+            row = {"n": n, "gpu": 2.0 ** n / (best * 1e-3), "gpu_ms": best, "p": ctx.plan_prefix_depth(n)}
+            if n <= 28:
+                t0 = time.perf_counter()
+                r = alg2_cpu.tor_alg2(O, threads=cores)
+                row["cpu_alg2"] = r.terms / (time.perf_counter() - t0)
+            if n <= 18:
+                t0 = time.perf_counter()
+                oracle.tor_brute(O, threads=cores)
+                row["oracle"] = 2.0 ** n / (time.perf_counter() - t0)
+            if n <= 14:
+                t0 = time.perf_counter()
+                oracle.tor_brute(O, threads=1)
+                row["oracle_1core"] = 2.0 ** n / (time.perf_counter() - t0)
+            rows.append(row)
+            print(json.dumps(row), file=sys.stderr, flush=True)
+    out = {"metric": "subset terms/s", "unit": "subset terms/s", "n_gpus": 1, "higher_is_better": True,
+           "dtype": "f64", "data": "synthetic",
+           "config": {"workload": "sweep_n", "desc": "lossy squeezed, r~U[0.3,0.8], eta_j~U[0.3,0.7], one matrix per n",
+                      "gpu": "one tor_eval per matrix, device-resident input, CUDA events (intake, units, reduce), best of 5 (2 for n > 28)",
+                      "cpu_alg2": f"paper Algorithm 2 in FP64, {cores} threads, the whole sum",
+                      "oracle": f"binary128 brute force, {cores} threads and 1 thread, the whole sum", "cpu": cpu_model()},
+           "rows": rows}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -497,6 +550,8 @@ def main():
         return run_serve(args, world, rank, local)
     if args.workload == "sample":
         return run_sample(args, world, rank, local)
+    if args.workload == "sweep_n":
+        return run_sweep_n(args, world, rank, local)
 
     import torch
 

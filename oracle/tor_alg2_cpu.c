@@ -17,11 +17,11 @@
  * rows (Algorithm 1 from row 2q on).  Every node adds
  *     (-1)^{#removed} / sqrt(det(I - O_K)) = (-1)^{#removed} / prod_a L_aa.
  *
- * Parallel split: the nodes with D removed modes are the tasks, ordered
- * largest subtree first (a node whose largest removed mode is r has
- * 2^(n-1-r) nodes below and including it); threads take them from an atomic
- * counter and rebuild each task's factor from the root along its D removals.
- * The caller's thread evaluates the nodes above them.  Sums: Neumaier in FP64,
+ * Parallel split: a node whose largest removed mode is r has 2^(n-1-r) nodes
+ * below and including it.  Nodes with more than 2^n / (32 threads) are split
+ * (the caller's thread adds their own terms), the others are the tasks,
+ * ordered largest subtree first; threads take them from an atomic counter and
+ * rebuild each task's factor from the root along its removals.  Sums: Neumaier in FP64,
  * per task in visiting order, then over tasks in task order, so the result does
  * not depend on the thread count or the schedule.
  */
@@ -49,9 +49,9 @@ static void ns_add(nsum* a, double x) {
 typedef struct {
   int n, N;
   cd* A;            /* I - O, pairs order, full N x N */
-  int D;            /* removed modes of a task node */
   int ntasks;       /* tasks to evaluate (a prefix of the ordered list) */
-  int* task_rm;     /* ntasks x D removed modes, ascending */
+  const int* pool;  /* removed modes of the task nodes, ascending, back to back */
+  const int* task_off, *task_len;  /* task t: pool[task_off[t] .. task_off[t] + task_len[t]) */
   nsum* task_tor;   /* per task */
   nsum* task_abs;
   int* task_rc;
@@ -153,15 +153,16 @@ static void* worker(void* arg) {
   for (;;) {
     const int t = __atomic_fetch_add(&S->next, 1, __ATOMIC_RELAXED);
     if (t >= S->ntasks) break;
-    const int* rm = S->task_rm + (size_t)t * S->D;
+    const int* rm = S->pool + S->task_off[t];
+    const int d = S->task_len[t];
     nsum tor = {0, 0}, ab = {0, 0};
-    int rc = node_factor(S, rm, S->D, kept, L, kept + n, L + (size_t)N * N);
-    const int nk = n - S->D;
+    int rc = node_factor(S, rm, d, kept, L, kept + n, L + (size_t)N * N);
+    const int nk = n - d;
     if (!rc) {
       const double v = inv_sqrt_det(L, 2 * nk);
-      ns_add(&tor, (S->D & 1) ? -v : v);
+      ns_add(&tor, (d & 1) ? -v : v);
       ns_add(&ab, v);
-      rc = subtree(S, kept, nk, L, S->D, rm[S->D - 1] + 1, kept + 2 * n, L + (size_t)2 * N * N, &tor, &ab);
+      rc = subtree(S, kept, nk, L, d, rm[d - 1] + 1, kept + 2 * n, L + (size_t)2 * N * N, &tor, &ab);
     }
     S->task_tor[t] = tor;
     S->task_abs[t] = ab;
@@ -172,43 +173,67 @@ static void* worker(void* arg) {
   return 0;
 }
 
-/* Removed sets of size d (ascending modes), ordered by largest mode ascending,
- * then lexicographically: largest subtree first. */
-static int enumerate(int n, int d, int* out) {
-  int cnt = 0, c[64];
-  for (int top = d - 1; top < n; ++top) {
-    /* sets {c_0 < ... < c_{d-2}} < top, lexicographic */
-    for (int i = 0; i < d - 1; ++i) c[i] = i;
-    for (;;) {
-      if (out) {
-        for (int i = 0; i < d - 1; ++i) out[cnt * d + i] = c[i];
-        out[cnt * d + d - 1] = top;
-      }
-      ++cnt;
-      int i = d - 2;
-      while (i >= 0 && c[i] == top - (d - 1) + i) --i;
-      if (i < 0) break;
-      ++c[i];
-      for (int k = i + 1; k < d - 1; ++k) c[k] = c[k - 1] + 1;
-    }
+/* Growable list of removed-mode sets. */
+typedef struct {
+  int *pool, *off, *len;
+  long long used, cap;
+  int cnt, capn;
+} setlist;
+
+static int sl_push(setlist* L, const int* R, int d) {
+  if (L->used + d > L->cap) {
+    long long c = L->cap ? 2 * L->cap : 1024;
+    while (c < L->used + d) c *= 2;
+    int* p = (int*)realloc(L->pool, sizeof(int) * (size_t)c);
+    if (!p) return -1;
+    L->pool = p;
+    L->cap = c;
   }
-  return cnt;
+  if (L->cnt == L->capn) {
+    int c = L->capn ? 2 * L->capn : 256;
+    int* o = (int*)realloc(L->off, sizeof(int) * (size_t)c);
+    if (!o) return -1;
+    L->off = o;
+    int* l = (int*)realloc(L->len, sizeof(int) * (size_t)c);
+    if (!l) return -1;
+    L->len = l;
+    L->capn = c;
+  }
+  L->off[L->cnt] = (int)L->used;
+  L->len[L->cnt] = d;
+  memcpy(L->pool + L->used, R, sizeof(int) * (size_t)d);
+  L->used += d;
+  ++L->cnt;
+  return 0;
 }
 
-static double binom(int n, int k) {
-  double r = 1;
-  for (int i = 0; i < k; ++i) r = r * (n - i) / (i + 1);
-  return r;
+static void sl_free(setlist* L) {
+  free(L->pool);
+  free(L->off);
+  free(L->len);
+}
+
+/* Node R (d removed modes, ascending): a task if its subtree has at most T
+ * nodes, else split (R goes to `top`, its children are visited in order). */
+static int gen(int n, double T, int* R, int d, setlist* top, setlist* tasks) {
+  const double size = d == 0 ? ldexp(1.0, n) : ldexp(1.0, n - 1 - R[d - 1]);
+  if (d > 0 && size <= T) return sl_push(tasks, R, d);
+  if (sl_push(top, R, d)) return -1;
+  for (int i = d ? R[d - 1] + 1 : 0; i < n; ++i) {
+    R[d] = i;
+    if (gen(n, T, R, d + 1, top, tasks)) return -1;
+  }
+  return 0;
 }
 
 /*
  * Tor of the 2n x 2n matrix O (complex128 interleaved, row stride ld complex
  * entries; layout 0: mode j owns rows {j, j+n}; 1: rows {2j, 2j+1}).
  * threads >= 1.  max_tasks < 0: every node (the full sum); otherwise only the
- * nodes above the tasks and the first max_tasks tasks (largest first), a
- * bounded sample for timing.  out[0] = the (partial) Tor, out[1] = its sum of
- * |term|, out[2] = the number of terms evaluated.  Returns 0, -1 (arguments,
- * memory) or -2 (not positive definite).
+ * split nodes and the first max_tasks tasks (largest first), a bounded sample
+ * for timing.  out[0] = the (partial) Tor, out[1] = its sum of |term|,
+ * out[2] = the number of terms evaluated.  Returns 0, -1 (arguments, memory)
+ * or -2 (not positive definite).
  */
 int tor_alg2_fp64(int n, const double* O, int ld, int layout, int threads, long long max_tasks, double* out) {
   if (n < 1 || n > 60 || !O || !out || ld < 2 * n || threads < 1) return -1;
@@ -227,54 +252,58 @@ int tor_alg2_fp64(int n, const double* O, int ld, int layout, int threads, long 
       S.A[a * N + b].re = (a == b ? 1.0 : 0.0) - o[0];
       S.A[a * N + b].im = -o[1];
     }
-  /* task depth: enough tasks for the threads, at most n - 1 */
-  int D = 1;
-  while (D < n - 1 && binom(n, D) < 16.0 * threads) ++D;
-  S.D = D;
-  const int total = enumerate(n, D, NULL);
-  S.task_rm = (int*)malloc(sizeof(int) * (size_t)total * D);
-  S.task_tor = (nsum*)calloc((size_t)total, sizeof(nsum));
-  S.task_abs = (nsum*)calloc((size_t)total, sizeof(nsum));
-  S.task_rc = (int*)calloc((size_t)total, sizeof(int));
+  setlist top, gtasks;
+  memset(&top, 0, sizeof top);
+  memset(&gtasks, 0, sizeof gtasks);
+  int R[64];
+  double T = ldexp(1.0, n) / (32.0 * threads);
+  if (T < 1.0) T = 1.0;
+  int rc = gen(n, T, R, 0, &top, &gtasks) ? -1 : 0;
+  /* tasks ordered largest subtree first (largest removed mode ascending), in generation order within a size */
+  const int total = gtasks.cnt;
+  int* off = (int*)malloc(sizeof(int) * (size_t)(total > 0 ? total : 1));
+  int* len = (int*)malloc(sizeof(int) * (size_t)(total > 0 ? total : 1));
+  S.task_tor = (nsum*)calloc((size_t)(total > 0 ? total : 1), sizeof(nsum));
+  S.task_abs = (nsum*)calloc((size_t)(total > 0 ? total : 1), sizeof(nsum));
+  S.task_rc = (int*)calloc((size_t)(total > 0 ? total : 1), sizeof(int));
   int* kept = (int*)malloc(sizeof(int) * (size_t)n * 2);
   cd* L = (cd*)calloc((size_t)N * N * 2, sizeof(cd));
-  int rc = (!S.task_rm || !S.task_tor || !S.task_abs || !S.task_rc || !kept || !L) ? -1 : 0;
+  if (!off || !len || !S.task_tor || !S.task_abs || !S.task_rc || !kept || !L) rc = -1;
+  if (!rc) {
+    int k = 0;
+    for (int r = 0; r < n; ++r)
+      for (int t = 0; t < total; ++t)
+        if (gtasks.pool[gtasks.off[t] + gtasks.len[t] - 1] == r) {
+          off[k] = gtasks.off[t];
+          len[k] = gtasks.len[t];
+          ++k;
+        }
+    S.pool = gtasks.pool;
+    S.task_off = off;
+    S.task_len = len;
+    S.ntasks = max_tasks < 0 || max_tasks > total ? total : (int)max_tasks;
+  }
   nsum tor = {0, 0}, ab = {0, 0};
   double terms = 0;
-  if (!rc) {
-    enumerate(n, D, S.task_rm);
-    S.ntasks = max_tasks < 0 || max_tasks > total ? total : (int)max_tasks;
-    /* the nodes above the tasks: removed sets of size < D, in the same order */
-    for (int d = 0; d < D && !rc; ++d) {
-      const int cnt = enumerate(n, d > 0 ? d : 1, NULL);
-      int* sets = (int*)malloc(sizeof(int) * (size_t)cnt * (d > 0 ? d : 1));
-      if (!sets) {
-        rc = -1;
-        break;
-      }
-      enumerate(n, d > 0 ? d : 1, sets);
-      const int count = d == 0 ? 1 : cnt;
-      for (int s = 0; s < count && !rc; ++s) {
-        if (node_factor(&S, sets + (size_t)s * d, d, kept, L, kept + n, L + (size_t)N * N)) {
-          rc = -2;
-          break;
-        }
-        const double v = inv_sqrt_det(L, 2 * (n - d));
-        ns_add(&tor, (d & 1) ? -v : v);
-        ns_add(&ab, v);
-        terms += 1;
-      }
-      free(sets);
+  /* the split nodes' own terms, in generation order */
+  for (int s = 0; !rc && s < top.cnt; ++s) {
+    const int d = top.len[s];
+    if (node_factor(&S, top.pool + top.off[s], d, kept, L, kept + n, L + (size_t)N * N)) {
+      rc = -2;
+      break;
     }
+    const double v = inv_sqrt_det(L, 2 * (n - d));
+    ns_add(&tor, (d & 1) ? -v : v);
+    ns_add(&ab, v);
+    terms += 1;
   }
   if (!rc) {
-    const int nt = threads;
-    pthread_t* th = (pthread_t*)malloc(sizeof(pthread_t) * (size_t)nt);
+    pthread_t* th = (pthread_t*)malloc(sizeof(pthread_t) * (size_t)threads);
     int started = 0;
     if (!th) rc = -1;
-    for (int t = 0; !rc && t < nt; ++t)
+    for (int t = 0; !rc && t < threads; ++t)
       if (pthread_create(&th[t], NULL, worker, &S) == 0) ++started;
-    if (!rc && started == 0) worker(&S);
+    if (!rc && started == 0 && worker(&S)) rc = -1;
     for (int t = 0; t < started; ++t) {
       void* r = 0;
       pthread_join(th[t], &r);
@@ -290,7 +319,7 @@ int tor_alg2_fp64(int n, const double* O, int ld, int layout, int threads, long 
       ns_add(&tor, S.task_tor[t].c);
       ns_add(&ab, S.task_abs[t].s);
       ns_add(&ab, S.task_abs[t].c);
-      terms += ldexp(1.0, n - 1 - S.task_rm[(size_t)t * D + D - 1]);
+      terms += ldexp(1.0, n - 1 - S.pool[S.task_off[t] + S.task_len[t] - 1]);
     }
   }
   if (!rc) {
@@ -300,10 +329,13 @@ int tor_alg2_fp64(int n, const double* O, int ld, int layout, int threads, long 
   }
   free(kept);
   free(L);
-  free(S.task_rm);
+  free(off);
+  free(len);
   free(S.task_tor);
   free(S.task_abs);
   free(S.task_rc);
+  sl_free(&top);
+  sl_free(&gtasks);
   free(S.A);
   return rc;
 }

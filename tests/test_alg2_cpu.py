@@ -2,8 +2,6 @@
 of the paper's own method (Sec. 2, Algorithm 2), checked on the CPU against
 the binary128 oracle and against what its task split fixes.
 """
-from math import comb
-
 import numpy as np
 import pytest
 
@@ -57,18 +55,37 @@ def test_thread_count_does_not_change_the_result():
     assert (a.tor, a.abs_sum, a.terms) == (b.tor, b.abs_sum, b.terms)
 
 
-def test_sample_counts_its_terms():
-    # max_tasks = 0: only the nodes above the task level (removed sets of size < D);
-    # each task with largest removed mode r adds the 2^(n-1-r) nodes of its subtree
-    n, threads = 11, 2
+def _split(n, threads):
+    # the baseline's task split, restated: a node whose largest removed mode is r
+    # heads 2^(n-1-r) nodes; nodes above 2^n / (32 threads) are split, the rest are
+    # tasks, largest subtree first
+    T = max(1.0, 2.0 ** n / (32 * threads))
+    top, tasks = [], []
+
+    def gen(R):
+        size = 2.0 ** n if not R else 2.0 ** (n - 1 - R[-1])
+        if R and size <= T:
+            tasks.append(tuple(R))
+            return
+        top.append(tuple(R))
+        for i in range(R[-1] + 1 if R else 0, n):
+            gen(R + [i])
+
+    gen([])
+    tasks.sort(key=lambda R: R[-1])
+    return top, tasks
+
+
+@pytest.mark.parametrize("n,threads", [(11, 2), (14, 16)])
+def test_sample_counts_its_terms(n, threads):
+    # max_tasks = 0: only the split nodes; each task adds the nodes of its subtree
     inst = inputs.config_single(n)
-    D = 1
-    while D < n - 1 and comb(n, D) < 16 * threads:
-        D += 1
-    top = sum(comb(n, d) for d in range(D))
-    assert alg2_cpu.tor_alg2(inst.O, threads=threads, max_tasks=0).terms == top
-    # the first task removes modes 0..D-1: 2^(n-D) nodes
-    assert alg2_cpu.tor_alg2(inst.O, threads=threads, max_tasks=1).terms == top + 2 ** (n - D)
+    top, tasks = _split(n, threads)
+    assert len(top) + sum(2 ** (n - 1 - R[-1]) for R in tasks) == 2 ** n
+    assert max(2 ** (n - 1 - R[-1]) for R in tasks) <= max(1, 2 ** n // (32 * threads))  # balanced
+    assert alg2_cpu.tor_alg2(inst.O, threads=threads, max_tasks=0).terms == len(top)
+    first = len(top) + 2 ** (n - 1 - tasks[0][-1])
+    assert alg2_cpu.tor_alg2(inst.O, threads=threads, max_tasks=1).terms == first
     assert alg2_cpu.tor_alg2(inst.O, threads=threads, max_tasks=10 ** 9).terms == 2 ** n
 
 
