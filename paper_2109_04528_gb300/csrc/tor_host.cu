@@ -116,8 +116,12 @@ struct MatIn {
 struct Slot {
   cudaStream_t stream = nullptr;
   bool own_stream = false;
-  DevBuf d_O, d_B, d_mats, d_tasks, d_partials, d_flags, d_results, d_lane, d_warp, d_ctl, d_modes;
-  HostBuf h_O, h_mats, h_tasks, h_results, h_ctl, h_modes;
+  DevBuf d_O, d_B, d_front, d_partials, d_flags, d_results, d_lane, d_warp, d_modes;
+  HostBuf h_O, h_front, h_results, h_ctl, h_modes;
+  // d_front holds the control words (64 bytes, zero at the start of a pass), the
+  // matrix descriptors and the task list, uploaded from h_front in one copy
+  void *p_ctl = nullptr, *p_mats = nullptr, *p_tasks = nullptr;
+  size_t off_mats = 0, off_tasks = 0, front_bytes = 0;
   cudaEvent_t ev[5] = {};
   cudaEvent_t done = nullptr;
   uint64_t gen = 0;
@@ -144,10 +148,9 @@ struct Slot {
   double t_start = 0;
 
   void release() {
-    for (DevBuf* b : {&d_O, &d_B, &d_mats, &d_tasks, &d_partials, &d_flags, &d_results, &d_lane, &d_warp, &d_ctl,
-                      &d_modes})
+    for (DevBuf* b : {&d_O, &d_B, &d_front, &d_partials, &d_flags, &d_results, &d_lane, &d_warp, &d_modes})
       b->release();
-    for (HostBuf* b : {&h_O, &h_mats, &h_tasks, &h_results, &h_ctl, &h_modes}) b->release();
+    for (HostBuf* b : {&h_O, &h_front, &h_results, &h_ctl, &h_modes}) b->release();
     for (auto& g : graphs) cudaGraphExecDestroy(g.exec);
     graphs.clear();
     for (int i = 0; i < 5; ++i)
@@ -429,20 +432,23 @@ static tor_status slot_prepare(tor_ctx* ctx, Slot& S, const std::vector<MatIn>& 
   CK(S.d_O.ensure(S.o_elems * 16, g), "alloc O");
   CK(S.d_B.ensure(S.b_elems * eb, g), "alloc B");
   CK(S.d_partials.ensure((S.parts + S.reds) * 32, g), "alloc partials");
-  CK(S.d_mats.ensure(J * sizeof(MatDesc), g), "alloc mats");
-  CK(S.d_tasks.ensure(S.tasks.size() * sizeof(TaskDesc), g), "alloc tasks");
+  S.off_mats = 256;
+  S.off_tasks = (S.off_mats + J * sizeof(MatDesc) + 255) / 256 * 256;
+  S.front_bytes = S.off_tasks + S.tasks.size() * sizeof(TaskDesc);
+  CK(S.d_front.ensure(S.front_bytes, g), "alloc descriptors");
   CK(S.d_flags.ensure(J * sizeof(int), g), "alloc flags");
   CK(S.d_results.ensure(J * sizeof(ResultRec), g), "alloc results");
   CK(S.d_lane.ensure(lane_bytes, g), "alloc lane scratch");
   CK(S.d_warp.ensure(warp_bytes, g), "alloc warp scratch");
-  CK(S.d_ctl.ensure(64, g), "alloc control");
   CK(S.d_modes.ensure(S.mode_elems * sizeof(int), g), "alloc modes");
   CK(S.h_O.ensure(S.o_elems * 16, g), "pinned O");
-  CK(S.h_mats.ensure(J * sizeof(MatDesc), g), "pinned mats");
-  CK(S.h_tasks.ensure(S.tasks.size() * sizeof(TaskDesc), g), "pinned tasks");
+  CK(S.h_front.ensure(S.front_bytes, g), "pinned descriptors");
   CK(S.h_results.ensure(J * sizeof(ResultRec) + (want_parts ? S.parts * 32 : 0), g), "pinned results");
   CK(S.h_ctl.ensure(64, g), "pinned control");
   CK(S.h_modes.ensure(S.mode_elems * sizeof(int), g), "pinned modes");
+  S.p_ctl = S.d_front.p;
+  S.p_mats = (char*)S.d_front.p + S.off_mats;
+  S.p_tasks = (char*)S.d_front.p + S.off_tasks;
   // staging
   long long oo = 0, bo = 0, mo = 0;
   double2* dO = (double2*)S.d_O.p;
@@ -474,8 +480,9 @@ static tor_status slot_prepare(tor_ctx* ctx, Slot& S, const std::vector<MatIn>& 
     D.B = dB + bo;
     bo += tri(m.n) * (long long)(eb / sizeof(double2));
   }
-  memcpy(S.h_mats.p, S.mats.data(), J * sizeof(MatDesc));
-  memcpy(S.h_tasks.p, S.tasks.data(), S.tasks.size() * sizeof(TaskDesc));
+  memset(S.h_front.p, 0, 64);  // the control words
+  memcpy((char*)S.h_front.p + S.off_mats, S.mats.data(), J * sizeof(MatDesc));
+  memcpy((char*)S.h_front.p + S.off_tasks, S.tasks.data(), S.tasks.size() * sizeof(TaskDesc));
   S.J = J;
   *any = true;
   return first;
@@ -496,13 +503,10 @@ static tor_status rec_front(tor_ctx* ctx, Slot& S, bool timed) {
   if (S.o_elems) CK(cudaMemcpyAsync(S.d_O.p, S.h_O.p, S.o_elems * 16, cudaMemcpyHostToDevice, s), "H2D O");
   if (S.mode_elems)
     CK(cudaMemcpyAsync(S.d_modes.p, S.h_modes.p, S.mode_elems * sizeof(int), cudaMemcpyHostToDevice, s), "H2D modes");
-  CK(cudaMemcpyAsync(S.d_mats.p, S.h_mats.p, J * sizeof(MatDesc), cudaMemcpyHostToDevice, s), "H2D mats");
-  CK(cudaMemcpyAsync(S.d_tasks.p, S.h_tasks.p, S.tasks.size() * sizeof(TaskDesc), cudaMemcpyHostToDevice, s),
-     "H2D tasks");
-  CK(cudaMemsetAsync(S.d_ctl.p, 0, 64, s), "memset control");
+  CK(cudaMemcpyAsync(S.p_ctl, S.h_front.p, S.front_bytes, cudaMemcpyHostToDevice, s), "H2D descriptors");
   if (timed) CK(cudaEventRecord(S.ev[1], s), "event");
   const bool check = !(ctx->cfg.flags & TOR_NO_CHECK);
-  CK(launch_intake((const MatDesc*)S.d_mats.p, J, check ? 1 : 0, (int*)S.d_flags.p, s), "k_intake");
+  CK(launch_intake((const MatDesc*)S.p_mats, J, check ? 1 : 0, (int*)S.d_flags.p, s), "k_intake");
   if (timed) CK(cudaEventRecord(S.ev[2], s), "event");
   return TOR_OK;
 }
@@ -511,11 +515,11 @@ static tor_status rec_front(tor_ctx* ctx, Slot& S, bool timed) {
 // long and copies (ticket, abort word) to h_ctl so the host can relaunch it.
 static tor_status rec_units(tor_ctx* ctx, Slot& S, long long slice_ns) {
   UnitsParams prm{};
-  prm.mats = (const MatDesc*)S.d_mats.p;
-  prm.tasks = (const TaskDesc*)S.d_tasks.p;
+  prm.mats = (const MatDesc*)S.p_mats;
+  prm.tasks = (const TaskDesc*)S.p_tasks;
   prm.ntasks = (int)S.tasks.size();
-  prm.ticket = (unsigned*)S.d_ctl.p;
-  prm.abort_word = (int*)S.d_ctl.p + 1;
+  prm.ticket = (unsigned*)S.p_ctl;
+  prm.abort_word = (int*)S.p_ctl + 1;
   prm.partials = (Part*)S.d_partials.p;
   prm.red_leaves = (Part*)S.d_partials.p + S.parts;
   prm.mat_flags = (int*)S.d_flags.p;
@@ -530,7 +534,7 @@ static tor_status rec_units(tor_ctx* ctx, Slot& S, long long slice_ns) {
   prm.ext = (ctx->cfg.flags & TOR_EXTENDED) ? 1 : 0;
   CK(launch_units(prm, ctx->grid, S.stream), "k_units");
   if (slice_ns > 0) {
-    CK(cudaMemcpyAsync(S.h_ctl.p, S.d_ctl.p, 2 * sizeof(int), cudaMemcpyDeviceToHost, S.stream), "D2H ticket");
+    CK(cudaMemcpyAsync(S.h_ctl.p, S.p_ctl, 2 * sizeof(int), cudaMemcpyDeviceToHost, S.stream), "D2H ticket");
     CK(cudaEventRecord(S.units_done, S.stream), "event");
   }
   return TOR_OK;
@@ -540,7 +544,7 @@ static tor_status rec_back(tor_ctx* ctx, Slot& S, bool timed) {
   cudaStream_t s = S.stream;
   const int J = S.J;
   if (timed) CK(cudaEventRecord(S.ev[3], s), "event");
-  CK(launch_reduce((const MatDesc*)S.d_mats.p, J, S.red_chunks, (Part*)S.d_partials.p + S.parts, (const int*)S.d_flags.p,
+  CK(launch_reduce((const MatDesc*)S.p_mats, J, S.red_chunks, (Part*)S.d_partials.p + S.parts, (const int*)S.d_flags.p,
                    (ResultRec*)S.d_results.p, s),
      "k_reduce");
   if (timed) CK(cudaEventRecord(S.ev[4], s), "event");
@@ -549,7 +553,7 @@ static tor_status rec_back(tor_ctx* ctx, Slot& S, bool timed) {
     CK(cudaMemcpyAsync((char*)S.h_results.p + J * sizeof(ResultRec), S.d_partials.p, S.parts * 32,
                        cudaMemcpyDeviceToHost, s),
        "D2H partials");
-  CK(cudaMemcpyAsync(S.h_ctl.p, S.d_ctl.p, 2 * sizeof(int), cudaMemcpyDeviceToHost, s), "D2H control");
+  CK(cudaMemcpyAsync(S.h_ctl.p, S.p_ctl, 2 * sizeof(int), cudaMemcpyDeviceToHost, s), "D2H control");
   return TOR_OK;
 }
 
@@ -740,7 +744,7 @@ static void server_loop(tor_ctx* ctx) {
           } else if (timed_out && ticket < S.tasks.size()) {
             int* w = (int*)S.h_ctl.p + 8;  // pinned; the results of this job become TOR_ETIMEOUT
             *w = ABORT_TIMEOUT;
-            cudaMemcpyAsync((int*)S.d_ctl.p + 1, w, sizeof(int), cudaMemcpyHostToDevice, S.stream);
+            cudaMemcpyAsync((int*)S.p_ctl + 1, w, sizeof(int), cudaMemcpyHostToDevice, S.stream);
           }
         }
         if (st == TOR_OK) st = rec_back(ctx, S, false);
