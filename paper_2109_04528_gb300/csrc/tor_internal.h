@@ -84,10 +84,12 @@ __host__ __device__ constexpr long long red_chunks(int red_log2) {
 // ---- scratch sizes, in entries of the arithmetic's own type (one definition
 // for the kernels, the host runtime and the allocation-free entry point) ----
 __host__ __device__ constexpr int tri_size(int m) { return m * (2 * m + 1); }  // packed entries, m modes
-// sum_{k=4}^{m-1} k(2k+1): offset of the lane stack buffer for m modes past the root
+// sum_{k=3}^{m-1} k(2k+1): offset of the lane stack buffer for m modes past the
+// root (levels from 3 modes up: a walk with 2-mode register subtrees stores
+// 3-mode nodes)
 __host__ __device__ constexpr int stack_off(int m) {
   int s = 0;
-  for (int k = 4; k < m; ++k) s += tri_size(k);
+  for (int k = 3; k < m; ++k) s += tri_size(k);
   return s;
 }
 // breadth-first fan-out arena of a task: level d's include children (2^d nodes of m0 - d - 1 modes)

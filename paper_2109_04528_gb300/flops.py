@@ -145,11 +145,11 @@ def path_ops(n: int, path: int) -> float:
                      product 12, a sum started from a product 4, its
                      normalisation 3, dd_mul 4, the sloppy double-word sum of
                      terms 11, reciprocal 12, reciprocal square root 18); a
-                     subtree sum and the lane's sum 12 each; 3 modes."""
+                     subtree sum and the lane's sum 12 each; 2 modes."""
     real, ext = bool(path & 1), bool(path & 2)
     a, b, c, pair, combine, acc, regs = {
         (True, False): (4, 8, 14, 9.0, 2.0, 8.0, 4), (False, False): (16, 16, 16, 10.0, 2.0, 8.0, 3),
-        (True, True): (54, 73, 65, 53.0, 12.0, 12.0, 3), (False, True): (204, 140, 81, 65.0, 12.0, 12.0, 3)}[(real, ext)]
+        (True, True): (54, 73, 65, 53.0, 12.0, 12.0, 2), (False, True): (204, 140, 81, 65.0, 12.0, 12.0, 2)}[(real, ext)]
     f = pair * 2.0 ** (n - 1) + _leaf_sums(n, combine, acc, regs)
     for j in range(n - 1):
         m = n - 1 - j

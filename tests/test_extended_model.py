@@ -252,7 +252,7 @@ def leaf_pair(A, S, phi, o):
 
 
 def subtree(A, S, m, phi, o):
-    """Signed sum below a node with m <= 3 modes (register subtree)."""
+    """Signed sum below a node with m <= 2 modes (register subtree)."""
     if m == 1:
         return leaf_pair(A, S, phi, o)
     v1 = subtree(A, trail(S), m - 1, phi, o)
@@ -263,7 +263,7 @@ def subtree(A, S, m, phi, o):
 
 
 def walk(A, S, m, phi, excl, acc, o):
-    if m <= 3:
+    if m <= 2:
         v = subtree(A, S, m, phi, o)  # signs of the exclusions below this node included
         sign = -1.0 if excl % 2 else 1.0  # (-1)^(modes excluded above)
         acc[0] = o.dd_sum(acc[0], (sign * v[0], sign * v[1]))
