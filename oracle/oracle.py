@@ -49,6 +49,8 @@ def _lib():
         lib.tor_oracle_brute.argtypes = [ctypes.c_int, dp, ctypes.c_int, ctypes.c_int, ctypes.c_uint64,
                                          ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int, ctypes.c_int, dp]
         lib.tor_oracle_recursive.argtypes = [ctypes.c_int, dp, ctypes.c_int, ctypes.c_int, dp]
+        lib.tor_oracle_recursive_split.argtypes = [ctypes.c_int, dp, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                                   ctypes.c_int, dp]
         lib.tor_oracle_det.argtypes = [ctypes.c_int, dp, ctypes.c_int, ctypes.c_int, ctypes.c_uint64, dp]
         lib.tor_oracle_quad_bits.argtypes = []
         _LIB = lib
@@ -102,12 +104,18 @@ def tor_unit(O: np.ndarray, p: int, u: int, layout: int = 0, threads: int | None
     return tor_brute(O, layout, threads, base=u, stride=1 << p, count=1 << (n - p))
 
 
-def tor_recursive(O: np.ndarray, layout: int = 0) -> OracleResult:
-    """The paper's Algorithm 2 (remove-mode recursion reusing L11/L21) in binary128."""
+def tor_recursive(O: np.ndarray, layout: int = 0, split: int = 0, threads: int | None = 1) -> OracleResult:
+    """The paper's Algorithm 2 (remove-mode recursion reusing L11/L21) in binary128.
+
+    split = d > 0 cuts the recursion into the 2^d tasks given by the removals
+    among modes 0..d-1 (the paper spreads the first loop of Algorithm 2 over
+    workers, Sec. 4); each task sums its addends, and the task sums are added in
+    task order, so the value depends on d but not on the thread count."""
     O, n = _as_input(O)
     out = (ctypes.c_double * 3)()
     ptr = O.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) if n else None
-    rc = _lib().tor_oracle_recursive(n, ptr, max(2 * n, 1), layout, out)
+    split = max(0, min(int(split), n))
+    rc = _lib().tor_oracle_recursive_split(n, ptr, max(2 * n, 1), layout, split, _threads(threads), out)
     if rc == -2:
         raise ValueError("I - O is not positive definite")
     if rc:

@@ -247,58 +247,146 @@ static int chol_rows(const cq* M, cq* L, int m, int r0) {
   return 0;
 }
 
-/* kept: list of kept modes (ascending), L: factor of I - A restricted to them. */
-static int recursive_tor(rec_state* S, const int* kept, int nk, const cq* L, int removed_count, int start) {
+/* One step of Algorithm 2: remove mode i (at position q of kept) from the kept set.
+ * createAZ builds I - A_Z for the reduced set; the rows and columns before the
+ * removed mode keep L11 and L21 of the parent factor (Fig. 2) and only the block
+ * 22 is refactored (Algorithm 1).  Returns the new kept list and factor
+ * (caller frees), or 0 if I - A_Z is not positive definite. */
+static cq* remove_mode(const rec_state* S, const int* kept, int nk, const cq* L, int q, int** kept_out) {
   int m = 2 * nk;
+  int nk2 = nk - 1, m2 = 2 * nk2;
+  int* kept2 = (int*)malloc(sizeof(int) * (size_t)(nk2 > 0 ? nk2 : 1));
+  for (int t = 0, u = 0; t < nk; ++t) if (t != q) kept2[u++] = kept[t];
+  /* Only lower triangles are written and read: M2 and L2 are Hermitian and
+   * lower triangular respectively, and Algorithm 1 reads M2 on and below the
+   * diagonal. */
+  cq* M2 = (cq*)malloc(sizeof(cq) * (size_t)(m2 > 0 ? m2 * m2 : 1));
+  cq* L2 = (cq*)malloc(sizeof(cq) * (size_t)(m2 > 0 ? m2 * m2 : 1));
+  int r0 = 2 * q;
+  /* createAZ: the entries of I - A_Z for the reduced mode set (A is global)
+   * that the refactorisation of block 22 reads: rows r0.., columns r0..row */
+  for (int a = r0; a < m2; ++a)
+    for (int b = r0; b <= a; ++b) {
+      int ra = 2 * kept2[a / 2] + (a & 1), rb = 2 * kept2[b / 2] + (b & 1);
+      M2[a * m2 + b] = S->A[ra * S->N + rb];
+    }
+  /* reuse L11 (rows/cols before mode i) and L21 (rows after, cols before) */
+  for (int a = 0; a < m2; ++a)
+    for (int b = 0; b < r0 && b <= a; ++b) {
+      int pa = a < r0 ? a : a + 2;   /* row index in the parent factor */
+      L2[a * m2 + b] = L[pa * m + b];
+    }
+  int rc = chol_rows(M2, L2, m2, r0);   /* recompute block 22 */
+  free(M2);
+  if (rc) { free(kept2); free(L2); return 0; }
+  *kept_out = kept2;
+  return L2;
+}
+
+/* The addend of one node: (-1)^{#removed} / sqrt(prod |L_aa|^2), into the node's sums. */
+static void add_term(rec_state* S, const cq* L, int m, int removed_count) {
+  quad det = 1;
+  for (int a = 0; a < m; ++a) det *= c_abs2(L[a * m + a]);
+  quad t = 1 / q_sqrt(det);
+  quad term = (removed_count & 1) ? -t : t;
+  nm_add(&S->tor, term);
+  nm_add(&S->abs, t);
+}
+
+/* kept: list of kept modes (ascending), L: factor of I - A restricted to them.
+ * Removes, one per step, every kept mode i >= start (the loop of Algorithm 2),
+ * adds that node's addend and recurses with start = i + 1. */
+static int recursive_tor(rec_state* S, const int* kept, int nk, const cq* L, int removed_count, int start) {
   for (int i = start; i < S->n; ++i) {
     /* position of mode i in kept */
     int q = -1;
     for (int t = 0; t < nk; ++t) if (kept[t] == i) { q = t; break; }
     if (q < 0) continue;
-    int nk2 = nk - 1, m2 = 2 * nk2;
-    int* kept2 = (int*)malloc(sizeof(int) * (size_t)(nk2 > 0 ? nk2 : 1));
-    for (int t = 0, u = 0; t < nk; ++t) if (t != q) kept2[u++] = kept[t];
-    cq* M2 = (cq*)malloc(sizeof(cq) * (size_t)(m2 > 0 ? m2 * m2 : 1));
-    cq* L2 = (cq*)calloc((size_t)(m2 > 0 ? m2 * m2 : 1), sizeof(cq));
-    /* createAZ: the matrix I - A_Z for the reduced mode set */
-    for (int a = 0; a < m2; ++a)
-      for (int b = 0; b < m2; ++b) {
-        int ra = 2 * kept2[a / 2] + (a & 1), rb = 2 * kept2[b / 2] + (b & 1);
-        M2[a * m2 + b] = S->A[ra * S->N + rb];
-      }
-    /* reuse L11 (rows/cols before mode i) and L21 (rows after, cols before) */
-    int r0 = 2 * q;
-    for (int a = 0; a < m2; ++a)
-      for (int b = 0; b < r0 && b <= a; ++b) {
-        int pa = a < r0 ? a : a + 2;   /* row index in the parent factor */
-        L2[a * m2 + b] = L[pa * m + b];
-      }
-    int rc = chol_rows(M2, L2, m2, r0);   /* recompute block 22 */
-    if (rc) { free(kept2); free(M2); free(L2); return rc; }
-    quad det = 1;
-    for (int a = 0; a < m2; ++a) det *= c_abs2(L2[a * m2 + a]);
-    quad t = 1 / q_sqrt(det);
-    int rem = removed_count + 1;
-    quad term = (rem & 1) ? -t : t;
-    nm_add(&S->tor, term);
-    nm_add(&S->abs, t);
-    rc = recursive_tor(S, kept2, nk2, L2, rem, i + 1);
-    free(kept2); free(M2); free(L2);
+    int* kept2 = 0;
+    cq* L2 = remove_mode(S, kept, nk, L, q, &kept2);
+    if (!L2) return -1;
+    add_term(S, L2, 2 * (nk - 1), removed_count + 1);
+    int rc = recursive_tor(S, kept2, nk - 1, L2, removed_count + 1, i + 1);
+    free(kept2); free(L2);
     if (rc) return rc;
   }
   return 0;
 }
 
-/* out[0..1] = Tor (dd), out[2] = sum |term|.  Returns 0, -1 (args) or -2 (not PD). */
-int tor_oracle_recursive(int n, const double* O, int ld, int layout, double* out) {
-  if (n < 0 || n > 24 || (n > 0 && !O) || !out || ld < 2 * n) return -1;
+/* Task u of a split at depth d (the paper distributes the first loop of
+ * Algorithm 2 over workers, Sec. 4; here the tasks are the 2^d patterns of
+ * removals among modes 0..d-1, which have equal subtrees).  The task reaches
+ * the node that removed exactly the modes of u (removals in increasing mode
+ * order, as the recursion makes them), adds its addend, then runs the
+ * recursion over the modes d..n-1 only.  Every subset of removed modes
+ * belongs to exactly one task. */
+typedef struct {
+  const rec_state* S0;
+  int d;
+  const cq* L0;
+  uint64_t next, ntasks;
+  pthread_mutex_t* lock;
+  neumaier* tor; neumaier* abs; int* rc;
+} alg2_pool;
+
+static int alg2_task(const rec_state* S0, int d, const cq* L0, uint64_t u, neumaier* tor, neumaier* abs) {
+  rec_state S = *S0;
+  S.tor.s = S.tor.c = 0; S.abs.s = S.abs.c = 0;
+  int n = S.n;
+  int* kept = (int*)malloc(sizeof(int) * (size_t)(n > 0 ? n : 1));
+  for (int j = 0; j < n; ++j) kept[j] = j;
+  int nk = n, removed = 0;
+  cq* L = (cq*)malloc(sizeof(cq) * (size_t)(n > 0 ? 4 * n * n : 1));
+  memcpy(L, L0, sizeof(cq) * (size_t)(4 * n * n));
+  int rc = 0;
+  for (int i = 0; i < d && !rc; ++i) {
+    if (!((u >> i) & 1ull)) continue;
+    int q = -1;
+    for (int t = 0; t < nk; ++t) if (kept[t] == i) { q = t; break; }
+    int* kept2 = 0;
+    cq* L2 = remove_mode(&S, kept, nk, L, q, &kept2);
+    if (!L2) { rc = -1; break; }
+    free(kept); free(L);
+    kept = kept2; L = L2; --nk; ++removed;
+  }
+  if (!rc) {
+    add_term(&S, L, 2 * nk, removed);
+    rc = recursive_tor(&S, kept, nk, L, removed, d);
+  }
+  free(kept); free(L);
+  *tor = S.tor; *abs = S.abs;
+  return rc;
+}
+
+static void* alg2_worker(void* arg) {
+  alg2_pool* P = (alg2_pool*)arg;
+  for (;;) {
+    pthread_mutex_lock(P->lock);
+    uint64_t u = P->next++;
+    pthread_mutex_unlock(P->lock);
+    if (u >= P->ntasks) break;
+    P->rc[u] = alg2_task(P->S0, P->d, P->L0, u, &P->tor[u], &P->abs[u]);
+  }
+  return 0;
+}
+
+/* Algorithm 2 of the paper in binary128, split into the 2^split tasks above and
+ * run on nthreads threads.  Each task sums its addends with Neumaier
+ * compensation; the task sums are then added in task order, so the value
+ * depends on split but not on nthreads.  split = 0 is the plain recursion from
+ * the root.  out[0..1] = Tor (dd), out[2] = sum |term|.  Returns 0, -1 (args)
+ * or -2 (not PD). */
+int tor_oracle_recursive_split(int n, const double* O, int ld, int layout, int split, int nthreads, double* out) {
+  if (n < 0 || n > 40 || (n > 0 && !O) || !out || ld < 2 * n || split < 0 || split > n || split > 20 ||
+      nthreads < 1)
+    return -1;
   problem P = {n, layout, ld, 0, O};
   rec_state S;
   S.n = n; S.N = 2 * n; S.mutate = 0;
   S.tor.s = S.tor.c = 0; S.abs.s = S.abs.c = 0;
   int N = 2 * n;
   S.A = (cq*)calloc((size_t)(N > 0 ? N * N : 1), sizeof(cq));
-  /* pairs order (a_1, a_1^dag, a_2, ...): P:Sec.2 */
+  /* pairs order (a_1, a_1^dag, a_2, ...): Sec. 2 */
   for (int a = 0; a < N; ++a)
     for (int b = 0; b < N; ++b) {
       cq o = O_at(&P, row_of(&P, a / 2, a & 1), row_of(&P, b / 2, b & 1));
@@ -307,21 +395,39 @@ int tor_oracle_recursive(int n, const double* O, int ld, int layout, double* out
       S.A[a * N + b] = v;
     }
   cq* L = (cq*)calloc((size_t)(N > 0 ? N * N : 1), sizeof(cq));
-  int rc = chol_rows(S.A, L, N, 0);
+  int rc = chol_rows(S.A, L, N, 0);   /* Algorithm 1 on I - A */
   if (rc) { free(S.A); free(L); return -2; }
-  quad det = 1;
-  for (int a = 0; a < N; ++a) det *= c_abs2(L[a * N + a]);
-  quad t0 = 1 / q_sqrt(det);
-  nm_add(&S.tor, t0);
-  nm_add(&S.abs, t0);
-  int* kept = (int*)malloc(sizeof(int) * (size_t)(n > 0 ? n : 1));
-  for (int j = 0; j < n; ++j) kept[j] = j;
-  rc = recursive_tor(&S, kept, n, L, 0, 0);
-  free(kept); free(L); free(S.A);
+  uint64_t ntasks = 1ull << split;
+  neumaier* tt = (neumaier*)calloc((size_t)ntasks, sizeof(neumaier));
+  neumaier* ta = (neumaier*)calloc((size_t)ntasks, sizeof(neumaier));
+  int* trc = (int*)calloc((size_t)ntasks, sizeof(int));
+  pthread_mutex_t lock = PTHREAD_MUTEX_INITIALIZER;
+  alg2_pool pool = {&S, split, L, 0, ntasks, &lock, tt, ta, trc};
+  if (nthreads > 256) nthreads = 256;
+  if ((uint64_t)nthreads > ntasks) nthreads = (int)ntasks;
+  if (nthreads == 1) {
+    alg2_worker(&pool);
+  } else {
+    pthread_t th[256];
+    for (int t = 0; t < nthreads; ++t) pthread_create(&th[t], 0, alg2_worker, &pool);
+    for (int t = 0; t < nthreads; ++t) pthread_join(th[t], 0);
+  }
+  neumaier acc = {0, 0}, abs_acc = {0, 0};
+  for (uint64_t u = 0; u < ntasks; ++u) {
+    if (trc[u]) rc = -2;
+    nm_add(&acc, tt[u].s); nm_add(&acc, tt[u].c);
+    nm_add(&abs_acc, ta[u].s); nm_add(&abs_acc, ta[u].c);
+  }
+  free(tt); free(ta); free(trc); free(L); free(S.A);
   if (rc) return -2;
-  quad_to_dd(S.tor.s + S.tor.c, &out[0], &out[1]);
-  out[2] = (double)(S.abs.s + S.abs.c);
+  quad_to_dd(acc.s + acc.c, &out[0], &out[1]);
+  out[2] = (double)(abs_acc.s + abs_acc.c);
   return 0;
+}
+
+/* The plain recursion from the root on one thread (split 0). */
+int tor_oracle_recursive(int n, const double* O, int ld, int layout, double* out) {
+  return tor_oracle_recursive_split(n, O, ld, layout, 0, 1, out);
 }
 
 /* Quad determinant of I - O_Z for one mask (for tests of the determinant step). */

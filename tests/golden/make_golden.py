@@ -2,6 +2,11 @@
 seeded input generator that produces the matrices, which it stores verbatim so
 that every machine reads the same complex128 entries).
 
+Up to n = 22 the full sum is the brute force of Eq. (tor); beyond that it is
+the oracle's binary128 Algorithm 2 (Sec. 2), split into 2^10 tasks over the
+host cores (the brute force would take hours to days), with prefix units from
+the brute force stored beside it.
+
 Usage: python tests/golden/make_golden.py [fixture names]  (default: all)
 """
 import json
@@ -17,10 +22,17 @@ import oracle  # noqa: E402
 from paper_2109_04528_gb300 import inputs  # noqa: E402
 
 
-def write(name, inst, note, units=()):
-    r = oracle.tor_brute(inst.O)
+def write(name, inst, note, units=(), method="brute"):
+    if method == "brute":
+        r = oracle.tor_brute(inst.O)
+        cite = "Eq. (tor), Sec. 1 (definition); values from the binary128 brute-force oracle"
+    else:
+        r = oracle.tor_recursive(inst.O, split=10, threads=None)
+        cite = ("Eq. (tor), Sec. 1; full sum from the oracle's binary128 Algorithm 2 (Sec. 2) split into "
+                "2^10 tasks, prefix units from the binary128 brute force")
     rec = {
-        "citation": "Eq. (tor), Sec. 1 (definition); values from the binary128 brute-force oracle",
+        "citation": cite,
+        "method": "brute force" if method == "brute" else "Algorithm 2, binary128, split 10",
         "note": note,
         "n": inst.n, "layout": "block", "kind": inst.kind, "seed": inst.seed,
         "O_re": np.real(inst.O).tolist(), "O_im": np.imag(inst.O).tolist(),
@@ -49,11 +61,17 @@ FIXTURES = {
     "lossy_n22.json": (lambda: inputs.config_single(22),
                        "n=22 lossy squeezed state of the benchmark's kind (r~U[0.3,0.8], eta_j~U[0.3,0.7]); "
                        "full brute force over 2^22 subsets", (8, [0, 37, 255])),
+    "lossy_n24.json": (lambda: inputs.config_single(24),
+                       "n=24 lossy squeezed state of the single-matrix benchmark (r~U[0.3,0.8], eta_j~U[0.3,0.7]); "
+                       "full sum by Algorithm 2 in binary128", (12, [0, 1365, 4095]), "alg2"),
+    "lossy_n30.json": (lambda: inputs.config_single(30),
+                       "n=30 lossy squeezed state of the large single-matrix benchmark (r~U[0.3,0.8], "
+                       "eta_j~U[0.3,0.7]); full sum by Algorithm 2 in binary128", (18, [0, 87381, 262143]), "alg2"),
 }
 
 
 if __name__ == "__main__":
     # python tests/golden/make_golden.py [NAME ...]   (default: every fixture)
     for name in sys.argv[1:] or FIXTURES:
-        make, note, units = FIXTURES[name]
-        write(name, make(), note, units)
+        make, note, units, *method = FIXTURES[name]
+        write(name, make(), note, units, *method)

@@ -199,9 +199,10 @@ def test_graph_replay_and_served_equal_plain(xctx):
         assert st == 0 and (r.hi, r.lo, r.abs_sum) == (p.hi, p.lo, p.abs_sum)
 
 
-@pytest.mark.parametrize("name", ["lossy_n20.json", "lossy_n22.json"])
-def test_golden_full_brute_force(xctx, name):
-    # n = 20 and 22 against the oracle's stored full brute force, at the double-double bound
+@pytest.mark.parametrize("name", ["lossy_n20.json", "lossy_n22.json", "lossy_n24.json"])
+def test_golden_full_sum(xctx, name):
+    # n = 20, 22 (full brute force) and 24 (binary128 Algorithm 2) against the oracle's
+    # stored sums, at the double-double bound
     import json
     import os
     with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", name)) as f:

@@ -107,14 +107,39 @@ def test_det_matches_numpy(oracle_mod):
         assert abs(got.imag) <= 1e-13 * abs(got)
 
 
-@pytest.mark.parametrize("n", [1, 2, 3, 5, 8])
+@pytest.mark.parametrize("n", [1, 2, 3, 5, 8, 9, 10, 11, 12])
 def test_brute_equals_algorithm2(oracle_mod, n):
+    # the paper's Algorithm 2 (plain recursion, and split into 2^d tasks as in Sec. 4)
+    # against the definition written out, on physical and on general Hermitian inputs
     for inst in (inputs.lossy_squeezed(n, 300 + n, (0.3, 0.8), 0.5),
                  inputs.random_hermitian_contraction(n, 400 + n, 0.8)):
         a = oracle_mod.tor_brute(inst.O)
-        b = oracle_mod.tor_recursive(inst.O)
-        assert abs((a.hi - b.hi) + (a.lo - b.lo)) <= 1e-28 * a.abs_sum
-        assert abs(a.abs_sum - b.abs_sum) <= 1e-14 * a.abs_sum
+        for split in (0, min(n, 3), n):
+            b = oracle_mod.tor_recursive(inst.O, split=split, threads=4)
+            assert abs((a.hi - b.hi) + (a.lo - b.lo)) <= 1e-28 * a.abs_sum, split
+            assert abs(a.abs_sum - b.abs_sum) <= 1e-14 * a.abs_sum
+
+
+def test_algorithm2_split_is_independent_of_threads(oracle_mod):
+    inst = inputs.lossy_squeezed(11, 17, (0.3, 0.8), (0.3, 0.7))
+    got = {(r.hi, r.lo, r.abs_sum) for r in (oracle_mod.tor_recursive(inst.O, split=6, threads=t)
+                                             for t in (1, 3, 8))}
+    assert len(got) == 1
+
+
+def test_algorithm2_reproduces_the_n20_brute_force(oracle_mod):
+    # the stored n = 20 fixture is the full brute force; the split Algorithm 2 (the
+    # method the n >= 24 fixtures use) must reach it to binary128 rounding
+    g, O = load_golden("lossy_n20.json")
+    r = oracle_mod.tor_recursive(O, split=8, threads=None)
+    assert abs((r.hi - g["tor_hi"]) + (r.lo - g["tor_lo"])) <= 1e-30 * g["abs_sum"]
+    assert abs(r.abs_sum - g["abs_sum"]) <= 1e-14 * g["abs_sum"]
+
+
+def test_algorithm2_rejects_non_pd(oracle_mod):
+    O = 2.0 * np.eye(6, dtype=np.complex128)  # I - O = -I
+    with pytest.raises(ValueError):
+        oracle_mod.tor_recursive(O, split=2, threads=2)
 
 
 def test_invariances(oracle_mod):
@@ -163,10 +188,10 @@ def test_golden_fixture_reproduces(oracle_mod, name):
     assert r.hi == g["tor_hi"] and abs(r.lo - g["tor_lo"]) <= 1e-30 * g["abs_sum"]
 
 
-@pytest.mark.parametrize("name", ["lossy_n20.json", "lossy_n22.json"])
+@pytest.mark.parametrize("name", ["lossy_n20.json", "lossy_n22.json", "lossy_n24.json"])
 def test_large_golden_units_reproduce(oracle_mod, name):
-    # the full brute force over 2^20 / 2^22 subsets takes minutes; its stored prefix
-    # units (2^12 / 2^14 subsets each) are recomputed here
+    # the full sums over 2^20 .. 2^24 subsets take minutes; the stored prefix units
+    # (2^12 .. 2^14 subsets each, brute force) are recomputed here
     g, O = load_golden(name)
     assert O.shape == (2 * g["n"], 2 * g["n"]) and g["abs_sum"] > 0
     for unit in g["units"]:
