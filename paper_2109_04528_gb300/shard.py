@@ -66,20 +66,45 @@ def partition_batch(ns, world: int):
     return [sorted(p) for p in parts]
 
 
+def _gather_checked(work, group=None):
+    """Runs work() on this rank and all-gathers (status, message, value) from every
+    rank.  A rank whose work fails (a TorError such as ETIMEOUT or ENOTPD, or any
+    other exception) still joins the collective, so no rank is left blocked in it;
+    afterwards every rank raises the first failure, by rank order.  Returns the
+    gathered values in rank order."""
+    import torch.distributed as dist
+
+    from .binding import TorError
+    world = dist.get_world_size(group)
+    try:
+        item = (0, "", work())
+    except TorError as e:
+        item = (int(e.status), str(e), None)
+    except Exception as e:  # reported to every rank below, then raised there
+        item = (-1, f"{type(e).__name__}: {e}", None)
+    got = [None] * world
+    dist.all_gather_object(got, item, group=group)
+    for r, (status, msg, _) in enumerate(got):
+        if status:
+            raise TorError(status if status > 0 else 1, f"rank {r} failed: {msg}")
+    return [v for _, _, v in got]
+
+
 def distributed_batch(evaluate, ns, group=None):
     """Evaluates a batch split by partition_batch: `evaluate(indices)` returns
     this rank's (hi, lo, abs) per index; one all-gather returns every rank the
     whole batch's results in batch order.  A matrix's result does not depend
-    on the batch it is evaluated in, so this equals one rank's tor_eval_batch."""
+    on the batch it is evaluated in, so this equals one rank's tor_eval_batch.
+    If any rank's evaluation fails, every rank raises after the gather."""
     import torch.distributed as dist
     world, rank = dist.get_world_size(group), dist.get_rank(group)
     mine = partition_batch(ns, world)[rank]
-    got = evaluate(mine)
-    rows = [(i, tuple(float(v) for v in r)) for i, r in zip(mine, got)]
-    allr = [None] * world
-    dist.all_gather_object(allr, rows, group=group)
+
+    def work():
+        got = evaluate(mine)
+        return [(i, tuple(float(v) for v in r)) for i, r in zip(mine, got)]
     out = [None] * len(ns)
-    for rows_r in allr:
+    for rows_r in _gather_checked(work, group):
         for i, r in rows_r:
             out[i] = r
     return out
@@ -87,10 +112,13 @@ def distributed_batch(evaluate, ns, group=None):
 
 def gather_merge(partial, group=None):
     """All-gather each rank's (hi, lo, abs) (torch.distributed) and merge in rank order."""
-    import torch.distributed as dist
-    world = dist.get_world_size(group)
-    got = [None] * world
-    dist.all_gather_object(got, tuple(float(v) for v in partial), group=group)
+    return distributed_partial(lambda: partial, group)
+
+
+def distributed_partial(evaluate, group=None):
+    """`evaluate()` gives this rank's (hi, lo, abs); all-gathers them and merges in
+    rank order.  If any rank's evaluation fails, every rank raises after the gather."""
+    got = _gather_checked(lambda: tuple(float(v) for v in evaluate()), group)
     return tree_merge(got)
 
 
@@ -101,6 +129,9 @@ def distributed_tor_batch(ctx, mats, group=None):
 
     def evaluate(idx):
         res = binding.tor_eval_batch(ctx, [mats[i] for i in idx]) if idx else []
+        for r in res:
+            if r.status != binding.TOR_OK:
+                raise binding.TorError(r.status, "tor_eval_batch")
         return [(r.hi, r.lo, r.abs_sum) for r in res]
     return distributed_batch(evaluate, ns, group)
 
@@ -113,5 +144,10 @@ def distributed_tor(ctx, O, group=None):
     from . import binding
     n = O.shape[0] // 2
     lo, count = shard_range(binding.tor_plan_leaves(ctx, n), dist.get_world_size(group), dist.get_rank(group))
-    r = binding.tor_eval_range(ctx, O, lo, count)
-    return gather_merge((r.hi, r.lo, r.abs_sum), group)
+
+    def evaluate():
+        r = binding.tor_eval_range(ctx, O, lo, count)
+        if r.status != binding.TOR_OK:
+            raise binding.TorError(r.status, "tor_eval_range")
+        return (r.hi, r.lo, r.abs_sum)
+    return distributed_partial(evaluate, group)

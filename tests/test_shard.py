@@ -164,3 +164,55 @@ def test_bench_rank_helpers_gloo(tmp_path):
     for rank in range(2):
         w, r, local, got = np.load(tmp_path / f"m{rank}.npy")
         assert (w, r, local, got) == (2, rank, rank, 11.0)
+
+
+def _failing_rank_main(rank, world, port, out_dir):
+    import datetime
+
+    import torch.distributed as dist
+
+    from paper_2109_04528_gb300 import binding
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world, timeout=datetime.timedelta(seconds=60))
+    seen = []
+
+    def evaluate_batch(idx):  # rank 1's evaluation fails on the host, before the collective
+        if rank == 1:
+            raise binding.TorError(binding.TOR_ETIMEOUT, "planted")
+        return [(1.0, 0.0, 1.0) for _ in idx]
+
+    def evaluate_partial():
+        if rank == 0:
+            raise binding.TorError(binding.TOR_ENOTPD, "planted")
+        return (1.0, 0.0, 1.0)
+    for call in (lambda: shard.distributed_batch(evaluate_batch, [3, 4, 5, 6]),
+                 lambda: shard.distributed_partial(evaluate_partial)):
+        try:
+            call()
+            seen.append(0)
+        except binding.TorError as e:
+            seen.append(e.status)
+    # the ranks are still in step: a plain merge afterwards works on both
+    merged = shard.gather_merge((float(rank), 0.0, 1.0))
+    np.save(os.path.join(out_dir, f"f{rank}.npy"), np.array(seen + list(merged)))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_failure_on_one_rank_raises_on_every_rank(tmp_path):
+    # a rank whose evaluation fails still joins the gather, and then every rank raises
+    # the failure (no rank is left waiting in the collective)
+    import socket
+
+    import torch.multiprocessing as mp
+
+    from paper_2109_04528_gb300 import binding
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    port = s.getsockname()[1]
+    s.close()
+    mp.start_processes(_failing_rank_main, args=(2, port, str(tmp_path)), nprocs=2, join=True, start_method="spawn")
+    for rank in range(2):
+        got = np.load(tmp_path / f"f{rank}.npy")
+        assert tuple(got[:2]) == (binding.TOR_ETIMEOUT, binding.TOR_ENOTPD)
+        assert tuple(got[2:]) == (1.0, 0.0, 2.0)
