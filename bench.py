@@ -3,9 +3,15 @@
 One step = one tor_eval_batch over a workload's matrices (intake, units,
 reduce: every step of the hot path).  Workloads (seeded synthetic inputs):
 
-  single_n16_20_24 (default)  lossy squeezed states n = 16, 20, 24
-                              (r ~ U[0.3,0.8], per-mode eta ~ U[0.3,0.7], Haar U)
-                              plus a product state at n = 24
+  large_n30_34 (default)      lossy squeezed states n = 30 and 34 (r ~ U[0.3,0.8],
+                              per-mode eta ~ U[0.3,0.7], Haar U); beside the timed
+                              steps, one evaluation each of a lossy n = 38 state and
+                              an n = 38 product state, the double-double factor on
+                              the step's matrices, the error of every result against
+                              the best available higher-precision reference, the
+                              4096-matrix batch against the plain per-matrix path,
+                              and the serving loop's p50/p99 against the plain path
+  single_n16_20_24            lossy squeezed n = 16, 20, 24 plus a product state at n = 24
   single_n30 / single_n34 / single_n38   one lossy squeezed state of that size
   batch4096                   4096 click patterns k ~ U{4..24} of one 100-mode state
   serve                       chain-rule marginal requests on a 144-mode state (p50/p99)
@@ -41,9 +47,15 @@ FP64_PER_SM_CLK = 2  # GB300: FP64 thread instructions (add, mul, FMA) issued pe
 MAX_SM_MHZ = 2070.0  # GB300 maximum SM clock, when the sampled clocks do not give it
 
 
+DEFAULT_WORKLOAD = "large_n30_34"
+
+
 def workload(name: str, rank: int = 0):
     """(list of O matrices, description)."""
     off = 7919 * rank
+    if name == "large_n30_34":
+        mats = [inputs.config_single(n, seed=inputs.SEED_BASE + 1000 + n + off).O for n in (30, 34)]
+        return mats, "lossy squeezed n=30,34 (r~U[0.3,0.8], eta_j~U[0.3,0.7], Haar U)"
     if name == "single_n16_20_24":
         mats = [inputs.config_single(n, seed=inputs.SEED_BASE + 1000 + n + off).O for n in (16, 20, 24)]
         mats.append(inputs.product_state(24, inputs.SEED_BASE + 2024 + off).O)
@@ -244,6 +256,198 @@ def cpu_baseline(mats, budget_s: float):
                       f"binary128 LU per subset, {dt:.1f} s"}
 
 
+GOLDEN_DIR = os.path.join(ROOT, "tests", "golden")
+
+
+def golden_for(O):
+    """The stored binary128 oracle sum of exactly this matrix, if the golden
+    fixtures hold one (written by the oracle alone): dict(hi, lo, abs_sum,
+    method) or None."""
+    n = O.shape[0] // 2
+    try:
+        with open(os.path.join(GOLDEN_DIR, f"lossy_n{n}.json")) as f:
+            g = json.load(f)
+    except (OSError, ValueError):
+        return None
+    G = np.array(g["O_re"]) + 1j * np.array(g["O_im"])
+    if G.shape != O.shape or not np.array_equal(G, O):
+        return None
+    return {"hi": g["tor_hi"], "lo": g["tor_lo"], "abs_sum": g["abs_sum"],
+            "method": g.get("method", "brute force")}
+
+
+def product_closed_form(inst):
+    """Tor and sum|term| of a product state in closed form (Eq. tor factorises
+    over modes): prod_j (x_j - 1) and prod_j (x_j + 1), x_j = sqrt(det Sigma_j)
+    of mode j's lossy squeezed vacuum (N = eta sinh^2 r, M = eta sinh r cosh r);
+    x - 1 is formed as (2N + N^2 - M^2) / (x + 1), without cancellation."""
+    import math
+    sh, ch = np.sinh(inst.r), np.cosh(inst.r)
+    N = inst.eta * sh * sh
+    M = inst.eta * sh * ch
+    x = np.sqrt((1 + N) ** 2 - M ** 2)
+    xm1 = (2 * N + N * N - M * M) / (x + 1)
+    return math.prod(float(v) for v in xm1), math.prod(float(v) for v in x + 1)
+
+
+def error_entry(r, ref_hi: float, ref_lo: float):
+    """|Tor - ref| of one result, against sum|term| and against |ref|."""
+    d = abs((r.hi - ref_hi) + (r.lo - ref_lo))
+    ref = ref_hi + ref_lo
+    return {"abs_err": d, "err_over_abs_sum": d / r.abs_sum if r.abs_sum else None,
+            "rel_err": d / abs(ref) if ref else None, "within_err_est": bool(d <= r.err_est)}
+
+
+def result_record(name: str, n: int, r64, rx=None, ref=None):
+    """One matrix's results and their errors.  ref = dict(hi, lo, name[, bound]):
+    the binary128 oracle, a closed form, or the double-double GPU path (whose own
+    a-priori bound is `bound`)."""
+    rec = {"matrix": name, "n": n, "abs_sum": r64.abs_sum, "path": r64.path,
+           "fp64": {"tor": r64.tor, "err_est": r64.err_est}}
+    if rx is not None:
+        rec["extended"] = {"tor": rx.tor, "err_est": rx.err_est}
+    if ref is None:
+        rec["ref"] = None
+        return rec
+    tref = ref["hi"] + ref["lo"]
+    rec["ref"] = ref["name"]
+    rec["tor_ref"] = tref
+    if ref.get("bound") is not None:
+        rec["ref_err_bound"] = ref["bound"]
+    rec["kappa"] = r64.abs_sum / abs(tref) if tref else None
+    rec["fp64"].update(error_entry(r64, ref["hi"], ref["lo"]))
+    if rx is not None and ref["name"] != "double-double GPU path":
+        rec["extended"].update(error_entry(rx, ref["hi"], ref["lo"]))
+    return rec
+
+
+def large_extras(local, stream, ctx_dev, mats, dmats, res64, ns):
+    """Beside the timed steps of the n = 30/34 workload: the double-double factor
+    on each step matrix, one evaluation each of a lossy and a product state at
+    n = 38, sampled oracle units at n = 34, and the error of every result."""
+    import torch
+
+    import oracle
+    from paper_2109_04528_gb300 import binding
+    device = torch.device("cuda", local)
+    out = {"results": [], "extended": [], "n38": []}
+    # double-double factor (TOR_EXTENDED) on the step's matrices, one timed evaluation each
+    rxs = []
+    with binding.Context(device=local, stream=stream.cuda_stream,
+                         flags=binding.TOR_IN_DEVICE | binding.TOR_EXTENDED) as cx:
+        binding.tor_eval(cx, torch.from_numpy(inputs.config_n8().O).to(device))  # module load, allocation
+        for d, n in zip(dmats, ns):
+            rx = binding.tor_eval(cx, d)
+            ms = cx.last_times()["total_ms"]
+            rxs.append(rx)
+            out["extended"].append({"n": n, "ms": ms, "terms_per_s": 2.0 ** n / (ms * 1e-3), "path": rx.path,
+                                    "status": rx.status})
+    for i, (O, n) in enumerate(zip(mats, ns)):
+        g = golden_for(O)
+        if g is not None:
+            ref = {"hi": g["hi"], "lo": g["lo"], "name": f"binary128 oracle ({g['method']}), stored"}
+        else:
+            ref = {"hi": rxs[i].hi, "lo": rxs[i].lo, "name": "double-double GPU path", "bound": rxs[i].err_est}
+        out["results"].append(result_record(f"lossy n={n} (timed step)", n, res64[i], rxs[i], ref))
+    # n = 38: a lossy squeezed state and a product state with a closed form, one evaluation each
+    lossy38 = inputs.config_single(38, seed=inputs.SEED_BASE + 1038)
+    prod38 = inputs.product_state(38, inputs.SEED_BASE + 2038)
+    for name, inst in (("lossy n=38", lossy38), ("product state n=38", prod38)):
+        d = torch.from_numpy(inst.O).to(device)
+        r = binding.tor_eval(ctx_dev, d)
+        ms = ctx_dev.last_times()["total_ms"]
+        out["n38"].append({"matrix": name, "ms": ms, "terms_per_s": 2.0 ** 38 / (ms * 1e-3), "status": r.status,
+                           "path": r.path, "prefix_depth": ctx_dev.plan_prefix_depth(38)})
+        ref = None
+        if inst.kind == "product_state":
+            t, a = product_closed_form(inst)
+            ref = {"hi": t, "lo": 0.0, "name": "closed form prod_j (x_j - 1)"}
+            out["n38"][-1]["abs_sum_closed_form"] = a
+            out["n38"][-1]["abs_sum_rel_err"] = abs(r.abs_sum - a) / a
+        rec = result_record(name, 38, r, None, ref)
+        if ref is None:
+            rec["note"] = ("no higher-precision reference within the bench's budget (the double-double path "
+                           "would take ~150 s, the binary128 oracle years)")
+        out["results"].append(rec)
+        del d
+    # sampled prefix units of the n = 34 step matrix against the binary128 oracle (same launch plan)
+    j = ns.index(34) if 34 in ns else len(ns) - 1
+    res, p, parts = binding.tor_eval_units(ctx_dev, dmats[j])
+    oracle.build()
+    checks = []
+    t0 = time.perf_counter()
+    for u in (0, 0b1011, 0b1010010001):
+        q = oracle.tor_unit(mats[j], p, u)
+        d = abs((parts[u][0] - q.hi) + (parts[u][1] - q.lo))
+        checks.append({"u": u, "abs_err": d, "err_over_abs_sum": d / q.abs_sum, "pass_1e-10": bool(d <= 1e-10 * q.abs_sum)})
+    out["units_parity"] = {"n": ns[j], "p": p, "subsets_per_unit": 1 << (ns[j] - p), "units": checks,
+                           "oracle_s": time.perf_counter() - t0,
+                           "what": "GPU unit partials (tor_eval_units, the timed launch plan) against the "
+                                   "binary128 brute force of the same units"}
+    return out
+
+
+def batch_compare(local, stream, steps: int):
+    """The 4096-matrix batch (k ~ U{4..24} click patterns of a 100-mode state):
+    one batched launch, its CUDA-graph replay, and the plain path (one tor_eval
+    per matrix, looped in C by tor_eval_seq), all device-resident."""
+    import torch
+
+    from paper_2109_04528_gb300 import binding
+    device = torch.device("cuda", local)
+    mats, desc = workload("batch4096")
+    dmats = [torch.from_numpy(m).to(device) for m in mats]
+    terms = float(sum(2.0 ** (m.shape[0] // 2) for m in mats))
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=device)
+
+    def run(ctx, k):
+        ms = []
+        for _ in range(k):
+            with torch.cuda.stream(stream):
+                flush.fill_(1.0)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            res = binding.tor_eval_batch(ctx, dmats)
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+            if any(r.status != 0 for r in res):
+                raise SystemExit("batch evaluation failed")
+        return ms, res
+
+    out = {"workload": "batch4096", "desc": desc, "matrices": len(mats), "terms_per_batch": terms}
+    with binding.Context(device=local, stream=stream.cuda_stream, flags=binding.TOR_IN_DEVICE) as c:
+        run(c, 2)
+        ms, res_b = run(c, steps)
+        out["batched"] = {"ms_per_batch": statistics.median(ms), "value": terms / (statistics.median(ms) * 1e-3),
+                          "unit": "subset terms/s", "steps": steps, "tor_per_s": len(mats) / (statistics.median(ms) * 1e-3)}
+    with binding.Context(device=local, stream=stream.cuda_stream,
+                         flags=binding.TOR_IN_DEVICE | binding.TOR_GRAPHS) as c:
+        run(c, 2)
+        ms, res_g = run(c, steps)
+        out["graph_replay"] = {"ms_per_batch": statistics.median(ms), "value": terms / (statistics.median(ms) * 1e-3),
+                               "unit": "subset terms/s", "steps": steps}
+    with binding.Context(device=local, stream=stream.cuda_stream, flags=binding.TOR_IN_DEVICE) as c:
+        binding.tor_eval_seq(c, dmats[:64])
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        res_p, lat = binding.tor_eval_seq(c, dmats)
+        plain_s = time.perf_counter() - t0
+    lat = np.sort(lat)
+    out["plain_per_matrix"] = {"s_per_batch": plain_s, "value": terms / plain_s, "unit": "subset terms/s",
+                               "tor_per_s": len(mats) / plain_s, "per_matrix_ms_p50": float(lat[len(lat) // 2]),
+                               "per_matrix_ms_p99": float(lat[min(len(lat) - 1, int(0.99 * len(lat)))]),
+                               "what": "tor_eval_seq: one tor_eval per matrix (descriptors H2D, 3 kernels, results "
+                                       "D2H, one sync) looped in C, host wall time"}
+    same = all((a.hi, a.lo, a.abs_sum) == (b.hi, b.lo, b.abs_sum) == (g.hi, g.lo, g.abs_sum)
+               for a, b, g in zip(res_b, res_p, res_g))
+    out["bitwise_equal_batched_graph_plain"] = bool(same)
+    out["batched_over_plain"] = out["batched"]["value"] / out["plain_per_matrix"]["value"]
+    out["graph_over_plain"] = out["graph_replay"]["value"] / out["plain_per_matrix"]["value"]
+    return out
+
+
 def launches_per_step(ctx, ns) -> int:
     """Kernels one tor_eval_batch launches: k_intake, k_units, k_reduce, and
     k_reduce_chunks when a matrix has more than 256 reduction leaves (2^(p-5)
@@ -334,8 +538,8 @@ def serve_requests(rate: float, window: float, seed: int, N: int = 144):
 def replay(ctx, sess, reqs, mode: str, drain_s: float):
     """Submits reqs at their scheduled times; returns latencies (s) of the
     requests completed by window end + drain_s, and counts.  mode 'served' =
-    tor_submit_marginal + polling; 'plain' = one blocking tor_eval_marginal at a
-    time in arrival order."""
+    tor_submit_marginal, completions collected as they happen (tor_poll_any);
+    'plain' = one blocking tor_eval_marginal at a time in arrival order."""
     from paper_2109_04528_gb300 import binding
     window = reqs[-1][0] if reqs else 0.0
     deadline = window + drain_s
@@ -352,63 +556,60 @@ def replay(ctx, sess, reqs, mode: str, drain_s: float):
             lat.append(time.perf_counter() - t0 - ta)
             terms_done += 2.0 ** len(S)
         return lat, len(lat), terms_done
-    pending = {}
+    tickets, meta = [], []
     i = 0
     while True:
         now = time.perf_counter() - t0
         while i < len(reqs) and reqs[i][0] <= now:
             ta, j, S = reqs[i]
-            pending[binding.tor_submit_marginal(ctx, sess, j, S)] = (ta, len(S))
+            tickets.append(binding.tor_submit_marginal(ctx, sess, j, S))
+            meta.append((ta, len(S)))
             i += 1
-        for t in list(pending):
-            st, r = binding.tor_poll(ctx, t, 0.0)
-            if st != binding.TOR_EAGAIN:
-                ta, k = pending.pop(t)
-                if st == 0:
-                    lat.append(time.perf_counter() - t0 - ta)
-                    terms_done += 2.0 ** k
-        if (i >= len(reqs) and not pending) or now > deadline:
+        if (i >= len(reqs) and not tickets) or now > deadline:
             break
-        time.sleep(0.0002)
+        wait = (reqs[i][0] - now) if i < len(reqs) else deadline - now
+        wait = max(0.0, min(wait, 0.05))
+        if not tickets:
+            time.sleep(wait)
+            continue
+        st, k, r = binding.tor_poll_any(ctx, tickets, wait)
+        if k < 0:
+            continue
+        done_at = time.perf_counter() - t0
+        ta, kk = meta[k]
+        tickets.pop(k)
+        meta.pop(k)
+        if st == 0:
+            lat.append(done_at - ta)
+            terms_done += 2.0 ** kk
     return lat, len(lat), terms_done
 
 
-def run_serve(args, world, rank, local):
-    """Serving benchmark on a 144-mode lossy squeezed state (r ~ U[0.5,1.2], eta = 0.3)."""
-    if rank != 0:
-        return 0
-    from paper_2109_04528_gb300 import binding, build
-    build.build()
+def _pct(x, q):
+    if not x:
+        return None
+    x = sorted(x)
+    return x[min(len(x) - 1, int(q * len(x)))]
+
+
+def serve_runs(local, loads, seed: int):
+    """Replays seeded Poisson streams of chain-rule marginal requests on the
+    144-mode state (r ~ U[0.5,1.2], eta = 0.3) through the serving loop and
+    through the plain blocking path.  loads: list of (name, rate or callable of
+    the runs so far, window_s, modes, drain_s)."""
+    from paper_2109_04528_gb300 import binding
     inst = inputs.lossy_squeezed(144, inputs.SEED_BASE + 5, (0.5, 1.2), 0.3)
-
-    def pct(x, q):
-        if not x:
-            return None
-        x = sorted(x)
-        return x[min(len(x) - 1, int(q * len(x)))]
-
-    out = {"metric": "requests/s", "unit": "requests/s", "n_gpus": 1, "higher_is_better": True,
-           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": "serve", "state": "144-mode lossy squeezed, r~U[0.5,1.2], eta=0.3",
-                      "request": "k~U{2..30}, j~U{max(k,1)..144}, S a k-subset of [j] containing j-1",
-                      "latency": "completion minus scheduled arrival"}}
     runs = {}
-    for name, rate, window in (("overload", args.serve_rate, args.serve_window),
-                               ("sustained", args.serve_sustain_rate, args.serve_sustain_window),
-                               ("high", args.serve_high_rate, args.serve_high_window)):
-        if name == "high" and rate <= 0:
-            # ~80 % of the measured capacity.  Under overload small requests pass large ones and the
-            # backlog is dropped, so its completion rate overstates capacity; capacity is the subset
-            # terms/s the GPU sustained there over the mean request, E[2^k] = (2^31 - 4) / 29
-            mean_terms = (2.0 ** 31 - 4.0) / 29.0
-            rate = round(0.8 * runs["overload_served"]["terms_per_s"] / mean_terms, 1)
-        reqs = serve_requests(rate, window, inputs.SEED_BASE + 17)
-        for mode in ("served", "plain"):
+    for name, rate, window, modes, drain in loads:
+        if callable(rate):
+            rate = rate(runs)
+        reqs = serve_requests(rate, window, seed)
+        for mode in modes:
             ctx = binding.Context(device=local)
             sess = binding.Session(ctx, inst.sigma)
             binding.tor_eval_marginal(ctx, sess, 10, [0, 3, 9])  # warm-up
             t0 = time.perf_counter()
-            lat, done, terms = replay(ctx, sess, reqs, mode, drain_s=2.0 if name == "overload" else 30.0)
+            lat, done, terms = replay(ctx, sess, reqs, mode, drain_s=drain)
             el = time.perf_counter() - t0
             stats = ctx.serving_stats()
             ctx.close()  # drops the backlog, stops running jobs, waits for the GPU
@@ -416,8 +617,36 @@ def run_serve(args, world, rank, local):
             runs[f"{name}_{mode}"] = {
                 "offered_rate": rate, "window_s": window, "offered": len(reqs), "completed": done,
                 "requests_per_s": done / el, "terms_per_s": terms / el,
-                "p50_ms": None if not lat else 1e3 * pct(lat, 0.5), "p99_ms": None if not lat else 1e3 * pct(lat, 0.99),
+                "p50_ms": None if not lat else 1e3 * _pct(lat, 0.5), "p99_ms": None if not lat else 1e3 * _pct(lat, 0.99),
                 "backlog_at_end": len(reqs) - done, "batches": stats["batches"]}
+    return runs
+
+
+def capacity_rate(runs, frac: float = 0.8):
+    """Requests/s at `frac` of the capacity measured under overload.  Under
+    overload small requests pass large ones and the backlog is dropped, so the
+    completion rate overstates capacity; capacity is the subset terms/s the GPU
+    sustained there over the mean request, E[2^k] = (2^31 - 4) / 29."""
+    mean_terms = (2.0 ** 31 - 4.0) / 29.0
+    return round(frac * runs["overload_served"]["terms_per_s"] / mean_terms, 1)
+
+
+def run_serve(args, world, rank, local):
+    """Serving benchmark on a 144-mode lossy squeezed state (r ~ U[0.5,1.2], eta = 0.3)."""
+    if rank != 0:
+        return 0
+    from paper_2109_04528_gb300 import build
+    build.build()
+    high = args.serve_high_rate if args.serve_high_rate > 0 else capacity_rate
+    runs = serve_runs(local, [("overload", args.serve_rate, args.serve_window, ("served", "plain"), 2.0),
+                              ("sustained", args.serve_sustain_rate, args.serve_sustain_window, ("served", "plain"), 30.0),
+                              ("high", high, args.serve_high_window, ("served", "plain"), 30.0)],
+                      inputs.SEED_BASE + 17)
+    out = {"metric": "requests/s", "unit": "requests/s", "n_gpus": 1, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": "serve", "state": "144-mode lossy squeezed, r~U[0.5,1.2], eta=0.3",
+                      "request": "k~U{2..30}, j~U{max(k,1)..144}, S a k-subset of [j] containing j-1",
+                      "latency": "completion minus scheduled arrival"}}
     out["runs"] = runs
     s = runs["high_served"]
     out["value"] = s["requests_per_s"]
@@ -426,6 +655,24 @@ def run_serve(args, world, rank, local):
     out["config"]["high_rate"] = runs["high_served"]["offered_rate"]
     print(json.dumps(out), flush=True)
     return 0
+
+
+def serve_summary(local, window: float, light_rate: float):
+    """The serving loop against the plain path at ~80 % of capacity and at a
+    light load, for the headline line."""
+    runs = serve_runs(local, [("overload", 2000.0, 2.0, ("served",), 2.0),
+                              ("high", capacity_rate, window, ("served", "plain"), 30.0),
+                              ("light", light_rate, window, ("served", "plain"), 30.0)],
+                      inputs.SEED_BASE + 17)
+    out = {"state": "144-mode lossy squeezed, r~U[0.5,1.2], eta=0.3",
+           "request": "chain-rule marginal Tor(O^(j)_S), k=|S|~U{2..30}, Poisson arrivals",
+           "latency": "completion minus scheduled arrival", "runs": runs}
+    for load in ("high", "light"):
+        a, b = runs[f"{load}_served"], runs[f"{load}_plain"]
+        out[load] = {"rate": a["offered_rate"], "served_p50_ms": a["p50_ms"], "served_p99_ms": a["p99_ms"],
+                     "plain_p50_ms": b["p50_ms"], "plain_p99_ms": b["p99_ms"],
+                     "served_requests_per_s": a["requests_per_s"], "plain_requests_per_s": b["requests_per_s"]}
+    return out
 
 
 def run_sample(args, world, rank, local):
@@ -522,7 +769,14 @@ def main():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
-    ap.add_argument("--workload", default="single_n16_20_24")
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
+    ap.add_argument("--weak", action="store_true",
+                    help="several ranks: every rank evaluates its own copy of large_n30_34 (default there: the "
+                         "ranks split each matrix's leaves, strong scaling)")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="large_n30_34: skip the nested results (n = 38, double-double, batch, serving)")
+    ap.add_argument("--e2e-steps", type=int, default=0,
+                    help="steps of the end-to-end (host buffer) timing; 0 = --steps, at most 5 for n >= 30")
     ap.add_argument("--impl", default="libtor", choices=["libtor", "reference"])
     ap.add_argument("--cpu-budget", type=float, default=12.0, help="seconds of host time for each CPU baseline (the oracle; Algorithm 2 in FP64)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -559,7 +813,11 @@ def main():
     build.build()
     device = torch.device("cuda", local)
     torch.cuda.set_device(device)
-    mats, desc = workload(args.workload, rank)
+    # Several ranks on one large-matrix workload split each matrix's leaves (strong scaling,
+    # one host-level gather of three doubles per matrix and rank); otherwise every rank
+    # evaluates its own copy of the workload (weak scaling, no data-path exchange).
+    sharded = world > 1 and args.workload == "large_n30_34" and not args.weak
+    mats, desc = workload(args.workload, 0 if sharded else rank)
     ns = [m.shape[0] // 2 for m in mats]
     terms = float(sum(2.0 ** n for n in ns))
     stream = torch.cuda.Stream(device=device)
@@ -572,8 +830,8 @@ def main():
     tuned = None
     if args.autotune > 0:
         sizes = sorted(set(ns))
-        plan_file = os.path.join(ROOT, "gpurun_out", f"plan_{args.workload}.txt")
-        os.makedirs(os.path.dirname(plan_file), exist_ok=True)
+        import tempfile
+        plan_file = os.path.join(tempfile.mkdtemp(prefix="torplan_"), f"plan_{args.workload}.txt")
         tuned = {}
         for n in sizes:
             tuned.update(ctx_host.autotune(n, n, args.autotune / len(sizes)))
@@ -583,6 +841,22 @@ def main():
     dfma, fp64_tflops = binding.tor_probe_fp64(local, 0.5)
 
     paths = {}
+    last_res = []
+
+    from paper_2109_04528_gb300 import shard
+
+    def sharded_batch(ctx, batch):
+        # this rank's aligned leaf range of every matrix, then one gather and the fixed-tree merge
+        res, units = [], 0.0
+        for O, n in zip(batch, ns):
+            lo, cnt = shard.shard_range(binding.tor_plan_leaves(ctx, n), world, rank)
+            res.append(binding.tor_eval_range(ctx, O, lo, cnt))
+            units += ctx.last_times()["units_ms"]
+        got = shard._gather_checked(lambda: [(r.hi, r.lo, r.abs_sum) for r in res])
+        merged = [shard.tree_merge([g[i] for g in got]) for i in range(len(batch))]
+        for r, m in zip(res, merged):
+            r.hi, r.lo, r.abs_sum = m
+        return res, units
 
     def timed(ctx, batch, k):
         ms, units_ms = [], []
@@ -592,15 +866,20 @@ def main():
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            res = binding.tor_eval_batch(ctx, batch)
+            if sharded:
+                res, u = sharded_batch(ctx, batch)
+            else:
+                res = binding.tor_eval_batch(ctx, batch)
+                u = ctx.last_times()["units_ms"]
             e1.record(stream)
             e1.synchronize()
             ms.append(e0.elapsed_time(e1))
-            units_ms.append(ctx.last_times()["units_ms"])
+            units_ms.append(u)
             for i, r in enumerate(res):
                 if r.status != 0:
                     raise SystemExit(f"evaluation failed: status {r.status}")
                 paths[i] = r.path
+            last_res[:] = res
         return ms, units_ms
 
     timed(ctx_dev, dmats, args.warmup)
@@ -612,47 +891,47 @@ def main():
     barrier(world)
     tot_ms = max_over_ranks(world, sum(ms), device)
     # end to end: host buffers, H2D + kernels + D2H per step
-    timed(ctx_host, mats, 2)
+    large = max(ns) >= 30
+    e2e_steps = args.e2e_steps or (min(args.steps, 5) if large else args.steps)
+    timed(ctx_host, mats, 1 if large else 2)
     barrier(world)
-    e2e_ms, _ = timed(ctx_host, mats, args.steps)
+    e2e_ms, _ = timed(ctx_host, mats, e2e_steps)
     barrier(world)
     e2e_tot = max_over_ranks(world, sum(e2e_ms), device)
-    value = terms * world * args.steps / (tot_ms * 1e-3)
-    e2e_value = terms * world * args.steps / (e2e_tot * 1e-3)
-    # the same device-resident step replayed as a CUDA graph
+    copies = 1 if sharded else world  # sharded: the ranks split one copy of the workload
+    value = terms * copies * args.steps / (tot_ms * 1e-3)
+    e2e_value = terms * copies * e2e_steps / (e2e_tot * 1e-3)
+    # the same device-resident step replayed as a CUDA graph (launch-bound steps only)
     graph_ms = None
-    with binding.Context(device=local, stream=stream.cuda_stream,
-                         flags=binding.TOR_IN_DEVICE | binding.TOR_GRAPHS | xf) as ctx_g:
-        if tuned:
-            ctx_g.load_plan(plan_file)
-        timed(ctx_g, dmats, 2)
-        gms, _ = timed(ctx_g, dmats, args.steps)
-        graph_ms = sum(gms) / len(gms)
+    if not large:
+        with binding.Context(device=local, stream=stream.cuda_stream,
+                             flags=binding.TOR_IN_DEVICE | binding.TOR_GRAPHS | xf) as ctx_g:
+            if tuned:
+                ctx_g.load_plan(plan_file)
+            timed(ctx_g, dmats, 2)
+            gms, _ = timed(ctx_g, dmats, args.steps)
+            graph_ms = sum(gms) / len(gms)
     plain = None
     if len(mats) > 8:
-        # the plain GPU path: one tor_eval (launch + sync) per matrix, same kernels and plan
+        # the plain GPU path: one tor_eval per matrix (launches + sync each), looped in C, same plan
         with binding.Context(device=local, stream=stream.cuda_stream,
                              flags=binding.TOR_IN_DEVICE | xf) as ctx_plain:
             if tuned:
                 ctx_plain.load_plan(plan_file)
-            for m in dmats[:64]:
-                binding.tor_eval(ctx_plain, m)
+            binding.tor_eval_seq(ctx_plain, dmats[:64])
             torch.cuda.synchronize()
-            lat = []
             t0 = time.perf_counter()
-            for m in dmats:
-                a = time.perf_counter()
-                binding.tor_eval(ctx_plain, m)
-                lat.append(time.perf_counter() - a)
+            _, lat = binding.tor_eval_seq(ctx_plain, dmats)
             plain_s = time.perf_counter() - t0
-        lat.sort()
+        lat = np.sort(lat)
         plain = {"value": terms / plain_s, "unit": "subset terms/s", "tor_per_s": len(mats) / plain_s,
-                 "ms_per_batch": 1e3 * plain_s, "per_matrix_ms_p50": 1e3 * lat[len(lat) // 2],
-                 "per_matrix_ms_p99": 1e3 * lat[min(len(lat) - 1, int(0.99 * len(lat)))],
-                 "what": "one blocking tor_eval per matrix (H2D descriptors, 3 kernels, D2H, sync), host-timed"}
+                 "ms_per_batch": 1e3 * plain_s, "per_matrix_ms_p50": float(lat[len(lat) // 2]),
+                 "per_matrix_ms_p99": float(lat[min(len(lat) - 1, int(0.99 * len(lat)))]),
+                 "what": "tor_eval_seq: one tor_eval per matrix (descriptors H2D, 3 kernels, D2H, sync), "
+                         "looped in C, host wall time"}
     units_avg = sum(units_ms) / len(units_ms)
     # algorithmic flops of the arithmetic each matrix actually took
-    flops = float(sum(algorithmic_flops(n, paths.get(i, 0)) for i, n in enumerate(ns)))
+    flops = float(sum(algorithmic_flops(n, paths.get(i, 0)) for i, n in enumerate(ns))) / (world if sharded else 1)
     n_real = sum(1 for i in range(len(ns)) if paths.get(i, 0) & 1)
     ext = any(paths.get(i, 0) & 2 for i in range(len(ns)))
     achieved = flops / (units_avg * 1e-3) / 1e12
@@ -667,7 +946,7 @@ def main():
     # The FP64 pipe issues one add, mul or FMA per slot alike, while the flop count weighs an FMA
     # twice; so also report the pipe's busy fraction in algorithmic FP64 instructions (flops.path_ops)
     from paper_2109_04528_gb300.flops import path_ops
-    ops = float(sum(path_ops(n, paths.get(i, 0)) for i, n in enumerate(ns)))
+    ops = float(sum(path_ops(n, paths.get(i, 0)) for i, n in enumerate(ns))) / (world if sharded else 1)
     inst = {"ops_per_launch": ops, "achieved_gops": ops / (units_avg * 1e-3) / 1e9,
             "peak_gops": peak_ops / 1e9, "frac": ops / (units_avg * 1e-3) / peak_ops,
             "probe_gops": dfma / 1e9,
@@ -677,15 +956,16 @@ def main():
         "metric": "subset terms/s", "value": value, "unit": "subset terms/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": tot_ms / args.steps,
         "ms_per_step_median": statistics.median(ms),
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64x2" if ext else "f64",
+        "higher_is_better": True, "scaling": "strong" if sharded else "weak", "vs_baseline": None,
+        "dtype": "f64x2" if ext else "f64",
         "data": "synthetic",
         "config": {"workload": args.workload, "desc": desc, "n": ns, "terms_per_step": terms,
                    "l2": "flushed between steps (512 MB write)",
                    "prefix_depth": {str(n): ctx_dev.plan_prefix_depth(n) for n in sorted(set(ns))}},
-        "tor_per_s": len(mats) * world * args.steps / (tot_ms * 1e-3),
+        "tor_per_s": len(mats) * copies * args.steps / (tot_ms * 1e-3),
         "e2e": {"value": e2e_value, "unit": "subset terms/s",
                 "h2d_bytes_per_step": int(sum(m.size * 16 for m in mats)),
-                "d2h_bytes_per_step": int(32 * len(mats))},
+                "d2h_bytes_per_step": int(32 * len(mats)), "steps": e2e_steps},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
                      "frac": achieved / peak_tflops,
                      "traffic": profiled_traffic(args.workload, "k_units_ext" if ext else "k_units",
@@ -701,12 +981,28 @@ def main():
         "clocks": clocks,
     }
     line["roofline"]["fp64_instructions"] = inst
-    line["graph_replay"] = {"ms_per_step": graph_ms, "value": terms / (graph_ms * 1e-3), "unit": "subset terms/s"}
+    if graph_ms:
+        line["graph_replay"] = {"ms_per_step": graph_ms, "value": terms / (graph_ms * 1e-3), "unit": "subset terms/s"}
     if tuned:
         line["config"]["autotuned"] = True
     if plain:
         line["plain_per_matrix"] = plain
         line["batched_over_plain"] = value / plain["value"]
+    if sharded:
+        one = [binding.tor_eval(ctx_dev, d) for d in dmats]  # the whole of every matrix on this GPU alone
+        line["config"]["parallelism"] = f"leaf ranges of each matrix split over {world} ranks, host gather + fixed-tree merge"
+        line["sharded_equals_one_gpu"] = all((a.hi, a.lo, a.abs_sum) == (b.hi, b.lo, b.abs_sum)
+                                             for a, b in zip(last_res, one))
+    if args.workload == "large_n30_34" and not args.no_extras and world == 1 and not xf:
+        res64 = list(binding.tor_eval_batch(ctx_dev, dmats))  # the timed step's own results
+        line.update(large_extras(local, stream, ctx_dev, mats, dmats, res64, ns))
+        line["batch4096"] = batch_compare(local, stream, steps=5)
+        line["serve"] = serve_summary(local, args.serve_high_window, args.serve_sustain_rate)
+    elif last_res:
+        line["results"] = [result_record(f"n={n}", n, r, None,
+                                         ({"hi": g["hi"], "lo": g["lo"], "name": f"binary128 oracle ({g['method']}), stored"}
+                                          if (g := golden_for(O)) is not None else None))
+                           for n, r, O in zip(ns, last_res, mats)][:16]
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(mats, args.cpu_budget)
         line["cpu_alg2"] = cpu_alg2(mats, args.cpu_budget)

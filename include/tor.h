@@ -92,7 +92,7 @@ typedef struct tor_session tor_session;
 typedef struct {
   int device;          /* CUDA device ordinal */
   void* stream;        /* cudaStream_t to run on; NULL = the library creates its own */
-  size_t mem_budget;   /* cap on the library's device memory in bytes; 0 = no cap */
+  size_t mem_budget;   /* cap on the device memory the context holds (slots and sessions), bytes; 0 = no cap */
   int prefix_depth;    /* unit prefix depth p for every n; -1 = built-in plan / autotune table */
   int layout;          /* TOR_LAYOUT_BLOCK or TOR_LAYOUT_PAIRS */
   unsigned flags;      /* TOR_IN_DEVICE | TOR_NO_CHECK */
@@ -135,13 +135,27 @@ tor_status tor_eval(tor_ctx* ctx, int n, const tor_c128* O, int ld, tor_result* 
 tor_status tor_eval_batch(tor_ctx* ctx, int count, const int* n, const tor_c128* const* O,
                           const int* ld, tor_result* out);
 
+/* The plain one-call-per-matrix path, looped in C: evaluates the `count`
+ * matrices one after the other, each exactly as its own tor_eval call (its
+ * own intake, units and reduce launches and one synchronisation), with no
+ * interpreter between the calls.  Arguments as for tor_eval_batch; ms (may be
+ * NULL) receives count host-measured wall times in milliseconds, one per
+ * matrix (call entry to return).  Results equal tor_eval_batch's bitwise.
+ * This is the baseline a batched launch (Sec. 4's task-parallel evaluation of
+ * many matrices) is compared with.  Returns the first error. */
+tor_status tor_eval_seq(tor_ctx* ctx, int count, const int* n, const tor_c128* const* O, const int* ld,
+                        tor_result* out, double* ms);
+
 /* Queues one matrix for evaluation and returns at once with a ticket.  The
  * context's serving thread batches queued requests continuously: a request
  * that arrives while others run is admitted as soon as a slot and the device
- * memory budget allow.  Large requests (more than 2^25 subset terms) run one
- * at a time in a low-priority lane whose persistent kernel yields the SMs
- * every ~5 ms; small requests are batched FIFO into high-priority lanes and
- * may pass a large request that waits.  Each result is bitwise the same as
+ * memory budget allow.  Large requests (more than 2^25 subset terms) run FIFO
+ * in two low-priority lanes, one request each, so the next large request's
+ * blocks take the SMs that the current one's last tasks leave idle; small
+ * requests are batched FIFO into two high-priority lanes, whose blocks take
+ * SMs as soon as any block of a large request ends, and may pass large
+ * requests that wait.  (Environment, for experiments: TOR_SERVE_SLICE_MS = t
+ * makes large requests yield the SMs every t ms; TOR_SERVE_LARGE_LANES = 1..3.)  Each result is bitwise the same as
  * tor_eval of the same matrix on the same context.  TOR_EAGAIN if the queue
  * is full. */
 tor_status tor_submit(tor_ctx* ctx, int n, const tor_c128* O, int ld, uint64_t* ticket);
@@ -150,6 +164,25 @@ tor_status tor_submit(tor_ctx* ctx, int n, const tor_c128* O, int ld, uint64_t* 
  * Returns TOR_EAGAIN if it is still pending, TOR_EINVAL for an unknown or
  * already collected ticket, else the request's status with *out filled. */
 tor_status tor_poll(tor_ctx* ctx, uint64_t ticket, tor_result* out, double timeout_s);
+
+/* Waits up to timeout_s (0 = do not wait, < 0 = forever) until any of the
+ * `count` tickets has completed, collects that one request (as tor_poll does)
+ * and writes its position in tickets[] to *index.  The others stay pending.
+ * Returns TOR_EAGAIN if none completed in time, TOR_EINVAL if a ticket is
+ * unknown or already collected, else the collected request's status.  For a
+ * client with many requests in flight, which then sees each completion when
+ * it happens rather than in submission order. */
+tor_status tor_poll_any(tor_ctx* ctx, const uint64_t* tickets, int count, double timeout_s, int* index,
+                        tor_result* out);
+
+/* Device bytes the context holds now -- every slot's buffers and the
+ * resident matrices of its sessions -- and its budget (tor_config.mem_budget,
+ * 0 = none); either pointer may be NULL.  Under a budget the serving loop
+ * admits a batch only if the bytes held stay within it: idle slots give their
+ * buffers back first, then the batch shrinks, and a request that cannot fit
+ * with nothing else running fails with TOR_ENOMEM.  A blocking call over the
+ * budget fails with TOR_ENOMEM (it does not take memory from serving slots). */
+tor_status tor_memory(tor_ctx* ctx, size_t* held, size_t* budget);
 
 /* Served requests, completed batches and requests still queued (any may be NULL). */
 tor_status tor_serving_stats(tor_ctx* ctx, long long* served, long long* batches, long long* queued);
@@ -177,6 +210,14 @@ tor_status tor_session_create(tor_ctx* ctx, int n_total, const tor_c128* M, int 
  * kernel reads the matrices after they are freed.  A session may outlive its
  * context (destroying the context detaches it).  NULL is ignored. */
 void tor_session_destroy(tor_session* s);
+
+/* Copies the session's resident O^(j) (2j x 2j, the exact matrix every
+ * marginal of prefix j reads) to the host buffer out, row-major with leading
+ * dimension ld >= 2j, in the layout of the context the session was made on
+ * (block if that context is gone).  For checking marginals against another
+ * evaluator on identical inputs.  TOR_EINVAL for j outside [1, n_total] or
+ * ld < 2j; TOR_ECUDA if the copy fails.  Blocking. */
+tor_status tor_session_marginal_matrix(tor_session* s, int j, tor_c128* out, int ld);
 
 /* Tor(O^(j)_S) for S = modes[0..k-1] (distinct, each < j, any order), blocking. */
 tor_status tor_eval_marginal(tor_ctx* ctx, tor_session* s, int j, int k, const int* modes,
@@ -281,6 +322,19 @@ tor_status tor_plan_load(tor_ctx* ctx, const char* path);
  * 8 warps each, independent chains) for about `seconds`.  Writes DFMA per
  * second and FP64 TFLOP/s (2 flops per DFMA). */
 tor_status tor_probe_fp64(int device, double seconds, double* dfma_per_s, double* fp64_tflops);
+
+/* The FP64 reciprocal and reciprocal square root of every include step's 2x2
+ * pivot (the rsqrt and rcp of Algorithm 1's diagonal and of the Schur
+ * complement's pivot, Sec. 2): the hardware estimate (rcp/rsqrt.approx.ftz.f64)
+ * refined by one cubic series step.  For each of the `count` host doubles x[i]
+ * writes four host doubles out[4i..4i+3] computed on `device`: the library's
+ * reciprocal, CUDA's IEEE division 1.0 / x (round to nearest), the library's
+ * reciprocal square root and CUDA's rsqrt(x) -- so a test can state the error
+ * of the library's versions.  Valid for normal x with a normal reciprocal
+ * (2^-1022 <= |x| < 2^1022; positive x for the square root): the estimates
+ * flush subnormals to zero.  Allocates and frees device memory; blocking.
+ * TOR_EINVAL for bad arguments (count above 2^26). */
+tor_status tor_check_recip(int device, int count, const double* x, double* out);
 
 /* ---- evaluation without allocation ---- */
 

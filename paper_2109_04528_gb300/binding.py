@@ -24,11 +24,11 @@ TOR_SESSION_SIGMA, TOR_SESSION_O = 0, 1
 
 # Every symbol include/tor.h declares (the ABI test checks the library exports them).
 EXPORTS = ["tor_config_default", "tor_create", "tor_destroy", "tor_eval", "tor_eval_batch", "tor_submit",
-           "tor_poll", "tor_cancel", "tor_strerror", "tor_last_error", "tor_plan_prefix_depth",
-           "tor_set_prefix_depth", "tor_eval_units", "tor_last_times", "tor_probe_fp64",
-           "tor_eval_noalloc", "tor_autotune", "tor_plan_save", "tor_plan_load", "tor_serving_stats",
+           "tor_poll", "tor_poll_any", "tor_cancel", "tor_strerror", "tor_last_error", "tor_plan_prefix_depth",
+           "tor_set_prefix_depth", "tor_eval_units", "tor_last_times", "tor_probe_fp64", "tor_check_recip",
+           "tor_eval_noalloc", "tor_autotune", "tor_plan_save", "tor_plan_load", "tor_serving_stats", "tor_memory",
            "tor_session_create", "tor_session_destroy", "tor_eval_marginal", "tor_submit_marginal",
-           "tor_plan_leaves", "tor_eval_range", "tor_sample"]
+           "tor_session_marginal_matrix", "tor_eval_seq", "tor_plan_leaves", "tor_eval_range", "tor_sample"]
 TOR_NOALLOC_MAX_N = 16
 
 
@@ -96,8 +96,10 @@ def load_library():
     lib.tor_destroy.restype = None
     lib.tor_eval.argtypes = [c_void_p, c_int, c_void_p, c_int, P(tor_result)]
     lib.tor_eval_batch.argtypes = [c_void_p, c_int, P(c_int), P(c_void_p), P(c_int), P(tor_result)]
+    lib.tor_eval_seq.argtypes = [c_void_p, c_int, P(c_int), P(c_void_p), P(c_int), P(tor_result), P(c_double)]
     lib.tor_submit.argtypes = [c_void_p, c_int, c_void_p, c_int, P(ctypes.c_uint64)]
     lib.tor_poll.argtypes = [c_void_p, ctypes.c_uint64, P(tor_result), c_double]
+    lib.tor_poll_any.argtypes = [c_void_p, P(ctypes.c_uint64), c_int, c_double, P(c_int), P(tor_result)]
     lib.tor_cancel.argtypes = [c_void_p]
     lib.tor_strerror.argtypes = [c_int]
     lib.tor_strerror.restype = ctypes.c_char_p
@@ -108,15 +110,18 @@ def load_library():
     lib.tor_eval_units.argtypes = [c_void_p, c_int, c_void_p, c_int, P(c_double), c_size_t, P(tor_result)]
     lib.tor_last_times.argtypes = [c_void_p, P(c_double)]
     lib.tor_probe_fp64.argtypes = [c_int, c_double, P(c_double), P(c_double)]
+    lib.tor_check_recip.argtypes = [c_int, c_int, P(c_double), P(c_double)]
     lib.tor_eval_noalloc.argtypes = [c_int, c_int, c_void_p, c_int, c_int, c_void_p, c_void_p]
     lib.tor_autotune.argtypes = [c_void_p, c_int, c_int, c_double, P(c_int)]
     lib.tor_plan_save.argtypes = [c_void_p, ctypes.c_char_p]
     lib.tor_plan_load.argtypes = [c_void_p, ctypes.c_char_p]
     LL = ctypes.c_longlong
     lib.tor_serving_stats.argtypes = [c_void_p, P(LL), P(LL), P(LL)]
+    lib.tor_memory.argtypes = [c_void_p, P(c_size_t), P(c_size_t)]
     lib.tor_session_create.argtypes = [c_void_p, c_int, c_void_p, c_int, c_int, P(c_void_p)]
     lib.tor_session_destroy.argtypes = [c_void_p]
     lib.tor_session_destroy.restype = None
+    lib.tor_session_marginal_matrix.argtypes = [c_void_p, c_int, c_void_p, c_int]
     lib.tor_eval_marginal.argtypes = [c_void_p, c_void_p, c_int, c_int, P(c_int), P(tor_result)]
     lib.tor_submit_marginal.argtypes = [c_void_p, c_void_p, c_int, c_int, P(c_int), P(ctypes.c_uint64)]
     lib.tor_sample.argtypes = [c_void_p, c_void_p, c_int, c_int, P(c_double), c_void_p, P(c_double), P(c_double)]
@@ -228,6 +233,12 @@ class Context:
         self._lib.tor_serving_stats(self.handle, ctypes.byref(s), ctypes.byref(bt), ctypes.byref(q))
         return {"served": s.value, "batches": bt.value, "queued": q.value}
 
+    def memory(self):
+        """(device bytes the context holds, its budget; 0 = none)."""
+        h, b = ctypes.c_size_t(), ctypes.c_size_t()
+        self._lib.tor_memory(self.handle, ctypes.byref(h), ctypes.byref(b))
+        return h.value, b.value
+
     def save_plan(self, path: str):
         st = self._lib.tor_plan_save(self.handle, os.fsencode(path))
         if st != TOR_OK:
@@ -283,6 +294,25 @@ def tor_eval_batch(ctx: Context, mats, check: bool = True):
     return [TorResult.of(r) for r in res]
 
 
+def tor_eval_seq(ctx: Context, mats, check: bool = True):
+    """The plain path looped in C: one tor_eval per matrix, no Python between
+    the calls.  Returns (list of TorResult, array of per-matrix wall ms)."""
+    k = len(mats)
+    if k == 0:
+        return [], np.zeros(0)
+    args = [_matrix_args(ctx, O) for O in mats]
+    ns = (ctypes.c_int * k)(*[a[1] for a in args])
+    lds = (ctypes.c_int * k)(*[a[2] for a in args])
+    ptrs = (ctypes.c_void_p * k)(*[a[3] for a in args])
+    res = (tor_result * k)()
+    ms = np.zeros(k, dtype=np.float64)
+    st = ctx._lib.tor_eval_seq(ctx.handle, k, ns, ptrs, lds, res, ms.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+    if check and st != TOR_OK:
+        raise TorError(st, ctx.last_error() or "tor_eval_seq")
+    del args
+    return [TorResult.of(r) for r in res], ms
+
+
 def tor_eval_units(ctx: Context, O):
     """tor_eval plus the per-unit partials: returns (TorResult, p, array of shape (2^p, 3))."""
     keep, n, ld, ptr = _matrix_args(ctx, O)
@@ -331,6 +361,31 @@ def tor_poll(ctx: Context, ticket: int, timeout_s: float = -1.0):
     return st, TorResult.of(res)
 
 
+def tor_check_recip(x, device: int = 0):
+    """(rcp64(x), 1.0/x, rsqrt64(x), rsqrt(x)) computed on the GPU, four float64 arrays."""
+    lib = load_library()
+    x = np.ascontiguousarray(np.asarray(x, dtype=np.float64))
+    out = np.zeros((x.size, 4), dtype=np.float64)
+    dp = ctypes.POINTER(ctypes.c_double)
+    st = lib.tor_check_recip(device, x.size, x.ctypes.data_as(dp), out.ctypes.data_as(dp))
+    if st != TOR_OK:
+        raise TorError(st, "tor_check_recip")
+    return out[:, 0], out[:, 1], out[:, 2], out[:, 3]
+
+
+def tor_poll_any(ctx: Context, tickets, timeout_s: float = -1.0):
+    """Waits for whichever of `tickets` completes first.  Returns (status,
+    index into tickets, TorResult); (TOR_EAGAIN, -1, None) if none did in time."""
+    k = len(tickets)
+    arr = (ctypes.c_uint64 * max(k, 1))(*[int(t) for t in tickets])
+    idx = ctypes.c_int(-1)
+    res = tor_result()
+    st = ctx._lib.tor_poll_any(ctx.handle, arr, k, timeout_s, ctypes.byref(idx), ctypes.byref(res))
+    if st == TOR_EAGAIN or idx.value < 0:
+        return st, -1, None
+    return st, idx.value, TorResult.of(res)
+
+
 def tor_probe_fp64(device: int = 0, seconds: float = 0.5):
     """(DFMA per second, FP64 TFLOP/s) from the library's saturating FMA kernel."""
     lib = load_library()
@@ -351,6 +406,14 @@ class Session:
         if st != TOR_OK:
             raise TorError(st, ctx.last_error() or "tor_session_create")
         self._h, self.ctx, self.n = h, ctx, n
+
+    def marginal_matrix(self, j: int) -> np.ndarray:
+        """The resident O^(j) (2j x 2j complex128, the context's layout)."""
+        out = np.zeros((2 * j, 2 * j), dtype=np.complex128)
+        st = self.ctx._lib.tor_session_marginal_matrix(self._h, j, ctypes.c_void_p(out.ctypes.data), 2 * j)
+        if st != TOR_OK:
+            raise TorError(st, self.ctx.last_error() or "tor_session_marginal_matrix")
+        return out
 
     def close(self):
         if getattr(self, "_h", None) is not None:

@@ -15,7 +15,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 BUILD = os.path.join(HERE, "_build")
-SOURCES = ["tor_kernels.cu", "tor_host.cu", "tor_noalloc.cu"]
+SOURCES = ["tor_kernels.cu", "tor_host.cu", "tor_noalloc.cu", "tor_checks.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -37,31 +37,42 @@ namespace {
 struct DevBuf {
   void* p = nullptr;
   size_t cap = 0;
+  std::atomic<long long>* acct = nullptr;  // the context's count of device bytes held, or null
+  bool exact = false;                      // allocate exactly what is asked (under a memory budget)
+  cudaStream_t astream = nullptr;          // stream-ordered allocation on this stream (serving slots)
   // grows (never shrinks); bumps *gen when the address changes
   cudaError_t ensure(size_t bytes, uint64_t* gen) {
     if (bytes <= cap && p) return cudaSuccess;
     bytes = std::max<size_t>(bytes, 256);
-    size_t want = std::max(bytes, cap + cap / 2);
-    if (p) cudaFree(p);
-    p = nullptr;
-    cap = 0;
+    size_t want = exact ? bytes : std::max(bytes, cap + cap / 2);
+    release();
     ++*gen;
-    cudaError_t e = cudaMalloc(&p, want);
+    cudaError_t e = alloc(want);
+    if (e != cudaSuccess && want > bytes) {
+      cudaGetLastError();
+      want = bytes;
+      e = alloc(want);
+    }
     if (e != cudaSuccess) {
       cudaGetLastError();
-      e = cudaMalloc(&p, bytes);
-      if (e != cudaSuccess) {
-        cudaGetLastError();
-        p = nullptr;
-        return e;
-      }
-      want = bytes;
+      p = nullptr;
+      return e;
     }
     cap = want;
+    if (acct) *acct += (long long)cap;
     return cudaSuccess;
   }
+  cudaError_t alloc(size_t bytes) {
+    // a serving slot allocates in its own stream's order: unlike cudaMalloc /
+    // cudaFree this does not wait for the kernels of the other slots
+    return astream ? cudaMallocAsync(&p, bytes, astream) : cudaMalloc(&p, bytes);
+  }
   void release() {
-    if (p) cudaFree(p);
+    if (p) {
+      if (astream) cudaFreeAsync(p, astream);
+      else cudaFree(p);
+      if (acct) *acct -= (long long)cap;
+    }
     p = nullptr;
     cap = 0;
   }
@@ -114,6 +125,9 @@ struct MatIn {
 };
 
 struct Slot {
+  Slot() = default;
+  Slot(const Slot&) = delete;
+  Slot& operator=(const Slot&) = delete;
   cudaStream_t stream = nullptr;
   bool own_stream = false;
   DevBuf d_O, d_B, d_front, d_partials, d_flags, d_results, d_lane, d_warp, d_modes;
@@ -134,6 +148,8 @@ struct Slot {
   std::vector<int> act;  // index into the caller's list, job order
   std::vector<MatDesc> mats;
   std::vector<TaskDesc> tasks;
+  std::vector<long long> task_shape;  // the job shape `tasks` was built for
+  uint64_t tasks_staged_gen = ~0ull;  // buffer generation when `tasks` was copied into h_front
   int J = 0;
   long long o_elems = 0, b_elems = 0, parts = 0, reds = 0, red_chunks = 0, mode_elems = 0, lane_e = 0, warp_e = 0;
   bool want_parts = false;
@@ -141,16 +157,30 @@ struct Slot {
   int cancel_epoch = 0;
   bool busy = false;
   bool graphed = false;  // the last pass was a graph replay
+  // scratch-slot pool of non-persistent k_units launches (one bit per resident block)
+  unsigned* d_pool = nullptr;
+  int pool_words = 0;
   // serving state
   cudaEvent_t units_done = nullptr;  // end of a time slice of k_units
   int phase = 0;                     // 0 idle, 1 k_units slice in flight, 2 reduce and copies in flight
   bool large = false;                // runs one large request, time-sliced, low priority
   double t_start = 0;
 
+  static constexpr int kBufs = 9;
+  DevBuf* bufs[kBufs] = {&d_O, &d_B, &d_front, &d_partials, &d_flags, &d_results, &d_lane, &d_warp, &d_modes};
+  size_t dev_bytes() const {
+    size_t t = 0;
+    for (const DevBuf* b : bufs) t += b->cap;
+    return t;
+  }
+  void release_dev() {
+    for (DevBuf* b : bufs) b->release();
+  }
   void release() {
-    for (DevBuf* b : {&d_O, &d_B, &d_front, &d_partials, &d_flags, &d_results, &d_lane, &d_warp, &d_modes})
-      b->release();
+    for (DevBuf* b : bufs) b->release();
     for (HostBuf* b : {&h_O, &h_front, &h_results, &h_ctl, &h_modes}) b->release();
+    if (d_pool) cudaFree(d_pool);
+    d_pool = nullptr;
     for (auto& g : graphs) cudaGraphExecDestroy(g.exec);
     graphs.clear();
     for (int i = 0; i < 5; ++i)
@@ -207,12 +237,17 @@ struct tor_ctx {
   std::thread server;
   bool server_started = false, stopping = false;
   size_t queue_limit = 1 << 20;
-  int n_serve_slots = 3;  // one large lane + two small lanes
+  int n_serve_slots = 4;   // large lanes first, then small lanes
+  int n_large_slots = 2;   // two large requests in flight: the next one's blocks fill the tail of the current one
+  long long large_slice_ns = 0;  // > 0: large jobs yield the SMs every slice (TOR_SERVE_SLICE_MS); 0 = run through
   int max_batch = 4096;
   double max_batch_terms = 268435456.0;  // ~45 ms of GPU work per served batch (2^28 subset terms)
   std::vector<std::unique_ptr<Slot>> serve;
   std::atomic<long long> served{0}, batches{0};
   std::vector<tor_session*> sessions;  // live sessions of this context (guarded by q_mu)
+  // device bytes held by the slots' buffers and the sessions' matrices: what
+  // tor_config.mem_budget caps
+  std::atomic<long long> dev_held{0};
 };
 
 // Bytes of one matrix entry the kernels may use: complex128, or a complex
@@ -290,26 +325,84 @@ static cudaError_t slot_init(Slot& s, cudaStream_t stream, int priority = 0) {
   return cudaEventCreateWithFlags(&s.done, cudaEventDisableTiming);
 }
 
-// Device bytes a job of these matrices needs (what admission checks).
-static size_t job_bytes(tor_ctx* ctx, const std::vector<MatIn>& ins, size_t count) {
-  long long o = 0, b = 0, parts = 0, md = 0, lane_e = 0, warp_e = 0, ntask = 0;
+// A slot's device buffers count toward the context's held bytes; under a
+// memory budget they are allocated exactly; serving slots allocate in their
+// own stream's order.
+static void slot_account(tor_ctx* ctx, Slot& S, bool stream_ordered) {
+  for (DevBuf* b : S.bufs) {
+    b->acct = &ctx->dev_held;
+    b->exact = ctx->cfg.mem_budget != 0;
+    b->astream = stream_ordered ? S.stream : nullptr;
+  }
+}
+
+// Device bytes of each of a slot's buffers (in Slot::bufs order) that a job of
+// these matrices needs: the sizes slot_prepare allocates.
+struct Needs {
+  size_t b[Slot::kBufs] = {};
+  size_t total() const {
+    size_t t = 0;
+    for (size_t v : b) t += v;
+    return t;
+  }
+};
+
+static Needs job_needs(tor_ctx* ctx, const std::vector<MatIn>& ins, size_t count) {
+  long long o = 0, bt = 0, parts = 0, reds = 0, md = 0, lane_e = 0, warp_e = 0, ntask = 0;
+  std::map<int, long long> small_units;  // n -> units of the matrices with p < 5 (one lane each)
+  long long J = 0;
   for (size_t i = 0; i < count; ++i) {
     const MatIn& m = ins[i];
     if (m.n < 1 || m.n > 64) continue;
+    ++J;
     const int p = plan_p(ctx, m.n);
     if (!m.dev && !m.modes) o += 4ll * m.n * m.n;
     if (m.modes) md += m.n;
-    b += tri(m.n);
-    parts += 2ll << p;
-    ntask += p >= 5 ? (1ll << (p - 5)) : 1;
+    bt += tri(m.n);
+    parts += 1ll << p;
+    if (m.leaf_count > 0) {
+      long long r = 1;
+      while (r < m.leaf_count) r <<= 1;
+      reds += r;
+    } else {
+      reds += 1ll << (p >= 5 ? p - 5 : p);
+    }
+    if (p >= 5) ntask += m.leaf_count > 0 ? m.leaf_count : (1ll << (p - 5));
+    else small_units[m.n] += 1ll << p;
     lane_e = std::max(lane_e, lane_elems_for(m.n, p));
     warp_e = std::max(warp_e, warp_elems_for(m.n, p));
   }
+  for (const auto& kv : small_units) ntask += (kv.second + 31) / 32;
   const size_t eb = entry_bytes(ctx);
-  return (size_t)(o * 16 + parts * 32 + md * 4 + ntask * (long long)sizeof(TaskDesc) +
-                  (long long)count * (long long)(sizeof(MatDesc) + sizeof(ResultRec) + 4)) +
-         (size_t)b * eb + (size_t)ctx->nwarps * 32 * lane_e * lane_entry_bytes(ctx) +
-         (size_t)ctx->nwarps * warp_e * eb + 4096;
+  const size_t off_tasks = (256 + (size_t)J * sizeof(MatDesc) + 255) / 256 * 256;
+  Needs N;
+  N.b[0] = (size_t)o * 16;                                                  // d_O
+  N.b[1] = (size_t)bt * eb;                                                 // d_B
+  N.b[2] = off_tasks + (size_t)ntask * sizeof(TaskDesc);                    // d_front
+  N.b[3] = (size_t)(parts + reds) * 32;                                     // d_partials
+  N.b[4] = (size_t)J * sizeof(int);                                         // d_flags
+  N.b[5] = (size_t)J * sizeof(ResultRec);                                   // d_results
+  N.b[6] = (size_t)ctx->nwarps * 32 * (size_t)lane_e * lane_entry_bytes(ctx);  // d_lane
+  N.b[7] = (size_t)ctx->nwarps * (size_t)warp_e * eb;                       // d_warp
+  N.b[8] = (size_t)md * sizeof(int);                                        // d_modes
+  for (size_t& v : N.b) v = std::max<size_t>(v, 256);  // DevBuf's smallest allocation
+  return N;
+}
+
+// Bytes slot S would add to what the context holds to run a job with these
+// needs: each buffer too small is replaced by one of exactly the needed size
+// (the slots of a budgeted context allocate exactly).
+static size_t slot_growth(const Slot& S, const Needs& N) {
+  size_t g = 0;
+  for (int i = 0; i < Slot::kBufs; ++i)
+    if (N.b[i] > S.bufs[i]->cap || !S.bufs[i]->p) g += N.b[i] - std::min(N.b[i], S.bufs[i]->cap);
+  return g;
+}
+
+static bool over_budget(tor_ctx* ctx, const Slot& S, const Needs& N) {
+  if (!ctx->cfg.mem_budget) return false;
+  const long long held = ctx->dev_held.load();
+  return (size_t)std::max(0ll, held) + slot_growth(S, N) > ctx->cfg.mem_budget;
 }
 
 // Validates the inputs, fills trivial results, plans the job and fills the
@@ -347,7 +440,6 @@ static tor_status slot_prepare(tor_ctx* ctx, Slot& S, const std::vector<MatIn>& 
   std::stable_sort(S.act.begin(), S.act.end(), [&](int a, int b) { return ins[a].n > ins[b].n; });
   const int J = (int)S.act.size();
   S.mats.assign(J, MatDesc{});
-  S.tasks.clear();
   S.o_elems = S.b_elems = S.parts = S.reds = S.red_chunks = S.mode_elems = S.lane_e = S.warp_e = 0;
   for (int j = 0; j < J; ++j) {
     const MatIn& m = ins[S.act[j]];
@@ -383,6 +475,19 @@ static tor_status slot_prepare(tor_ctx* ctx, Slot& S, const std::vector<MatIn>& 
   // warp tasks, largest subtrees first.  All tasks of one size group (equal n,
   // adjacent after the sort above) share M, so ordering the groups stably by M
   // and emitting their tasks in order is a stable sort of the tasks by M.
+  // The list depends only on the job's shape (sizes, prefix depths and leaf
+  // ranges in job order); a slot keeps the list of its last job and reuses it
+  // when the shape repeats (a batch of thousands of matrices has millions of
+  // tasks, whose ordering is host time with the GPU idle).
+  std::vector<long long> shape;
+  shape.reserve(3 * (size_t)J);
+  for (int j = 0; j < J; ++j) {
+    const MatIn& m = ins[S.act[j]];
+    shape.push_back((long long)S.mats[j].n | (long long)S.mats[j].p << 8);
+    shape.push_back(m.leaf_lo);
+    shape.push_back(m.leaf_count);
+  }
+  const bool reuse_tasks = !S.tasks.empty() && shape == S.task_shape;
   struct Group {
     int j, k, M;
   };
@@ -401,8 +506,14 @@ static tor_status slot_prepare(tor_ctx* ctx, Slot& S, const std::vector<MatIn>& 
     j = k;
   }
   std::stable_sort(groups.begin(), groups.end(), [](const Group& a, const Group& b) { return a.M > b.M; });
-  S.tasks.reserve((size_t)ntasks);
+  if (!reuse_tasks) {
+    S.tasks.clear();
+    S.task_shape.swap(shape);
+    S.tasks_staged_gen = ~0ull;
+  }
+  if (!reuse_tasks) S.tasks.reserve((size_t)ntasks);
   for (const Group& g : groups) {
+    if (reuse_tasks) break;
     const int j = g.j, k = g.k, p = S.mats[j].p, M = g.M;
     if (p >= 5) {
       for (int a = j; a < k; ++a) {
@@ -421,8 +532,9 @@ static tor_status slot_prepare(tor_ctx* ctx, Slot& S, const std::vector<MatIn>& 
   const size_t eb = entry_bytes(ctx);
   const size_t lane_bytes = (size_t)ctx->nwarps * 32 * S.lane_e * lane_entry_bytes(ctx);
   const size_t warp_bytes = (size_t)ctx->nwarps * S.warp_e * eb;
-  S.bytes = job_bytes(ctx, ins, ins.size());
-  if (ctx->cfg.mem_budget && S.bytes > ctx->cfg.mem_budget) {
+  const Needs needs = job_needs(ctx, ins, ins.size());
+  S.bytes = needs.total();
+  if (over_budget(ctx, S, needs)) {
     for (int j = 0; j < J; ++j) out[S.act[j]].status = TOR_ENOMEM;
     S.act.clear();
     S.J = 0;
@@ -482,7 +594,10 @@ static tor_status slot_prepare(tor_ctx* ctx, Slot& S, const std::vector<MatIn>& 
   }
   memset(S.h_front.p, 0, 64);  // the control words
   memcpy((char*)S.h_front.p + S.off_mats, S.mats.data(), J * sizeof(MatDesc));
-  memcpy((char*)S.h_front.p + S.off_tasks, S.tasks.data(), S.tasks.size() * sizeof(TaskDesc));
+  if (S.tasks_staged_gen != S.gen) {  // not already in the pinned staging buffer
+    memcpy((char*)S.h_front.p + S.off_tasks, S.tasks.data(), S.tasks.size() * sizeof(TaskDesc));
+    S.tasks_staged_gen = S.gen;
+  }
   S.J = J;
   *any = true;
   return first;
@@ -513,7 +628,7 @@ static tor_status rec_front(tor_ctx* ctx, Slot& S, bool timed) {
 
 // One launch of k_units; with slice_ns > 0 it stops taking tasks after that
 // long and copies (ticket, abort word) to h_ctl so the host can relaunch it.
-static tor_status rec_units(tor_ctx* ctx, Slot& S, long long slice_ns) {
+static tor_status rec_units(tor_ctx* ctx, Slot& S, long long slice_ns, bool one_task = false) {
   UnitsParams prm{};
   prm.mats = (const MatDesc*)S.p_mats;
   prm.tasks = (const TaskDesc*)S.p_tasks;
@@ -532,7 +647,15 @@ static tor_status rec_units(tor_ctx* ctx, Slot& S, long long slice_ns) {
   prm.budget_ns = ctx->cfg.timeout_s > 0 ? (long long)(ctx->cfg.timeout_s * 1e9) : 0;
   prm.slice_ns = slice_ns;
   prm.ext = (ctx->cfg.flags & TOR_EXTENDED) ? 1 : 0;
-  CK(launch_units(prm, ctx->grid, S.stream), "k_units");
+  int grid = ctx->grid;
+  if (one_task && S.d_pool) {  // a warp per task, blocks end throughout the job (see UnitsParams)
+    prm.one_task = 1;
+    prm.slot_pool = S.d_pool;
+    prm.slot_words = S.pool_words;
+    const int wpb = units_block_threads() / 32;
+    grid = (int)std::min<long long>(((long long)S.tasks.size() + wpb - 1) / wpb, 0x7fffffffll);
+  }
+  CK(launch_units(prm, grid, S.stream), "k_units");
   if (slice_ns > 0) {
     CK(cudaMemcpyAsync(S.h_ctl.p, S.p_ctl, 2 * sizeof(int), cudaMemcpyDeviceToHost, S.stream), "D2H ticket");
     CK(cudaEventRecord(S.units_done, S.stream), "event");
@@ -636,6 +759,7 @@ static tor_status slot_finish(Slot& S, tor_result* out, double* unit_partials, d
     r.path = ((q.flags & FLAG_REAL) ? 1 : 0) | (S.mats[j].ext ? 2 : 0);
     if (q.flags & FLAG_NONFINITE) r.status = TOR_EINVAL;
     else if (q.flags & FLAG_NOTHERM) r.status = TOR_ENOTHERM;
+    else if (abort_word & ABORT_NOSLOT) r.status = TOR_ECUDA;
     else if (abort_word & ABORT_CANCEL) r.status = TOR_ECANCELED;
     else if (abort_word & ABORT_TIMEOUT) r.status = TOR_ETIMEOUT;
     else if (q.flags & FLAG_NOTPD) r.status = TOR_ENOTPD;
@@ -711,8 +835,7 @@ static void server_loop(tor_ctx* ctx) {
     bool failed = false;
   };
   std::vector<InFlight> fl(ctx->serve.size());
-  size_t reserved = 0;
-  const long long slice_ns = 5000000;  // 5 ms
+  const long long slice_ns = ctx->large_slice_ns;
   auto fail_slot = [&](size_t i, tor_status st) {
     Slot& S = *ctx->serve[i];
     for (int a : S.act) fl[i].res[a].status = st;
@@ -771,7 +894,6 @@ static void server_loop(tor_ctx* ctx) {
       }
       ctx->served += (long long)fl[i].reqs.size();
       ctx->batches += 1;
-      reserved -= S.bytes;
       S.busy = false;
       S.phase = 0;
       fl[i] = InFlight();
@@ -782,7 +904,7 @@ static void server_loop(tor_ctx* ctx) {
     for (size_t i = 0; i < ctx->serve.size(); ++i) {
       Slot& S = *ctx->serve[i];
       if (S.busy) continue;
-      const bool large_lane = (i == 0);
+      const bool large_lane = (int)i < ctx->n_large_slots;
       const double big = ctx->max_batch_terms / 8;
       std::vector<Request*> batch;
       {
@@ -806,29 +928,51 @@ static void server_loop(tor_ctx* ctx) {
       if (batch.empty()) continue;
       std::vector<MatIn> ins;
       for (Request* r : batch) ins.push_back(r->in);
-      // device-memory budget: shrink the batch until it fits beside the jobs in flight
+      // device-memory budget: everything the context holds (every slot's
+      // buffers, the sessions' matrices) stays within mem_budget.  Idle slots
+      // give their buffers back first; then the batch shrinks; a request that
+      // cannot fit even with nothing else running fails with TOR_ENOMEM, else
+      // it waits for a running job to finish.
       if (ctx->cfg.mem_budget) {
-        size_t need = job_bytes(ctx, ins, ins.size());
-        while (batch.size() > 1 && reserved + need > ctx->cfg.mem_budget) {
+        Needs need = job_needs(ctx, ins, ins.size());
+        if (over_budget(ctx, S, need)) {
+          for (size_t k = 0; k < ctx->serve.size(); ++k)
+            if (k != i && !ctx->serve[k]->busy) ctx->serve[k]->release_dev();
+          std::unique_lock<std::mutex> ml(ctx->run_mu, std::try_to_lock);
+          if (ml) ctx->main.release_dev();
+        }
+        while (batch.size() > 1 && over_budget(ctx, S, need)) {
           std::lock_guard<std::mutex> lk(ctx->q_mu);
           if (batch.back()->sess) --batch.back()->sess->inflight;
           ctx->queue.push_front(batch.back());
           batch.pop_back();
           ins.pop_back();
-          need = job_bytes(ctx, ins, ins.size());
+          need = job_needs(ctx, ins, ins.size());
         }
-        if (reserved + need > ctx->cfg.mem_budget) {
-          std::lock_guard<std::mutex> lk(ctx->q_mu);
-          if (reserved == 0) {  // cannot fit even alone
+        if (over_budget(ctx, S, need)) {
+          bool others = false;  // another slot (or a blocking call on the main slot) holds memory in use
+          for (size_t k = 0; k < ctx->serve.size(); ++k) others |= k != i && ctx->serve[k]->busy;
+          {
+            std::unique_lock<std::mutex> ml(ctx->run_mu, std::try_to_lock);
+            others |= !ml;
+          }
+          const long long alone = ctx->dev_held.load() - (long long)S.dev_bytes() + (long long)need.total();
+          if (!others && alone > (long long)ctx->cfg.mem_budget) {  // cannot fit even alone
+            std::lock_guard<std::mutex> lk(ctx->q_mu);
             batch[0]->res = tor_result{};
             batch[0]->res.n = batch[0]->in.n;
             batch[0]->res.status = TOR_ENOMEM;
             complete(ctx, batch);
-          } else {  // wait for a job in flight to finish
+            continue;
+          }
+          if (!others) {
+            S.release_dev();  // fits once this slot's own smaller buffers are gone
+          } else {            // wait for a job in flight to finish
+            std::lock_guard<std::mutex> lk(ctx->q_mu);
             if (batch[0]->sess) --batch[0]->sess->inflight;
             ctx->queue.push_front(batch[0]);
+            continue;
           }
-          continue;
         }
       }
       std::vector<tor_result> res(ins.size());
@@ -850,8 +994,8 @@ static void server_loop(tor_ctx* ctx) {
         S.graphed = false;
         S.t_start = now_s();
         st = rec_front(ctx, S, false);
-        if (st == TOR_OK) st = rec_units(ctx, S, large_lane ? slice_ns : 0);
-        if (st == TOR_OK && !large_lane) {
+        if (st == TOR_OK) st = rec_units(ctx, S, large_lane ? slice_ns : 0, large_lane && slice_ns == 0);
+        if (st == TOR_OK && !(large_lane && slice_ns > 0)) {
           st = rec_back(ctx, S, false);
           if (st == TOR_OK && cudaEventRecord(S.done, S.stream) != cudaSuccess) st = TOR_ECUDA;
         }
@@ -868,8 +1012,7 @@ static void server_loop(tor_ctx* ctx) {
       }
       S.busy = true;
       S.large = large_lane;
-      S.phase = large_lane ? 1 : 2;
-      reserved += S.bytes;
+      S.phase = (large_lane && slice_ns > 0) ? 1 : 2;
       fl[i].reqs = std::move(batch);
       fl[i].res = std::move(res);
       progressed = true;
@@ -880,8 +1023,14 @@ static void server_loop(tor_ctx* ctx) {
     std::unique_lock<std::mutex> lk(ctx->q_mu);
     if (ctx->stopping && !busy && ctx->queue.empty()) return;
     if (!progressed) {
-      if (!busy && ctx->queue.empty()) ctx->q_cv.wait(lk, [&] { return ctx->stopping || !ctx->queue.empty(); });
-      else ctx->q_cv.wait_for(lk, std::chrono::microseconds(50));
+      if (!busy && ctx->queue.empty()) {
+        ctx->q_cv.wait(lk, [&] { return ctx->stopping || !ctx->queue.empty(); });
+      } else {
+        // jobs in flight: poll their events again at once (a timed wait would
+        // sleep for the kernel's timer slack, ~50 us, on every completion)
+        lk.unlock();
+        std::this_thread::yield();
+      }
     }
   }
 }
@@ -891,10 +1040,31 @@ static tor_status start_server(tor_ctx* ctx) {  // caller holds q_mu
   cudaSetDevice(ctx->cfg.device);
   for (int i = 0; i < ctx->n_serve_slots; ++i) {
     std::unique_ptr<Slot> s(new Slot());
-    cudaError_t e = slot_init(*s, nullptr, i == 0 ? 1 : -1);  // large lane low priority, small lanes high
+    // large lanes low priority, small lanes high
+    cudaError_t e = slot_init(*s, nullptr, i < ctx->n_large_slots ? 1 : -1);
     if (e != cudaSuccess) {
       s->release();
       return cuda_fail(ctx, e, "serving slot");
+    }
+    slot_account(ctx, *s, true);
+    if (i < ctx->n_large_slots) {  // the scratch-slot pool of its non-persistent launches
+      s->pool_words = (ctx->grid + 31) / 32;
+      std::vector<unsigned> init((size_t)s->pool_words, 0u);
+      if (ctx->grid % 32) init.back() = ~0u << (ctx->grid % 32);  // no slots past the resident blocks
+      e = cudaMalloc((void**)&s->d_pool, sizeof(unsigned) * init.size());
+      if (e == cudaSuccess) e = cudaMemcpy(s->d_pool, init.data(), sizeof(unsigned) * init.size(), cudaMemcpyHostToDevice);
+      if (e != cudaSuccess) {
+        s->release();
+        return cuda_fail(ctx, e, "serving slot pool");
+      }
+    }
+    // pinned staging sized up front: growing it later (cudaFreeHost) would wait for the device
+    uint64_t* g = &s->gen;
+    for (HostBuf* b : {&s->h_O, &s->h_front}) e = e == cudaSuccess ? b->ensure(1 << 20, g) : e;
+    for (HostBuf* b : {&s->h_results, &s->h_ctl, &s->h_modes}) e = e == cudaSuccess ? b->ensure(1 << 16, g) : e;
+    if (e != cudaSuccess) {
+      s->release();
+      return cuda_fail(ctx, e, "serving slot staging");
     }
     ctx->serve.push_back(std::move(s));
   }
@@ -1052,6 +1222,9 @@ static tor_status tor_create_impl(const tor_config* cfg, tor_ctx** out) {
   ctx->grid = ctx->sms * ctx->blocks_per_sm;
   ctx->nwarps = ctx->grid * (units_block_threads() / 32);
   if ((e = slot_init(ctx->main, (cudaStream_t)c.stream)) != cudaSuccess) return fail(e, "stream/events");
+  slot_account(ctx, ctx->main, false);
+  if (const char* v = getenv("TOR_SERVE_SLICE_MS")) ctx->large_slice_ns = (long long)(atof(v) * 1e6);
+  if (const char* v = getenv("TOR_SERVE_LARGE_LANES")) ctx->n_large_slots = std::max(1, std::min(3, atoi(v)));
   if ((e = cudaHostAlloc((void**)&ctx->h_cancel, sizeof(int), cudaHostAllocMapped)) != cudaSuccess)
     return fail(e, "cancel flag");
   *ctx->h_cancel = 0;
@@ -1089,7 +1262,10 @@ void tor_destroy(tor_ctx* ctx) {
   if (ctx->server.joinable()) ctx->server.join();
   for (auto& kv : ctx->reqs) delete kv.second;
   ctx->reqs.clear();
-  for (tor_session* s : ctx->sessions) s->ctx = nullptr;  // sessions outlive the context, detached
+  for (tor_session* s : ctx->sessions) {  // sessions outlive the context, detached
+    s->ctx = nullptr;
+    s->d_O.acct = nullptr;
+  }
   ctx->sessions.clear();
   cudaSetDevice(ctx->cfg.device);
   if (ctx->main.stream) {
@@ -1180,6 +1356,24 @@ tor_status tor_eval(tor_ctx* ctx, int n, const tor_c128* O, int ld, tor_result* 
   return guarded([&] { return tor_eval_impl(ctx, n, O, ld, out); });
 }
 
+static tor_status tor_eval_seq_impl(tor_ctx* ctx, int count, const int* n, const tor_c128* const* O, const int* ld,
+                                    tor_result* out, double* ms) {
+  if (!ctx || count < 0 || (count > 0 && (!n || !O || !ld || !out))) return TOR_EINVAL;
+  tor_status first = TOR_OK;
+  for (int i = 0; i < count; ++i) {
+    const auto t0 = std::chrono::steady_clock::now();
+    const tor_status st = tor_eval_impl(ctx, n[i], O[i], ld[i], &out[i]);
+    if (ms) ms[i] = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    if (first == TOR_OK && st != TOR_OK) first = st;
+  }
+  return first;
+}
+
+tor_status tor_eval_seq(tor_ctx* ctx, int count, const int* n, const tor_c128* const* O, const int* ld,
+                        tor_result* out, double* ms) {
+  return guarded([&] { return tor_eval_seq_impl(ctx, count, n, O, ld, out, ms); });
+}
+
 static tor_status tor_eval_units_impl(tor_ctx* ctx, int n, const tor_c128* O, int ld, double* partials, size_t partials_len,
                           tor_result* out) {
   if (!ctx || !out || !partials || n < 1 || n > 64) return TOR_EINVAL;
@@ -1268,6 +1462,44 @@ tor_status tor_poll(tor_ctx* ctx, uint64_t ticket, tor_result* out, double timeo
   ctx->reqs.erase(it);
   delete r;
   return out->status;
+}
+
+tor_status tor_poll_any(tor_ctx* ctx, const uint64_t* tickets, int count, double timeout_s, int* index,
+                        tor_result* out) {
+  if (!ctx || !out || !index || count < 1 || !tickets) return TOR_EINVAL;
+  std::unique_lock<std::mutex> lk(ctx->q_mu);
+  std::vector<Request*> rs((size_t)count);
+  for (int i = 0; i < count; ++i) {
+    auto it = ctx->reqs.find(tickets[i]);
+    if (it == ctx->reqs.end()) return TOR_EINVAL;
+    rs[i] = it->second;
+  }
+  int hit = -1;
+  auto any_done = [&] {
+    for (int i = 0; i < count; ++i)
+      if (rs[i]->done) {
+        hit = i;
+        return true;
+      }
+    return false;
+  };
+  if (!any_done()) {
+    if (timeout_s == 0) return TOR_EAGAIN;
+    if (timeout_s < 0) ctx->done_cv.wait(lk, any_done);
+    else if (!ctx->done_cv.wait_for(lk, std::chrono::duration<double>(timeout_s), any_done)) return TOR_EAGAIN;
+  }
+  *index = hit;
+  *out = rs[hit]->res;
+  ctx->reqs.erase(tickets[hit]);
+  delete rs[hit];
+  return out->status;
+}
+
+tor_status tor_memory(tor_ctx* ctx, size_t* held, size_t* budget) {
+  if (!ctx) return TOR_EINVAL;
+  if (held) *held = (size_t)std::max(0ll, ctx->dev_held.load());
+  if (budget) *budget = ctx->cfg.mem_budget;
+  return TOR_OK;
 }
 
 tor_status tor_serving_stats(tor_ctx* ctx, long long* served, long long* batches, long long* queued) {
@@ -1392,6 +1624,11 @@ static tor_status tor_session_create_impl(tor_ctx* ctx, int n_total, const tor_c
   s->logdet_sigma.assign(N + 1, 0.0L);
   for (int j = 1; j <= N; ++j) s->logdet_sigma[j] = s->logdet_sigma[j - 1] - logd[j];
   cudaSetDevice(ctx->cfg.device);
+  if (ctx->cfg.mem_budget && (size_t)std::max(0ll, ctx->dev_held.load()) + (size_t)tot * 16 > ctx->cfg.mem_budget) {
+    delete s;
+    return TOR_ENOMEM;
+  }
+  s->d_O.acct = &ctx->dev_held;
   cudaError_t e = s->d_O.ensure((size_t)tot * 16, &s->gen);
   if (e == cudaSuccess) e = cudaMemcpy(s->d_O.p, host.data(), (size_t)tot * 16, cudaMemcpyHostToDevice);
   if (e != cudaSuccess) {
@@ -1439,6 +1676,24 @@ void tor_session_destroy(tor_session* s) {
   cudaSetDevice(s->device);
   s->d_O.release();
   delete s;
+}
+
+tor_status tor_session_marginal_matrix(tor_session* s, int j, tor_c128* out, int ld) {
+  if (!s || !out || j < 1 || j > s->N || ld < 2 * j) return TOR_EINVAL;
+  return guarded([&] {
+    const int mj = 2 * j;
+    std::vector<tor_c128> pairs((size_t)mj * mj);
+    cudaSetDevice(s->device);
+    cudaError_t e = cudaMemcpy(pairs.data(), (const double2*)s->d_O.p + s->off[j], pairs.size() * 16,
+                               cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(s->ctx, e, "session matrix copy");
+    // resident copies are in pairs order; hand the caller its context's layout
+    const bool block = !s->ctx || s->ctx->cfg.layout == TOR_LAYOUT_BLOCK;
+    auto dst = [&](int r) { return block ? (r >> 1) + (r & 1) * j : r; };
+    for (int a = 0; a < mj; ++a)
+      for (int b = 0; b < mj; ++b) out[(size_t)dst(a) * ld + dst(b)] = pairs[(size_t)a * mj + b];
+    return TOR_OK;
+  });
 }
 
 }  // extern "C"

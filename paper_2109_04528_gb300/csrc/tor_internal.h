@@ -43,7 +43,7 @@ enum { FLAG_NOTPD = 1, FLAG_NOTHERM = 2, FLAG_NONFINITE = 4, FLAG_REAL = 8 };
 // (task-node) scratch: one complex entry.
 constexpr int kLaneEntryBytes = 8 + 16, kLaneEntryBytesExt = 16 + 32;
 constexpr int kWarpEntryBytes = 16, kWarpEntryBytesExt = 32;
-enum { ABORT_TIMEOUT = 1, ABORT_CANCEL = 2 };
+enum { ABORT_TIMEOUT = 1, ABORT_CANCEL = 2, ABORT_NOSLOT = 4 };
 
 struct UnitsParams {
   const MatDesc* mats;
@@ -64,6 +64,15 @@ struct UnitsParams {
                                // relaunches the kernel, which continues from the ticket
   int* abort_word;             // ABORT_* bits set by the kernel
   int ext;                     // 1: launch k_units_ext (double-double entries)
+  // Non-persistent launch (one_task = 1): the grid has a warp per task and every
+  // warp takes one task, so blocks end all through the job and the block slots
+  // they free go to whichever kernel waits -- a higher-priority stream's first.
+  // A block then takes its warps' scratch from the slot it claims in slot_pool
+  // (one bit per resident block, slot_words words; bits past the resident count
+  // are preset) and gives the slot back when it ends.
+  int one_task;
+  unsigned* slot_pool;
+  int slot_words;
 };
 
 struct ResultRec {

@@ -548,12 +548,47 @@ constexpr int kUnitsThreads = 128;
 // area and an SC area side by side, each lane-interleaved in its own entry
 // size, because the lanes of one task (p < 5) may take different arithmetic;
 // its task-node scratch (p >= 5: one matrix, one arithmetic) is sized for SC.
+// Claims a free bit of the slot pool (one bit per resident block of a
+// non-persistent launch): the slot whose scratch the block's warps use.  At most
+// that many blocks of the launch are resident at once, so a free bit exists;
+// the search is bounded all the same (-1 if it finds none).
+__device__ __noinline__ int claim_slot(unsigned* pool, int words, int start) {
+  // a slot released by a block that has just ended may not be visible yet:
+  // pass over the pool up to 4096 times, pausing between passes (~ms in all)
+  for (int it = 0; it < 4096 * words; ++it) {
+    if (it && it % words == 0) __nanosleep(256);
+    const int w = (start + it) % words;
+    unsigned cur = atomicOr(&pool[w], 0u);
+    for (int tries = 0; tries < 33 && cur != 0xffffffffu; ++tries) {
+      const int b = __ffs(~cur) - 1;
+      const unsigned old = atomicOr(&pool[w], 1u << b);
+      if (!(old & (1u << b))) return w * 32 + b;
+      cur = old | (1u << b);
+    }
+  }
+  return -1;
+}
+
 template <class SR, class SC>
 __device__ __forceinline__ void units_loop(const UnitsParams& prm) {
   using TR = typename SR::T;
   using TC = typename SC::T;
   const int lane = threadIdx.x & (kWarp - 1);
-  const long long gw = (long long)blockIdx.x * (blockDim.x / kWarp) + threadIdx.x / kWarp;
+  __shared__ int s_slot;
+  long long blk = blockIdx.x;
+  if (prm.one_task) {
+    if (threadIdx.x == 0) {
+      s_slot = claim_slot(prm.slot_pool, prm.slot_words, (int)(blockIdx.x % prm.slot_words));
+      __threadfence();  // the previous holder's stores (fenced before its release) precede ours
+    }
+    __syncthreads();
+    if (s_slot < 0) {  // no slot (cannot happen within the occupancy bound): the job reports a failure
+      if (threadIdx.x == 0) atomicOr(prm.abort_word, ABORT_NOSLOT);
+      return;
+    }
+    blk = s_slot;
+  }
+  const long long gw = blk * (blockDim.x / kWarp) + threadIdx.x / kWarp;
   char* lreg_r = (char*)prm.lane_scratch + gw * kWarp * prm.lane_elems * (long long)(sizeof(TR) + sizeof(TC));
   char* lreg_c = lreg_r + (long long)kWarp * prm.lane_elems * (long long)sizeof(TR);
   char* wreg = (char*)prm.warp_scratch + gw * prm.warp_elems * (long long)sizeof(TC);
@@ -579,6 +614,12 @@ __device__ __forceinline__ void units_loop(const UnitsParams& prm) {
       run_task_lanes_any<SR, SC>(prm, T, lane, lreg_r, lreg_c);
     }
     __syncwarp();
+    if (prm.one_task) break;
+  }
+  if (prm.one_task) {  // every warp of the block is done with the slot's scratch: give it back
+    __threadfence();  // this thread's scratch stores are performed before the slot can be reused
+    __syncthreads();
+    if (threadIdx.x == 0) atomicAnd(&prm.slot_pool[s_slot >> 5], ~(1u << (s_slot & 31)));
   }
 }
 

@@ -2,8 +2,9 @@
 while they run (pre-reserved device pools, latency-critical loops where an
 allocation would synchronise the device, plugins restricted to start-up
 allocation).  It keeps every intermediate buffer in a static device array, so
-this test checks that it gives the same answers as tor_eval, on two calls in
-a row that share that array, and that it refuses sizes it has no room for.
+this test checks that it gives the same answers as tor_eval and as the CPU
+oracle, on two calls in a row that share that array, and that it refuses sizes
+it has no room for.
 
 The test file is named so that pytest collects it last; it builds the library
 itself and passes alone in a fresh process as well as after the other tests.
@@ -31,7 +32,7 @@ def _read(torch, out):
     return binding.tor_result.from_buffer_copy(bytes(out.cpu().numpy()))
 
 
-def test_noalloc_matches_tor_eval_twice_in_a_row():
+def test_noalloc_matches_tor_eval_twice_in_a_row(oracle_mod):
     torch = pytest.importorskip("torch")
     build.build()
     lib = binding.load_library()
@@ -42,6 +43,7 @@ def test_noalloc_matches_tor_eval_twice_in_a_row():
     with binding.Context(device=0) as ctx:
         for inst in cases:
             ref = binding.tor_eval(ctx, inst.O)
+            exact = oracle_mod.tor_brute(inst.O)  # binary128, every subset (Eq. tor)
             O_dev = torch.from_numpy(inst.O).to(dev)
             for _ in range(2):  # the second call reuses what the first left in the array
                 st, out = _call(lib, torch, O_dev, inst.n, stream)
@@ -50,6 +52,8 @@ def test_noalloc_matches_tor_eval_twice_in_a_row():
                 assert r.status == binding.TOR_OK and r.n == inst.n
                 assert abs((r.hi - ref.hi) + (r.lo - ref.lo)) <= TOL * ref.abs_sum
                 assert abs(r.abs_sum - ref.abs_sum) <= 1e-12 * ref.abs_sum
+                assert abs((r.hi - exact.hi) + (r.lo - exact.lo)) <= TOL * exact.abs_sum
+                assert abs(r.abs_sum - exact.abs_sum) <= 1e-12 * exact.abs_sum
 
 
 def test_noalloc_rejects_what_does_not_fit():
