@@ -321,7 +321,7 @@ def result_record(name: str, n: int, r64, rx=None, ref=None):
     return rec
 
 
-def large_extras(local, stream, ctx_dev, mats, dmats, res64, ns):
+def large_extras(local, stream, ctx_dev, mats, dmats, res64, ns, peak_ops: float):
     """Beside the timed steps of the n = 30/34 workload: the double-double factor
     on each step matrix, one evaluation each of a lossy and a product state at
     n = 38, sampled oracle units at n = 34, and the error of every result."""
@@ -340,8 +340,10 @@ def large_extras(local, stream, ctx_dev, mats, dmats, res64, ns):
             rx = binding.tor_eval(cx, d)
             ms = cx.last_times()["total_ms"]
             rxs.append(rx)
+            from paper_2109_04528_gb300.flops import path_ops
             out["extended"].append({"n": n, "ms": ms, "terms_per_s": 2.0 ** n / (ms * 1e-3), "path": rx.path,
-                                    "status": rx.status})
+                                    "status": rx.status, "prefix_depth": cx.plan_prefix_depth(n),
+                                    "fp64_instructions_frac": path_ops(n, rx.path) / (ms * 1e-3) / peak_ops})
     for i, (O, n) in enumerate(zip(mats, ns)):
         g = golden_for(O)
         if g is not None:
@@ -995,7 +997,7 @@ def main():
                                              for a, b in zip(last_res, one))
     if args.workload == "large_n30_34" and not args.no_extras and world == 1 and not xf:
         res64 = list(binding.tor_eval_batch(ctx_dev, dmats))  # the timed step's own results
-        line.update(large_extras(local, stream, ctx_dev, mats, dmats, res64, ns))
+        line.update(large_extras(local, stream, ctx_dev, mats, dmats, res64, ns, peak_ops))
         line["batch4096"] = batch_compare(local, stream, steps=5)
         line["serve"] = serve_summary(local, args.serve_high_window, args.serve_sustain_rate)
     elif last_res:
