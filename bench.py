@@ -450,6 +450,25 @@ def batch_compare(local, stream, steps: int):
     return out
 
 
+def sharded_step(binding, ctx, batch, ns, world: int, rank: int):
+    """One step split over the ranks (paper Sec. 4): this rank evaluates its
+    aligned leaf range of every matrix (tor_eval_range), the ranks gather three
+    doubles per matrix, and every rank merges them with the fixed tree, which
+    reproduces one GPU's result bitwise.  Returns (merged results, this rank's
+    units-kernel ms)."""
+    from paper_2109_04528_gb300 import shard
+    res, units = [], 0.0
+    for O, n in zip(batch, ns):
+        lo, cnt = shard.shard_range(binding.tor_plan_leaves(ctx, n), world, rank)
+        res.append(binding.tor_eval_range(ctx, O, lo, cnt))
+        units += ctx.last_times()["units_ms"]
+    got = shard._gather_checked(lambda: [(r.hi, r.lo, r.abs_sum) for r in res])
+    merged = [shard.tree_merge([g[i] for g in got]) for i in range(len(batch))]
+    for r, m in zip(res, merged):
+        r.hi, r.lo, r.abs_sum = m
+    return res, units
+
+
 def launches_per_step(ctx, ns) -> int:
     """Kernels one tor_eval_batch launches: k_intake, k_units, k_reduce, and
     k_reduce_chunks when a matrix has more than 256 reduction leaves (2^(p-5)
@@ -845,20 +864,8 @@ def main():
     paths = {}
     last_res = []
 
-    from paper_2109_04528_gb300 import shard
-
     def sharded_batch(ctx, batch):
-        # this rank's aligned leaf range of every matrix, then one gather and the fixed-tree merge
-        res, units = [], 0.0
-        for O, n in zip(batch, ns):
-            lo, cnt = shard.shard_range(binding.tor_plan_leaves(ctx, n), world, rank)
-            res.append(binding.tor_eval_range(ctx, O, lo, cnt))
-            units += ctx.last_times()["units_ms"]
-        got = shard._gather_checked(lambda: [(r.hi, r.lo, r.abs_sum) for r in res])
-        merged = [shard.tree_merge([g[i] for g in got]) for i in range(len(batch))]
-        for r, m in zip(res, merged):
-            r.hi, r.lo, r.abs_sum = m
-        return res, units
+        return sharded_step(binding, ctx, batch, ns, world, rank)
 
     def timed(ctx, batch, k):
         ms, units_ms = [], []

@@ -1,6 +1,7 @@
 """Host-side helpers of bench.py, on the CPU: the kernel count behind the
-`gpu_launches` claim, the spread sample of the oracle baseline, and the
-Algorithm 2 baseline leg on a small matrix."""
+`gpu_launches` claim, the spread sample of the oracle baseline, the
+Algorithm 2 baseline leg on a small matrix, and the strong-scaling step of
+several ranks (leaf ranges, gather, fixed-tree merge) on two gloo ranks."""
 import pytest
 
 import bench
@@ -42,3 +43,68 @@ def test_cpu_alg2_leg_runs_the_whole_small_sum():
     assert out["unit"] == "subset terms/s" and out["value"] > 0
     assert out["sample"].startswith("all of the 2^12 terms")
     assert out["cores"] >= 1 and "Algorithm 2" in out["kind"]
+
+
+class LeafStub:
+    """Stands in for the binding and a context on the CPU: a matrix with n modes has
+    2^(n-10) reduction leaves with fixed partial sums, and tor_eval_range returns
+    the binary-tree sum of its range's leaves, as the device does."""
+
+    class Res:
+        def __init__(self, t):
+            self.hi, self.lo, self.abs_sum = t
+
+    def __init__(self):
+        self.calls = []
+
+    def leaves(self, n):
+        return [(1.0 + k / 7.0, (k % 5) * 2.0 ** -60, 1.0 + k) for k in range(1 << (n - 10))]
+
+    def tor_plan_leaves(self, ctx, n):
+        return 1 << (n - 10)
+
+    def tor_eval_range(self, ctx, O, lo, cnt):
+        from paper_2109_04528_gb300 import shard
+        self.calls.append((O, lo, cnt))
+        return self.Res(shard.tree_merge(self.leaves(O)[lo:lo + cnt]))
+
+    def last_times(self):
+        return {"units_ms": 1.0}
+
+
+def _sharded_rank_main(rank, world, port, out_dir):
+    import os
+
+    import numpy as np
+    import torch.distributed as dist
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    stub = LeafStub()
+    ns = [14, 16]
+    res, units = bench.sharded_step(stub, stub, ns, ns, world, rank)  # "matrices" are their n here
+    np.save(os.path.join(out_dir, f"s{rank}.npy"),
+            np.array([[r.hi, r.lo, r.abs_sum] for r in res] + [[units, len(stub.calls), stub.calls[1][1]]]))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_sharded_step_two_ranks_equals_one_gpu(tmp_path):
+    # the bench's strong-scaling step on two gloo ranks: each rank evaluates half the leaves
+    # of every matrix, and the merged results equal the single-range tree sum bitwise
+    import socket
+
+    import numpy as np
+    import torch.multiprocessing as mp
+
+    from paper_2109_04528_gb300 import shard
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    port = s.getsockname()[1]
+    s.close()
+    mp.start_processes(_sharded_rank_main, args=(2, port, str(tmp_path)), nprocs=2, join=True, start_method="spawn")
+    stub = LeafStub()
+    want = [shard.tree_merge(stub.leaves(n)) for n in (14, 16)]
+    for rank in range(2):
+        got = np.load(tmp_path / f"s{rank}.npy")
+        assert [tuple(row) for row in got[:2]] == want
+        assert tuple(got[2]) == (2.0, 2, rank * (1 << 5))  # two ranges; n = 16's half starts at leaf 32
