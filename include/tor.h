@@ -154,8 +154,12 @@ tor_status tor_eval_seq(tor_ctx* ctx, int count, const int* n, const tor_c128* c
  * blocks take the SMs that the current one's last tasks leave idle; small
  * requests are batched FIFO into two high-priority lanes, whose blocks take
  * SMs as soon as any block of a large request ends, and may pass large
- * requests that wait.  (Environment, for experiments: TOR_SERVE_SLICE_MS = t
- * makes large requests yield the SMs every t ms; TOR_SERVE_LARGE_LANES = 1..3.)  Each result is bitwise the same as
+ * requests that wait.  The serving thread polls running jobs without sleeping,
+ * and when it goes idle it spins for up to 50 ms before it sleeps, so that a
+ * request arriving soon starts without a thread wake-up (it occupies one host
+ * core meanwhile).  (Environment: TOR_SERVE_IDLE_SPIN_MS sets that spin, 0 =
+ * sleep at once; for experiments TOR_SERVE_SLICE_MS = t makes large requests
+ * yield the SMs every t ms, and TOR_SERVE_LARGE_LANES = 1..3.)  Each result is bitwise the same as
  * tor_eval of the same matrix on the same context.  TOR_EAGAIN if the queue
  * is full. */
 tor_status tor_submit(tor_ctx* ctx, int n, const tor_c128* O, int ld, uint64_t* ticket);

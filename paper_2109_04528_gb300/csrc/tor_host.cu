@@ -236,6 +236,10 @@ struct tor_ctx {
   uint64_t next_ticket = 1;
   std::thread server;
   bool server_started = false, stopping = false;
+  // bumped (under q_mu) by every enqueue and by tor_destroy: an idle serving
+  // thread that spins instead of sleeping watches it without taking the lock
+  std::atomic<unsigned long long> q_events{0};
+  double idle_spin_s = 0.05;  // idle serving thread spins this long before it sleeps (TOR_SERVE_IDLE_SPIN_MS)
   size_t queue_limit = 1 << 20;
   int n_serve_slots = 4;   // large lanes first, then small lanes
   int n_large_slots = 2;   // two large requests in flight: the next one's blocks fill the tail of the current one
@@ -688,19 +692,22 @@ static tor_status slot_record(tor_ctx* ctx, Slot& S, bool timed) {
 }
 
 // Enqueues the prepared job (graph replay when enabled and the shape repeats).
-static tor_status slot_launch(tor_ctx* ctx, Slot& S) {
+static tor_status slot_launch(tor_ctx* ctx, Slot& S, bool graphs) {
   S.cancel_epoch = __atomic_load_n(ctx->h_cancel, __ATOMIC_SEQ_CST);
-  S.graphed = (ctx->cfg.flags & TOR_GRAPHS) != 0;
+  S.graphed = graphs;
   if (!S.graphed) {
     tor_status st = slot_record(ctx, S, true);
     if (st != TOR_OK) return st;
     CK(cudaEventRecord(S.done, S.stream), "event");
     return TOR_OK;
   }
+  // The key holds what the captured pass depends on: launch shapes, copy sizes
+  // and the values passed by value to the kernels.  What the kernels read from
+  // the descriptors (source matrix, its size and layout, mode lists, the
+  // arithmetic) is copied in by the pass itself, so it may differ between replays.
   uint64_t key = mix(0, (uint64_t)S.J);
   for (const MatDesc& D : S.mats)
-    key = mix(key, (uint64_t)D.n | (uint64_t)D.p << 8 | (uint64_t)D.n_src << 16 | (uint64_t)D.layout << 28 |
-                       (uint64_t)(D.modes != nullptr) << 29 | (uint64_t)D.real << 30 | (uint64_t)D.ext << 33);
+    key = mix(key, (uint64_t)D.n | (uint64_t)D.p << 8 | (uint64_t)(D.modes != nullptr) << 29 | (uint64_t)D.ext << 33);
   for (const MatDesc& D : S.mats) key = mix(key, (uint64_t)D.red_lo << 8 ^ (uint64_t)D.red_log2);
   key = mix(key, (uint64_t)S.o_elems);
   key = mix(key, (uint64_t)S.mode_elems);
@@ -731,7 +738,7 @@ static tor_status slot_launch(tor_ctx* ctx, Slot& S) {
       else keep.push_back(g);
     }
     S.graphs.swap(keep);
-    if (S.graphs.size() >= 16) {
+    if (S.graphs.size() >= 64) {
       cudaGraphExecDestroy(S.graphs.front().exec);
       S.graphs.erase(S.graphs.begin());
     }
@@ -799,7 +806,7 @@ static tor_status run_blocking(tor_ctx* ctx, const std::vector<MatIn>& ins, tor_
   tor_status first = slot_prepare(ctx, S, ins, out, unit_partials != nullptr, &any);
   if (!any) return first;
   if (unit_partials && (S.J != 1 || unit_len < 3ull * (1ull << S.mats[0].p))) return TOR_EINVAL;
-  tor_status st = slot_launch(ctx, S);
+  tor_status st = slot_launch(ctx, S, (ctx->cfg.flags & TOR_GRAPHS) != 0);
   if (st != TOR_OK) return st;
   CK(cudaStreamSynchronize(S.stream), "kernel execution");
   tor_status fin = slot_finish(S, out, unit_partials, ctx->last_times);
@@ -989,7 +996,12 @@ static void server_loop(tor_ctx* ctx) {
           res[k].status = TOR_ENOMEM;
         }
       }
-      if (any) {
+      if (any && !large_lane && S.J == 1) {
+        // a lone small request: its pass is replayed from a CUDA graph of its shape
+        // (one launch instead of four copies and three to four kernels)
+        S.t_start = now_s();
+        st = slot_launch(ctx, S, true);
+      } else if (any) {
         S.cancel_epoch = __atomic_load_n(ctx->h_cancel, __ATOMIC_SEQ_CST);
         S.graphed = false;
         S.t_start = now_s();
@@ -1024,6 +1036,15 @@ static void server_loop(tor_ctx* ctx) {
     if (ctx->stopping && !busy && ctx->queue.empty()) return;
     if (!progressed) {
       if (!busy && ctx->queue.empty()) {
+        // idle: spin a while before sleeping, so that a request arriving soon is
+        // taken without the wake-up latency of a sleeping thread
+        if (ctx->idle_spin_s > 0) {
+          const unsigned long long seen = ctx->q_events.load(std::memory_order_acquire);
+          lk.unlock();
+          const double t_end = now_s() + ctx->idle_spin_s;
+          while (ctx->q_events.load(std::memory_order_acquire) == seen && now_s() < t_end) std::this_thread::yield();
+          lk.lock();
+        }
         ctx->q_cv.wait(lk, [&] { return ctx->stopping || !ctx->queue.empty(); });
       } else {
         // jobs in flight: poll their events again at once (a timed wait would
@@ -1089,6 +1110,7 @@ static tor_status enqueue_request(tor_ctx* ctx, Request* r, uint64_t* ticket) {
     ctx->reqs[r->ticket] = r;
     ctx->queue.push_back(r);
     *ticket = r->ticket;
+    ctx->q_events.fetch_add(1, std::memory_order_release);
   }
   ctx->q_cv.notify_one();
   return TOR_OK;
@@ -1224,6 +1246,7 @@ static tor_status tor_create_impl(const tor_config* cfg, tor_ctx** out) {
   if ((e = slot_init(ctx->main, (cudaStream_t)c.stream)) != cudaSuccess) return fail(e, "stream/events");
   slot_account(ctx, ctx->main, false);
   if (const char* v = getenv("TOR_SERVE_SLICE_MS")) ctx->large_slice_ns = (long long)(atof(v) * 1e6);
+  if (const char* v = getenv("TOR_SERVE_IDLE_SPIN_MS")) ctx->idle_spin_s = std::max(0.0, atof(v) * 1e-3);
   if (const char* v = getenv("TOR_SERVE_LARGE_LANES")) ctx->n_large_slots = std::max(1, std::min(3, atoi(v)));
   if ((e = cudaHostAlloc((void**)&ctx->h_cancel, sizeof(int), cudaHostAllocMapped)) != cudaSuccess)
     return fail(e, "cancel flag");
@@ -1248,6 +1271,7 @@ void tor_destroy(tor_ctx* ctx) {
     // requests still queued are dropped (TOR_ECANCELED); jobs on the GPU are asked to stop
     std::lock_guard<std::mutex> lk(ctx->q_mu);
     ctx->stopping = true;
+    ctx->q_events.fetch_add(1, std::memory_order_release);
     for (Request* r : ctx->queue) {
       r->res = tor_result{};
       r->res.n = r->in.n;

@@ -4,15 +4,18 @@ estimate refined by one cubic series step (tor_device.cuh rcp64 / rsqrt64),
 against CUDA's own IEEE division 1.0 / x and rsqrt(x) on the same inputs and
 against the exact values.
 
-Stated bound, checked here: both stay below 1 ulp of the exact result for
-every normal x with a normal result (2^-1022 <= |x| < 2^1022 for the
-reciprocal, positive normal x for the square root), on a log-spaced sweep of
-all exponents, the extreme exponents themselves, and a dense sample of the
-pivot range (1e-3 .. 10).  Derivation: the estimate's relative error is below
-2^-19.9, so the dropped series terms are below 2^-59 relative; with the
-roundings of the refinement that is < 0.6 ulp for the reciprocal and < 0.9 ulp
-for the reciprocal square root (the product x*y is rounded once before the
-residual)."""
+Stated bound, checked here: the reciprocal stays below 0.6 ulp and the
+reciprocal square root at most 1 ulp from the exact result, for every normal
+x with a normal result (2^-1022 <= |x| < 2^1022 for the reciprocal, positive
+normal x for the square root), on a log-spaced sweep of all exponents, the
+extreme exponents themselves, and a dense sample of the pivot range
+(1e-3 .. 10).  Derivation: the estimate's relative error is below 2^-19.9, so
+the dropped series terms are below 2^-59 relative.  The reciprocal's residual
+1 - x y is formed by one FMA, exactly enough, so only the final rounding
+(0.5 ulp) remains; for the square root the product x y is rounded once before
+the residual 1 - (x y) y, which moves the result by up to another 0.5 ulp.
+Measured on a GB300 over 6e5 inputs: 0.506 ulp (0.03 % not correctly
+rounded) and 0.981 ulp (mean 0.28; CUDA's rsqrt: 0.505)."""
 import numpy as np
 import pytest
 
@@ -59,7 +62,7 @@ def test_reciprocal_below_one_ulp(sweep):
     assert np.array_equal(div, 1.0 / x)  # CUDA's division is IEEE round-to-nearest, as numpy's
     exact = np.longdouble(1.0) / x.astype(np.longdouble)
     err = _ulp_err(rcp, exact)
-    assert float(err.max()) < 1.0, (float(err.max()), x[int(err.argmax())])
+    assert float(err.max()) < 0.6, (float(err.max()), x[int(err.argmax())])
 
 
 def test_reciprocal_sqrt_below_one_ulp(sweep):
@@ -67,7 +70,7 @@ def test_reciprocal_sqrt_below_one_ulp(sweep):
     _, _, rs, cuda_rs = binding.tor_check_recip(x)
     exact = np.longdouble(1.0) / np.sqrt(x.astype(np.longdouble))
     err = _ulp_err(rs, exact)
-    assert float(err.max()) < 1.0, (float(err.max()), x[int(err.argmax())])
+    assert float(err.max()) <= 1.0, (float(err.max()), x[int(err.argmax())])
     # CUDA's rsqrt, documented to 1 ulp, on the same sweep
     cuda_err = _ulp_err(cuda_rs, exact)
     assert float(cuda_err.max()) <= 1.0 + 1e-9
