@@ -1016,10 +1016,21 @@ def main():
         line["sharded_equals_one_gpu"] = all((a.hi, a.lo, a.abs_sum) == (b.hi, b.lo, b.abs_sum)
                                              for a, b in zip(last_res, one))
     if args.workload == "large_n30_34" and not args.no_extras and world == 1 and not xf:
+        # nested results beside the timed steps; a failure in one of them is recorded in the
+        # line instead of costing the headline
+        def nested(key, fn):
+            try:
+                got = fn()
+                if key is None:
+                    line.update(got)
+                else:
+                    line[key] = got
+            except Exception as e:  # noqa: BLE001 -- reported in the JSON line
+                line.setdefault("nested_errors", {})[key or "errors_and_extended"] = f"{type(e).__name__}: {e}"
         res64 = list(binding.tor_eval_batch(ctx_dev, dmats))  # the timed step's own results
-        line.update(large_extras(local, stream, ctx_dev, mats, dmats, res64, ns, peak_ops))
-        line["batch4096"] = batch_compare(local, stream, steps=5)
-        line["serve"] = serve_summary(local, args.serve_high_window, args.serve_sustain_rate)
+        nested(None, lambda: large_extras(local, stream, ctx_dev, mats, dmats, res64, ns, peak_ops))
+        nested("batch4096", lambda: batch_compare(local, stream, steps=5))
+        nested("serve", lambda: serve_summary(local, args.serve_high_window, args.serve_sustain_rate))
     elif last_res:
         line["results"] = [result_record(f"n={n}", n, r, None,
                                          ({"hi": g["hi"], "lo": g["lo"], "name": f"binary128 oracle ({g['method']}), stored"}
