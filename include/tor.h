@@ -141,8 +141,8 @@ tor_status tor_eval_batch(tor_ctx* ctx, int count, const int* n, const tor_c128*
  * interpreter between the calls.  Arguments as for tor_eval_batch; ms (may be
  * NULL) receives count host-measured wall times in milliseconds, one per
  * matrix (call entry to return).  Results equal tor_eval_batch's bitwise.
- * This is the baseline a batched launch (Sec. 4's task-parallel evaluation of
- * many matrices) is compared with.  Returns the first error. */
+ * The paper has no counterpart: this is the plain path that a batched launch
+ * of many matrices is compared with.  Returns the first error. */
 tor_status tor_eval_seq(tor_ctx* ctx, int count, const int* n, const tor_c128* const* O, const int* ld,
                         tor_result* out, double* ms);
 
@@ -175,7 +175,8 @@ tor_status tor_poll(tor_ctx* ctx, uint64_t ticket, tor_result* out, double timeo
  * Returns TOR_EAGAIN if none completed in time, TOR_EINVAL if a ticket is
  * unknown or already collected, else the collected request's status.  For a
  * client with many requests in flight, which then sees each completion when
- * it happens rather than in submission order. */
+ * it happens rather than in submission order.  Serving machinery; the paper
+ * has no counterpart. */
 tor_status tor_poll_any(tor_ctx* ctx, const uint64_t* tickets, int count, double timeout_s, int* index,
                         tor_result* out);
 
@@ -185,7 +186,8 @@ tor_status tor_poll_any(tor_ctx* ctx, const uint64_t* tickets, int count, double
  * admits a batch only if the bytes held stay within it: idle slots give their
  * buffers back first, then the batch shrinks, and a request that cannot fit
  * with nothing else running fails with TOR_ENOMEM.  A blocking call over the
- * budget fails with TOR_ENOMEM (it does not take memory from serving slots). */
+ * budget fails with TOR_ENOMEM (it does not take memory from serving slots).
+ * Serving machinery; the paper has no counterpart. */
 tor_status tor_memory(tor_ctx* ctx, size_t* held, size_t* budget);
 
 /* Served requests, completed batches and requests still queued (any may be NULL). */
@@ -218,9 +220,10 @@ void tor_session_destroy(tor_session* s);
 /* Copies the session's resident O^(j) (2j x 2j, the exact matrix every
  * marginal of prefix j reads) to the host buffer out, row-major with leading
  * dimension ld >= 2j, in the layout of the context the session was made on
- * (block if that context is gone).  For checking marginals against another
- * evaluator on identical inputs.  TOR_EINVAL for j outside [1, n_total] or
- * ld < 2j; TOR_ECUDA if the copy fails.  Blocking. */
+ * (block if that context is gone): the sampling matrix of the first j modes'
+ * marginal state (Eq. A applied to Sigma_[j], Sec. 1).  For checking marginals
+ * against another evaluator on identical inputs.  TOR_EINVAL for j outside
+ * [1, n_total] or ld < 2j; TOR_ECUDA if the copy fails.  Blocking. */
 tor_status tor_session_marginal_matrix(tor_session* s, int j, tor_c128* out, int ld);
 
 /* Tor(O^(j)_S) for S = modes[0..k-1] (distinct, each < j, any order), blocking. */
