@@ -193,6 +193,20 @@ def test_admission_by_memory_budget():
         assert st == binding.TOR_ENOMEM
 
 
+@pytest.mark.parametrize("flags", [0, binding.TOR_EXTENDED])
+def test_large_lanes_bitwise_equal_tor_eval(flags):
+    # requests over 2^25 terms take the large lanes, whose k_units launch has a warp
+    # per task and scratch slots claimed from a pool (FP64: 4 blocks per SM; double-
+    # double: 2): two at once, then one behind them, each bitwise its tor_eval result
+    mats = [inputs.lossy_squeezed(26, 70 + i, (0.3, 0.8), (0.3, 0.7)).O for i in range(3)]
+    with binding.Context(device=0, flags=flags) as c:
+        alone = [binding.tor_eval(c, O) for O in mats]
+        tickets = [binding.tor_submit(c, O) for O in mats]
+        for t, a in zip(tickets, alone):
+            st, r = binding.tor_poll(c, t, 300.0)
+            assert st == 0 and same(r, a)
+
+
 def test_memory_held_stays_within_budget():
     # a large request (n = 26, the large lane), then many small batches and another large
     # one: the bytes the context holds (every slot's buffers, sampled while requests run)
