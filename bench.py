@@ -329,6 +329,7 @@ def large_extras(local, stream, ctx_dev, mats, dmats, res64, ns, peak_ops: float
 
     import oracle
     from paper_2109_04528_gb300 import binding
+    from paper_2109_04528_gb300.flops import path_ops
     device = torch.device("cuda", local)
     out = {"results": [], "extended": [], "n38": []}
     # double-double factor (TOR_EXTENDED) on the step's matrices, one timed evaluation each
@@ -340,7 +341,6 @@ def large_extras(local, stream, ctx_dev, mats, dmats, res64, ns, peak_ops: float
             rx = binding.tor_eval(cx, d)
             ms = cx.last_times()["total_ms"]
             rxs.append(rx)
-            from paper_2109_04528_gb300.flops import path_ops
             out["extended"].append({"n": n, "ms": ms, "terms_per_s": 2.0 ** n / (ms * 1e-3), "path": rx.path,
                                     "status": rx.status, "prefix_depth": cx.plan_prefix_depth(n),
                                     "fp64_instructions_frac": path_ops(n, rx.path) / (ms * 1e-3) / peak_ops})
