@@ -108,3 +108,35 @@ def test_sharded_step_two_ranks_equals_one_gpu(tmp_path):
         got = np.load(tmp_path / f"s{rank}.npy")
         assert [tuple(row) for row in got[:2]] == want
         assert tuple(got[2]) == (2.0, 2, rank * (1 << 5))  # two ranges; n = 16's half starts at leaf 32
+
+
+def test_product_closed_form_matches_the_oracle(oracle_mod):
+    # the bench's reference for its n = 38 product state, checked against the binary128
+    # brute force of Eq. (tor) on a small product state of the same recipe
+    inst = inputs.product_state(6, 4242)
+    tor, absum = bench.product_closed_form(inst)
+    r = oracle_mod.tor_brute(inst.O)
+    assert abs(r.tor - tor) <= 1e-13 * abs(tor)
+    assert abs(r.abs_sum - absum) <= 1e-13 * absum
+
+
+def test_result_record_states_errors_against_the_reference():
+    class R:
+        def __init__(self, hi, lo, abs_sum, err_est):
+            self.hi, self.lo, self.abs_sum, self.err_est, self.path = hi, lo, abs_sum, err_est, 1
+
+        @property
+        def tor(self):
+            return self.hi + self.lo
+    r64 = R(1.0e-10, 0.0, 1.0e6, 1.0e-8)
+    rx = R(2.0e-12, 1.0e-29, 1.0e6, 1.0e-20)
+    rec = bench.result_record("m", 20, r64, rx, {"hi": 2.0e-12, "lo": 0.0, "name": "binary128 oracle"})
+    assert rec["kappa"] == 1.0e6 / 2.0e-12
+    assert abs(rec["fp64"]["abs_err"] - (1.0e-10 - 2.0e-12)) <= 1e-25
+    assert rec["fp64"]["within_err_est"] and rec["extended"]["within_err_est"]
+    assert rec["extended"]["abs_err"] == 1.0e-29
+    # against the double-double GPU path, only the FP64 result gets an error (the reference is itself)
+    rec2 = bench.result_record("m", 20, r64, rx, {"hi": rx.hi, "lo": rx.lo, "name": "double-double GPU path",
+                                                  "bound": rx.err_est})
+    assert "abs_err" in rec2["fp64"] and "abs_err" not in rec2["extended"] and rec2["ref_err_bound"] == 1.0e-20
+    assert bench.result_record("m", 20, r64)["ref"] is None
