@@ -199,10 +199,10 @@ def test_graph_replay_and_served_equal_plain(xctx):
         assert st == 0 and (r.hi, r.lo, r.abs_sum) == (p.hi, p.lo, p.abs_sum)
 
 
-@pytest.mark.parametrize("name", ["lossy_n20.json", "lossy_n22.json", "lossy_n24.json"])
+@pytest.mark.parametrize("name", ["lossy_n20.json", "lossy_n22.json", "lossy_n24.json", "lossy_n30.json"])
 def test_golden_full_sum(xctx, name):
-    # n = 20, 22 (full brute force) and 24 (binary128 Algorithm 2) against the oracle's
-    # stored sums, at the double-double bound
+    # n = 20, 22 (full brute force), 24 and 30 (binary128 Algorithm 2) against the
+    # oracle's stored sums, at the double-double bound
     import json
     import os
     with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", name)) as f:

@@ -54,10 +54,10 @@ def test_golden_fixture(ctx):
     assert abs(r.abs_sum - g["abs_sum"]) <= 1e-12 * g["abs_sum"]
 
 
-@pytest.mark.parametrize("name", ["lossy_n20.json", "lossy_n22.json", "lossy_n24.json"])
+@pytest.mark.parametrize("name", ["lossy_n20.json", "lossy_n22.json", "lossy_n24.json", "lossy_n30.json"])
 def test_golden_full_sum(ctx, name):
-    # n = 20 and 22 against the oracle's full brute force, n = 24 (the single-matrix
-    # benchmark's own matrix) against its binary128 Algorithm 2 (stored: minutes of CPU
+    # n = 20 and 22 against the oracle's full brute force, n = 24 and 30 (the benchmark's
+    # own matrices) against its binary128 Algorithm 2 (stored: minutes to hours of CPU
     # work), and prefix units against the stored brute-force unit sums
     with open(os.path.join(HERE, "golden", name)) as f:
         g = json.load(f)

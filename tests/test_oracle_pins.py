@@ -188,7 +188,7 @@ def test_golden_fixture_reproduces(oracle_mod, name):
     assert r.hi == g["tor_hi"] and abs(r.lo - g["tor_lo"]) <= 1e-30 * g["abs_sum"]
 
 
-@pytest.mark.parametrize("name", ["lossy_n20.json", "lossy_n22.json", "lossy_n24.json"])
+@pytest.mark.parametrize("name", ["lossy_n20.json", "lossy_n22.json", "lossy_n24.json", "lossy_n30.json"])
 def test_large_golden_units_reproduce(oracle_mod, name):
     # the full sums over 2^20 .. 2^24 subsets take minutes; the stored prefix units
     # (2^12 .. 2^14 subsets each, brute force) are recomputed here
