@@ -152,6 +152,46 @@ def test_poll_any_collects_each_ticket_once(ctx):
     assert st == binding.TOR_EINVAL and r is None
 
 
+def test_eval_seq_reports_per_matrix_errors(ctx):
+    # an empty matrix (Tor = 1) and a non-Hermitian one among good ones: each result has its
+    # own status and the call returns the first error, like tor_eval_batch
+    good = inputs.lossy_squeezed(6, 31, (0.5, 1.2), 0.4).O
+    bad = good.copy()
+    bad[0, 1] += 1e-3
+    seq, ms = binding.tor_eval_seq(ctx, [good, np.zeros((0, 0), dtype=np.complex128), bad, good], check=False)
+    assert [r.status for r in seq] == [0, 0, binding.TOR_ENOTHERM, 0]
+    assert seq[1].tor == 1.0 and same(seq[0], seq[3])
+    with pytest.raises(binding.TorError):
+        binding.tor_eval_seq(ctx, [good, bad])
+
+
+def test_poll_any_without_waiting_and_unknown_tickets(ctx):
+    big = inputs.config_single(30).O  # ~65 ms of GPU work
+    t = binding.tor_submit(ctx, big)
+    st, k, r = binding.tor_poll_any(ctx, [t], 0.0)
+    assert st == binding.TOR_EAGAIN and k < 0 and r is None
+    st, k, r = binding.tor_poll_any(ctx, [t], 60.0)
+    assert st == 0 and k == 0 and r.n == 30
+    st, k, r = binding.tor_poll_any(ctx, [t, 10 ** 9], 0.0)
+    assert st == binding.TOR_EINVAL
+
+
+def test_memory_counts_sessions_and_refuses_over_budget():
+    inst = inputs.lossy_squeezed(40, 5, (0.5, 1.2), 0.3)
+    session_bytes = 16 * sum(4 * j * j for j in range(1, 41))
+    with binding.Context(device=0, mem_budget=session_bytes + (1 << 20)) as c:
+        held0, budget = c.memory()
+        assert budget == session_bytes + (1 << 20)
+        s = binding.Session(c, inst.sigma)
+        held1, _ = c.memory()
+        assert held1 - held0 == session_bytes
+        with pytest.raises(binding.TorError) as e:
+            binding.Session(c, inst.sigma)  # a second copy does not fit
+        assert e.value.status == binding.TOR_ENOMEM
+        s.close()
+        assert c.memory()[0] == held0
+
+
 def test_same_alone_and_in_the_mix(ctx):
     rng = np.random.default_rng(8)
     mats = [inputs.lossy_squeezed(int(k), 1000 + i, (0.5, 1.2), 0.4).O for i, k in enumerate(rng.integers(1, 23, 60))]
