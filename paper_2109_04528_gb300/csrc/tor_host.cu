@@ -649,6 +649,7 @@ static tor_status rec_units(tor_ctx* ctx, Slot& S, long long slice_ns, bool one_
   prm.cancel = ctx->d_cancel;
   prm.cancel_epoch = S.cancel_epoch;
   prm.budget_ns = ctx->cfg.timeout_s > 0 ? (long long)(ctx->cfg.timeout_s * 1e9) : 0;
+  prm.job_t0 = (unsigned long long*)((char*)S.p_ctl + 8);  // control words 2..3, zeroed with the pass
   prm.slice_ns = slice_ns;
   prm.ext = (ctx->cfg.flags & TOR_EXTENDED) ? 1 : 0;
   int grid = ctx->grid;

@@ -59,7 +59,10 @@ struct UnitsParams {
   long long warp_elems;
   const volatile int* cancel;  // host-mapped cancel counter
   int cancel_epoch;            // its value when the job started; a change = stop
-  long long budget_ns;         // 0 = no time limit
+  long long budget_ns;         // 0 = no time limit, else counted from the job's start (job_t0)
+  unsigned long long* job_t0;  // zeroed before the job; its first warp stores %globaltimer there, so a
+                               // launch whose warps start late (one task each) or a relaunch keeps the
+                               // job's clock.  Null: each warp counts from its own start
   long long slice_ns;          // > 0: warps stop taking tasks after this long (no abort); the host
                                // relaunches the kernel, which continues from the ticket
   int* abort_word;             // ABORT_* bits set by the kernel

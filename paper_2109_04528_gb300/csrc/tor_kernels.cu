@@ -592,16 +592,21 @@ __device__ __forceinline__ void units_loop(const UnitsParams& prm) {
   char* lreg_r = (char*)prm.lane_scratch + gw * kWarp * prm.lane_elems * (long long)(sizeof(TR) + sizeof(TC));
   char* lreg_c = lreg_r + (long long)kWarp * prm.lane_elems * (long long)sizeof(TR);
   char* wreg = (char*)prm.warp_scratch + gw * prm.warp_elems * (long long)sizeof(TC);
-  const unsigned long long t0 = global_ns();
+  const unsigned long long t0 = global_ns();  // this launch's start (time slices)
+  unsigned long long t_job = t0;               // the job's start (time budget)
+  if (lane == 0 && prm.job_t0 && prm.budget_ns > 0) {
+    const unsigned long long first = atomicCAS(prm.job_t0, 0ull, t0);
+    if (first) t_job = first;
+  }
   for (;;) {
     unsigned t = 0xffffffffu;
     if (lane == 0) {
       int ab = 0;
-      const long long el = (long long)(global_ns() - t0);
+      const unsigned long long now = global_ns();
       if (*prm.cancel != prm.cancel_epoch) ab = ABORT_CANCEL;
-      else if (prm.budget_ns > 0 && el > prm.budget_ns) ab = ABORT_TIMEOUT;
+      else if (prm.budget_ns > 0 && (long long)(now - t_job) > prm.budget_ns) ab = ABORT_TIMEOUT;
       if (ab) atomicOr(prm.abort_word, ab);
-      else if (*(volatile int*)prm.abort_word == 0 && !(prm.slice_ns > 0 && el > prm.slice_ns))
+      else if (*(volatile int*)prm.abort_word == 0 && !(prm.slice_ns > 0 && (long long)(now - t0) > prm.slice_ns))
         t = atomicAdd(prm.ticket, 1u);
     }
     t = __shfl_sync(0xffffffffu, t, 0);

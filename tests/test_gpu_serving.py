@@ -247,6 +247,20 @@ def test_large_lanes_bitwise_equal_tor_eval(flags):
             assert st == 0 and same(r, a)
 
 
+def test_timeout_of_a_served_large_request():
+    # a large request runs as a launch whose warps start one after another (one task
+    # each); the time budget still counts from the job's start, so it stops in time
+    big = inputs.config_single(34).O  # ~1 s of GPU work
+    with binding.Context(device=0, timeout_s=0.05) as c:
+        t0 = time.perf_counter()
+        st, r = binding.tor_poll(c, binding.tor_submit(c, big), 60.0)
+        assert st == binding.TOR_ETIMEOUT and r.status == binding.TOR_ETIMEOUT
+        assert time.perf_counter() - t0 < 0.6
+        small = inputs.lossy_squeezed(8, 3, (0.5, 1.2), 0.4).O  # the context is still usable
+        st, r = binding.tor_poll(c, binding.tor_submit(c, small), 60.0)
+        assert st == 0
+
+
 def test_memory_held_stays_within_budget():
     # a large request (n = 26, the large lane), then many small batches and another large
     # one: the bytes the context holds (every slot's buffers, sampled while requests run)
