@@ -125,7 +125,10 @@ __device__ __forceinline__ dd_t dd_rsqrt(dd_t a) {
 // ---------------------------------------------------------------------------
 struct XRe {
   using Re = dd_t;
-  static constexpr int kUnrollK = 2;
+  // entry loop of an include from memory not unrolled: measured against 2x, the
+  // same bits, +3.1 % on the complex path (n = 26), +1.0 % on the real path at
+  // n = 16..24, neutral on the n = 30 + 34 step
+  static constexpr int kUnrollK = 1;
   // modes of the register-resident subtrees of the lane walk: 2 (a 3-mode node
   // of double words is 42 doubles, of complex ones 84, which crowds the 255
   // registers; measured with 2 modes: real +6.6 %, complex +22 %)
