@@ -50,6 +50,21 @@ def test_graph_replay_device_inputs():
             assert all(same(x, y) for x, y in zip(a, b))
 
 
+def test_graph_replay_of_marginals_with_other_prefixes():
+    # a captured pass is keyed by launch shapes and copy sizes only: marginals of the same
+    # size k on different prefixes j (other source matrices and mode lists, read through
+    # the descriptors) replay the same graph and must still read their own inputs
+    inst = inputs.lossy_squeezed(12, 41, (0.5, 1.2), 0.4)
+    cases = [(12, [0, 4, 7, 11]), (9, [1, 2, 5, 8]), (12, [3, 6, 9, 10]), (5, [0, 1, 2, 4])]
+    with binding.Context(device=0) as plain, binding.Context(device=0, flags=binding.TOR_GRAPHS) as g:
+        with binding.Session(plain, inst.sigma) as sp, binding.Session(g, inst.sigma) as sg:
+            for rep in range(2):
+                for j, S in cases:
+                    a = binding.tor_eval_marginal(g, sg, j, S)
+                    b = binding.tor_eval_marginal(plain, sp, j, S)
+                    assert same(a, b), (rep, j, S)
+
+
 def test_autotune_and_plan_roundtrip(ctx, oracle_mod, tmp_path):
     with binding.Context(device=0) as c:
         chosen = c.autotune(10, 13, budget_s=3.0)
