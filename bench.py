@@ -441,7 +441,7 @@ def large_extras(local, stream, ctx_dev, mats, dmats, res64, ns, peak_ops: float
     return out
 
 
-def batch_compare(local, stream, steps: int):
+def batch_compare(local, stream, steps: int, tune_s: float = 15.0):
     """The 4096-matrix batch (k ~ U{4..24} click patterns of a 100-mode state):
     one batched launch, its CUDA-graph replay, and the plain path (one tor_eval
     per matrix, looped in C by tor_eval_seq), all device-resident."""
@@ -482,6 +482,22 @@ def batch_compare(local, stream, steps: int):
         ms, res_g = run(c, steps)
         out["graph_replay"] = {"ms_per_batch": statistics.median(ms), "value": terms / (statistics.median(ms) * 1e-3),
                                "unit": "subset terms/s", "steps": steps}
+    # the batch autotuner: prefix depths tuned for this batch's throughput (a bounded budget)
+    with binding.Context(device=local, stream=stream.cuda_stream, flags=binding.TOR_IN_DEVICE) as c:
+        t0 = time.perf_counter()
+        plan = binding.tor_autotune_batch(c, dmats, tune_s)
+        tune_took = time.perf_counter() - t0
+        run(c, 1)
+        ms, _ = run(c, steps)
+        builtin = {}
+        with binding.Context(device=local, flags=binding.TOR_IN_DEVICE) as c0:
+            builtin = {n: c0.plan_prefix_depth(n) for n in sorted(plan)}
+        out["batched_autotuned"] = {"ms_per_batch": statistics.median(ms), "value": terms / (statistics.median(ms) * 1e-3),
+                                    "unit": "subset terms/s", "steps": steps, "tune_s": tune_took,
+                                    "changed_depths": {str(n): [builtin[n], p] for n, p in sorted(plan.items())
+                                                       if p != builtin[n]},
+                                    "what": "tor_autotune_batch (coordinate descent over the sizes' prefix depths, "
+                                            "timing the whole batch), then the same timed batch"}
     with binding.Context(device=local, stream=stream.cuda_stream, flags=binding.TOR_IN_DEVICE) as c:
         binding.tor_eval_seq(c, dmats[:64])
         torch.cuda.synchronize()
@@ -499,6 +515,7 @@ def batch_compare(local, stream, steps: int):
     out["bitwise_equal_batched_graph_plain"] = bool(same)
     out["batched_over_plain"] = out["batched"]["value"] / out["plain_per_matrix"]["value"]
     out["graph_over_plain"] = out["graph_replay"]["value"] / out["plain_per_matrix"]["value"]
+    out["autotuned_over_builtin"] = out["batched_autotuned"]["value"] / out["batched"]["value"]
     return out
 
 

@@ -317,6 +317,21 @@ tor_status tor_last_times(tor_ctx* ctx, double* times);
  * n_hi - n_lo + 1 depths.  Not for contexts created with TOR_IN_DEVICE. */
 tor_status tor_autotune(tor_ctx* ctx, int n_lo, int n_hi, double budget_s, int* chosen);
 
+/* Autotuner for a batch shape: tunes the prefix depths of the sizes in the
+ * batch (n[i], O[i], ld[i] as for tor_eval_batch, in the context's input kind)
+ * for the throughput of the whole batch, which may want other depths than
+ * single matrices of those sizes (larger units cost less per term once many
+ * matrices fill the GPU).  Coordinate descent, the sizes with the most subset
+ * terms first; each trial times the whole batch (best of two after a warm-up),
+ * and a depth moves while the batch gets faster by more than 0.5 %.  Spends
+ * about budget_s seconds (at least one trial).  chosen (may be NULL) receives
+ * count depths, one per matrix.  The depths stay in the context's plan (save
+ * them with tor_plan_save); results change in rounding with the depth.  The
+ * paper has no counterpart (its decomposition is the uneven first loop of
+ * Algorithm 2, Sec. 4). */
+tor_status tor_autotune_batch(tor_ctx* ctx, int count, const int* n, const tor_c128* const* O, const int* ld,
+                              double budget_s, int* chosen);
+
 /* Writes / reads the context's prefix-depth table (text: "n p" per line,
  * plus the resident warp count it was tuned for).  tor_plan_load rejects a
  * table tuned for a different number of resident warps with TOR_EINVAL.

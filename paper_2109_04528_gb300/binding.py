@@ -26,7 +26,7 @@ TOR_SESSION_SIGMA, TOR_SESSION_O = 0, 1
 EXPORTS = ["tor_config_default", "tor_create", "tor_destroy", "tor_eval", "tor_eval_batch", "tor_submit",
            "tor_poll", "tor_poll_any", "tor_cancel", "tor_strerror", "tor_last_error", "tor_plan_prefix_depth",
            "tor_set_prefix_depth", "tor_eval_units", "tor_last_times", "tor_probe_fp64", "tor_check_recip",
-           "tor_eval_noalloc", "tor_autotune", "tor_plan_save", "tor_plan_load", "tor_serving_stats", "tor_memory",
+           "tor_eval_noalloc", "tor_autotune", "tor_autotune_batch", "tor_plan_save", "tor_plan_load", "tor_serving_stats", "tor_memory",
            "tor_session_create", "tor_session_destroy", "tor_eval_marginal", "tor_submit_marginal",
            "tor_session_marginal_matrix", "tor_eval_seq", "tor_plan_leaves", "tor_eval_range", "tor_sample"]
 TOR_NOALLOC_MAX_N = 16
@@ -113,6 +113,7 @@ def load_library():
     lib.tor_check_recip.argtypes = [c_int, c_int, P(c_double), P(c_double)]
     lib.tor_eval_noalloc.argtypes = [c_int, c_int, c_void_p, c_int, c_int, c_void_p, c_void_p]
     lib.tor_autotune.argtypes = [c_void_p, c_int, c_int, c_double, P(c_int)]
+    lib.tor_autotune_batch.argtypes = [c_void_p, c_int, P(c_int), P(c_void_p), P(c_int), c_double, P(c_int)]
     lib.tor_plan_save.argtypes = [c_void_p, ctypes.c_char_p]
     lib.tor_plan_load.argtypes = [c_void_p, ctypes.c_char_p]
     LL = ctypes.c_longlong
@@ -311,6 +312,24 @@ def tor_eval_seq(ctx: Context, mats, check: bool = True):
         raise TorError(st, ctx.last_error() or "tor_eval_seq")
     del args
     return [TorResult.of(r) for r in res], ms
+
+
+def tor_autotune_batch(ctx: Context, mats, budget_s: float = 10.0):
+    """Tune the prefix depths of the batch's sizes for the throughput of the whole
+    batch (tor_autotune_batch); returns {n: p}.  The depths stay in ctx's plan."""
+    k = len(mats)
+    if k == 0:
+        return {}
+    args = [_matrix_args(ctx, O) for O in mats]
+    ns = (ctypes.c_int * k)(*[a[1] for a in args])
+    lds = (ctypes.c_int * k)(*[a[2] for a in args])
+    ptrs = (ctypes.c_void_p * k)(*[a[3] for a in args])
+    chosen = (ctypes.c_int * k)()
+    st = ctx._lib.tor_autotune_batch(ctx.handle, k, ns, ptrs, lds, budget_s, chosen)
+    if st != TOR_OK:
+        raise TorError(st, ctx.last_error() or "tor_autotune_batch")
+    del args
+    return {int(ns[i]): int(chosen[i]) for i in range(k)}
 
 
 def tor_eval_units(ctx: Context, O):

@@ -1958,6 +1958,86 @@ tor_status tor_autotune(tor_ctx* ctx, int n_lo, int n_hi, double budget_s, int* 
   return guarded([&] { return tor_autotune_impl(ctx, n_lo, n_hi, budget_s, chosen); });
 }
 
+// Batch autotuner: coordinate descent over the prefix depths of the batch's
+// sizes, largest total work first, timing the whole batch (one tor_eval_batch
+// per trial, best of two after a warm-up).  A depth moves while the batch gets
+// faster by more than 0.5 %; the search ends when no size improves or the
+// budget is spent.
+static tor_status tor_autotune_batch_impl(tor_ctx* ctx, int count, const int* n, const tor_c128* const* O,
+                                          const int* ld, double budget_s, int* chosen) {
+  if (!ctx || count < 1 || !n || !O || budget_s <= 0) return TOR_EINVAL;
+  std::map<int, double> work;  // size -> subset terms in the batch
+  for (int i = 0; i < count; ++i) {
+    if (n[i] < 1 || n[i] > 64) return TOR_EINVAL;
+    work[n[i]] += std::ldexp(1.0, n[i]);
+  }
+  std::vector<int> sizes;
+  for (const auto& kv : work) sizes.push_back(kv.first);
+  std::stable_sort(sizes.begin(), sizes.end(), [&](int a, int b) { return work[a] > work[b]; });
+  std::vector<tor_result> res((size_t)count);
+  auto time_batch = [&](double* ms) -> tor_status {
+    double best = 1e300;
+    for (int rep = 0; rep < 3; ++rep) {  // the first pass warms up (and grows buffers)
+      tor_status st = tor_eval_batch_impl(ctx, count, n, O, ld, res.data());
+      if (st != TOR_OK) return st;
+      if (rep) best = std::min(best, ctx->last_times[3]);
+    }
+    *ms = best;
+    return TOR_OK;
+  };
+  auto set_p = [&](int nn, int p) {
+    std::lock_guard<std::mutex> lk(ctx->run_mu);
+    ctx->plan[nn] = p;
+  };
+  auto get_p = [&](int nn) {
+    std::lock_guard<std::mutex> lk(ctx->run_mu);
+    return plan_p(ctx, nn);
+  };
+  const double t_end = now_s() + budget_s;
+  double best;
+  tor_status st = time_batch(&best);
+  if (st != TOR_OK) return st;
+  for (int pass = 0; pass < 3 && now_s() < t_end; ++pass) {
+    bool moved = false;
+    for (int nn : sizes) {
+      if (now_s() >= t_end) break;
+      const int p0 = get_p(nn);
+      for (int dir : {-1, +1}) {
+        int p = p0;
+        for (;;) {
+          const int q = p + dir;
+          if (q < 0 || q > std::min(nn - 1, kMaxPrefixDepth) || nn - q > 22 || now_s() >= t_end) break;
+          set_p(nn, q);
+          double t;
+          st = time_batch(&t);
+          if (st != TOR_OK) {
+            set_p(nn, p);
+            return st;
+          }
+          if (t < best * 0.995) {
+            best = t;
+            p = q;
+            moved = true;
+          } else {
+            set_p(nn, p);
+            break;
+          }
+        }
+        if (p != p0) break;  // improved in this direction: the other one starts from worse
+      }
+    }
+    if (!moved) break;
+  }
+  if (chosen)
+    for (int i = 0; i < count; ++i) chosen[i] = get_p(n[i]);
+  return TOR_OK;
+}
+
+tor_status tor_autotune_batch(tor_ctx* ctx, int count, const int* n, const tor_c128* const* O, const int* ld,
+                              double budget_s, int* chosen) {
+  return guarded([&] { return tor_autotune_batch_impl(ctx, count, n, O, ld, budget_s, chosen); });
+}
+
 static tor_status tor_plan_save_impl(tor_ctx* ctx, const char* path) {
   if (!ctx || !path) return TOR_EINVAL;
   FILE* f = fopen(path, "w");

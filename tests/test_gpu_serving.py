@@ -86,6 +86,22 @@ def test_autotune_and_plan_roundtrip(ctx, oracle_mod, tmp_path):
             c.load_plan(str(bad))
 
 
+def test_autotune_batch(oracle_mod):
+    # prefix depths tuned for one batch's throughput: every size of the batch gets a valid
+    # depth, the context keeps them, and results stay within the tolerance of the oracle
+    rng = np.random.default_rng(31)
+    mats = [inputs.lossy_squeezed(int(k), 60 + i, (0.5, 1.2), 0.4).O for i, k in enumerate(rng.integers(10, 17, 40))]
+    with binding.Context(device=0) as c:
+        plan = binding.tor_autotune_batch(c, mats, 3.0)
+        assert set(plan) == {m.shape[0] // 2 for m in mats}
+        for n, p in plan.items():
+            assert 0 <= p < n and n - p <= 22 and c.plan_prefix_depth(n) == p
+        res = binding.tor_eval_batch(c, mats)
+        for O, r in list(zip(mats, res))[:5]:
+            ref = oracle_mod.tor_brute(O)
+            assert r.status == 0 and abs((r.hi - ref.hi) + (r.lo - ref.lo)) <= TOL * ref.abs_sum
+
+
 def marginal_O(sigma, j):
     n = sigma.shape[0] // 2
     idx = np.concatenate([np.arange(j), n + np.arange(j)])
