@@ -521,21 +521,29 @@ def batch_compare(local, stream, steps: int, tune_s: float = 15.0):
 
 def sharded_step(binding, ctx, batch, ns, world: int, rank: int):
     """One step split over the ranks (paper Sec. 4): this rank evaluates its
-    aligned leaf range of every matrix (tor_eval_range), the ranks gather three
-    doubles per matrix, and every rank merges them with the fixed tree, which
-    reproduces one GPU's result bitwise.  Returns (merged results, this rank's
-    units-kernel ms)."""
+    aligned leaf range of every matrix in one launch (tor_eval_range_batch), the
+    ranks gather three doubles per matrix, and every rank merges them with the
+    fixed tree, which reproduces one GPU's result bitwise.  Returns (merged
+    results, this rank's units-kernel ms)."""
     from paper_2109_04528_gb300 import shard
-    res, units = [], 0.0
-    for O, n in zip(batch, ns):
-        lo, cnt = shard.shard_range(binding.tor_plan_leaves(ctx, n), world, rank)
-        res.append(binding.tor_eval_range(ctx, O, lo, cnt))
-        units += ctx.last_times()["units_ms"]
+    ranges = [shard.shard_range(binding.tor_plan_leaves(ctx, n), world, rank) for n in ns]
+    res = binding.tor_eval_range_batch(ctx, batch, ranges)
+    units = ctx.last_times()["units_ms"]
     got = shard._gather_checked(lambda: [(r.hi, r.lo, r.abs_sum) for r in res])
     merged = [shard.tree_merge([g[i] for g in got]) for i in range(len(batch))]
     for r, m in zip(res, merged):
         r.hi, r.lo, r.abs_sum = m
     return res, units
+
+
+def sharded_depths(ctx, ns, world: int):
+    """Prefix depth per size for a matrix split over `world` ranks: the context's
+    plan deepened by log2(world) - 1 levels (none for two ranks), so that each
+    rank's share of a matrix keeps about as many warp tasks per SM as one GPU's
+    whole matrix, up to the limit of 30 and n - 1.  Every rank and the one-GPU
+    check use the same depths, so the merge stays bitwise equal to one GPU."""
+    deeper = max(0, world.bit_length() - 2)
+    return {n: min(30, n - 1, ctx.plan_prefix_depth(n) + deeper) for n in sorted(set(ns))}
 
 
 def launches_per_step(ctx, ns) -> int:
@@ -928,6 +936,10 @@ def main():
             tuned.update(ctx_host.autotune(n, n, args.autotune / len(sizes)))
         ctx_host.save_plan(plan_file)
         ctx_dev.load_plan(plan_file)
+    if sharded and not tuned:
+        for n, p in sharded_depths(ctx_dev, ns, world).items():
+            ctx_dev.set_prefix_depth(n, p)
+            ctx_host.set_prefix_depth(n, p)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=device)
     dfma, fp64_tflops = binding.tor_probe_fp64(local, 0.5)
 

@@ -304,6 +304,20 @@ long long tor_plan_leaves(tor_ctx* ctx, int n);
 tor_status tor_eval_range(tor_ctx* ctx, int n, const tor_c128* O, int ld, long long leaf_lo, long long leaf_count,
                           tor_result* out);
 
+/* A shard of each of several matrices in one launch (one process's share of a
+ * strong-scaled batch, paper Sec. 4): matrix i (n[i], O[i], ld[i] as for
+ * tor_eval_batch; ld may be NULL for 2 n[i]) evaluates the leaves
+ * [leaf_lo[i], leaf_lo[i] + leaf_count[i]) under the rules of tor_eval_range,
+ * or, with leaf_count[i] < 0, all of them (any p).  The warp tasks of all the
+ * ranges share one persistent launch, largest subtrees first, so the tail of
+ * one matrix's range is filled by the others'.  Each out[i] equals the
+ * tor_eval_range (or tor_eval) result of its matrix alone bitwise.  An invalid
+ * range (leaf_count 0, not a power of two, misaligned, beyond the leaves, or
+ * p < 5) sets out[i].status = TOR_EINVAL and the others still run; returns the
+ * first error. */
+tor_status tor_eval_range_batch(tor_ctx* ctx, int count, const int* n, const tor_c128* const* O, const int* ld,
+                                const long long* leaf_lo, const long long* leaf_count, tor_result* out);
+
 /* Device time of the last tor_eval / tor_eval_batch, split by kernel, from CUDA
  * events on the context's stream: [0] intake, [1] units, [2] reduce, [3] total
  * (ms).  With TOR_GRAPHS only the total is measured; [0..2] are -1.  times

@@ -28,7 +28,8 @@ EXPORTS = ["tor_config_default", "tor_create", "tor_destroy", "tor_eval", "tor_e
            "tor_set_prefix_depth", "tor_eval_units", "tor_last_times", "tor_probe_fp64", "tor_check_recip",
            "tor_eval_noalloc", "tor_autotune", "tor_autotune_batch", "tor_plan_save", "tor_plan_load", "tor_serving_stats", "tor_memory",
            "tor_session_create", "tor_session_destroy", "tor_eval_marginal", "tor_submit_marginal",
-           "tor_session_marginal_matrix", "tor_eval_seq", "tor_plan_leaves", "tor_eval_range", "tor_sample"]
+           "tor_session_marginal_matrix", "tor_eval_seq", "tor_plan_leaves", "tor_eval_range",
+           "tor_eval_range_batch", "tor_sample"]
 TOR_NOALLOC_MAX_N = 16
 
 
@@ -129,6 +130,8 @@ def load_library():
     lib.tor_plan_leaves.argtypes = [c_void_p, c_int]
     lib.tor_plan_leaves.restype = LL
     lib.tor_eval_range.argtypes = [c_void_p, c_int, c_void_p, c_int, LL, LL, P(tor_result)]
+    lib.tor_eval_range_batch.argtypes = [c_void_p, c_int, P(c_int), P(c_void_p), P(c_int), P(LL), P(LL),
+                                         P(tor_result)]
     _LIB = lib
     return lib
 
@@ -360,6 +363,28 @@ def tor_eval_range(ctx: Context, O, leaf_lo: int, leaf_count: int) -> TorResult:
         raise TorError(st, ctx.last_error() or "tor_eval_range")
     del keep
     return TorResult.of(res)
+
+
+def tor_eval_range_batch(ctx: Context, mats, ranges, check: bool = True):
+    """One launch over a leaf range of each matrix: ranges[i] = (leaf_lo, leaf_count),
+    or None for the whole matrix.  Returns a list of TorResult."""
+    k = len(mats)
+    if k != len(ranges):
+        raise ValueError("one range per matrix")
+    if k == 0:
+        return []
+    args = [_matrix_args(ctx, O) for O in mats]
+    ns = (ctypes.c_int * k)(*[a[1] for a in args])
+    lds = (ctypes.c_int * k)(*[a[2] for a in args])
+    ptrs = (ctypes.c_void_p * k)(*[a[3] for a in args])
+    los = (ctypes.c_longlong * k)(*[0 if r is None else int(r[0]) for r in ranges])
+    cnts = (ctypes.c_longlong * k)(*[-1 if r is None else int(r[1]) for r in ranges])
+    res = (tor_result * k)()
+    st = ctx._lib.tor_eval_range_batch(ctx.handle, k, ns, ptrs, lds, los, cnts, res)
+    if check and st != TOR_OK:
+        raise TorError(st, ctx.last_error() or "tor_eval_range_batch")
+    del args
+    return [TorResult.of(r) for r in res]
 
 
 def tor_submit(ctx: Context, O) -> int:

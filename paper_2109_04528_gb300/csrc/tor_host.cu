@@ -121,6 +121,7 @@ struct MatIn {
   const int* modes = nullptr;   // host list of n source modes (session marginals), or null
   long long leaf_lo = 0;        // tor_eval_range: first reduction leaf (warp task) to evaluate
   long long leaf_count = -1;    // tor_eval_range: number of leaves; -1 = all
+  bool bad_range = false;       // the caller asked for an empty range (TOR_EINVAL)
   int real_hint = -1;           // 1/0: structured or not, already known (sessions); -1 = detect
 };
 
@@ -340,6 +341,13 @@ static void slot_account(tor_ctx* ctx, Slot& S, bool stream_ordered) {
   }
 }
 
+// A shard of a matrix with prefix depth p: leaf_count a power of two, leaf_lo a
+// multiple of it, inside the 2^(p-5) reduction leaves, and p >= 5.
+static bool range_ok(int p, long long leaf_lo, long long leaf_count) {
+  if (p < 5 || leaf_count < 1 || (leaf_count & (leaf_count - 1)) || leaf_lo < 0 || leaf_lo % leaf_count) return false;
+  return leaf_lo + leaf_count <= (1ll << (p - 5));
+}
+
 // Device bytes of each of a slot's buffers (in Slot::bufs order) that a job of
 // these matrices needs: the sizes slot_prepare allocates.
 struct Needs {
@@ -357,9 +365,10 @@ static Needs job_needs(tor_ctx* ctx, const std::vector<MatIn>& ins, size_t count
   long long J = 0;
   for (size_t i = 0; i < count; ++i) {
     const MatIn& m = ins[i];
-    if (m.n < 1 || m.n > 64) continue;
-    ++J;
+    if (m.n < 1 || m.n > 64 || m.bad_range) continue;
     const int p = plan_p(ctx, m.n);
+    if (m.leaf_count > 0 && !range_ok(p, m.leaf_lo, m.leaf_count)) continue;
+    ++J;
     if (!m.dev && !m.modes) o += 4ll * m.n * m.n;
     if (m.modes) md += m.n;
     bt += tri(m.n);
@@ -433,6 +442,8 @@ static tor_status slot_prepare(tor_ctx* ctx, Slot& S, const std::vector<MatIn>& 
       r.abs_sum = 1.0;
       r.status = TOR_OK;
     } else if (!m.O || (!m.modes && m.ld < 2 * m.n) || (m.modes && m.ld < 2 * m.n_src)) r.status = TOR_EINVAL;
+    else if (m.bad_range || (m.leaf_count > 0 && !range_ok(plan_p(ctx, m.n), m.leaf_lo, m.leaf_count)))
+      r.status = TOR_EINVAL;
     else {
       S.act.push_back(i);
       continue;
@@ -456,6 +467,8 @@ static tor_status slot_prepare(tor_ctx* ctx, Slot& S, const std::vector<MatIn>& 
     D.ext = (ctx->cfg.flags & TOR_EXTENDED) ? 1 : 0;
     D.layout = m.layout;
     D.n_src = m.modes ? m.n_src : m.n;
+    // unit u's partial at part_off + u.  A shard needs all 2^p places too: the 32
+    // units of warp task t are t + l 2^(p-5), spread over the whole range of u.
     D.part_off = S.parts;
     S.parts += 1ll << p;
     D.red_log2 = p >= 5 ? p - 5 : p;
@@ -1427,12 +1440,7 @@ long long tor_plan_leaves(tor_ctx* ctx, int n) {
 static tor_status tor_eval_range_impl(tor_ctx* ctx, int n, const tor_c128* O, int ld, long long leaf_lo, long long leaf_count,
                           tor_result* out) {
   if (!ctx || !out || n < 1 || n > 64) return TOR_EINVAL;
-  const int p = plan_p(ctx, n);
-  if (p < 5) return TOR_EINVAL;
-  const long long L = 1ll << (p - 5);
-  if (leaf_count < 1 || (leaf_count & (leaf_count - 1)) || leaf_lo < 0 || leaf_lo % leaf_count ||
-      leaf_lo + leaf_count > L)
-    return TOR_EINVAL;
+  if (!range_ok(plan_p(ctx, n), leaf_lo, leaf_count)) return TOR_EINVAL;
   std::vector<MatIn> ins(1);
   ins[0].n = n;
   ins[0].O = O;
@@ -1449,6 +1457,34 @@ static tor_status tor_eval_range_impl(tor_ctx* ctx, int n, const tor_c128* O, in
 tor_status tor_eval_range(tor_ctx* ctx, int n, const tor_c128* O, int ld, long long leaf_lo, long long leaf_count,
                           tor_result* out) {
   return guarded([&] { return tor_eval_range_impl(ctx, n, O, ld, leaf_lo, leaf_count, out); });
+}
+
+static tor_status tor_eval_range_batch_impl(tor_ctx* ctx, int count, const int* n, const tor_c128* const* O,
+                                            const int* ld, const long long* leaf_lo, const long long* leaf_count,
+                                            tor_result* out) {
+  if (!ctx || count < 0 || (count > 0 && (!n || !O || !leaf_lo || !leaf_count || !out))) return TOR_EINVAL;
+  std::vector<MatIn> ins(count);
+  const bool dev = (ctx->cfg.flags & TOR_IN_DEVICE) != 0;
+  for (int i = 0; i < count; ++i) {
+    ins[i].n = n[i];
+    ins[i].O = O[i];
+    ins[i].ld = ld ? ld[i] : 2 * n[i];
+    ins[i].n_src = n[i];
+    ins[i].layout = ctx->cfg.layout;
+    ins[i].dev = dev;
+    if (leaf_count[i] >= 0) {  // a shard; slot_prepare flags an invalid range TOR_EINVAL
+      ins[i].leaf_lo = leaf_lo[i];
+      ins[i].leaf_count = leaf_count[i];
+      ins[i].bad_range = leaf_count[i] == 0;
+    }
+  }
+  std::lock_guard<std::mutex> lk(ctx->run_mu);
+  return run_blocking(ctx, ins, out, nullptr, 0);
+}
+
+tor_status tor_eval_range_batch(tor_ctx* ctx, int count, const int* n, const tor_c128* const* O, const int* ld,
+                                const long long* leaf_lo, const long long* leaf_count, tor_result* out) {
+  return guarded([&] { return tor_eval_range_batch_impl(ctx, count, n, O, ld, leaf_lo, leaf_count, out); });
 }
 
 static tor_status tor_submit_impl(tor_ctx* ctx, int n, const tor_c128* O, int ld, uint64_t* ticket) {

@@ -136,6 +136,30 @@ def distributed_tor_batch(ctx, mats, group=None):
     return distributed_batch(evaluate, ns, group)
 
 
+def distributed_tor_many(ctx, mats, group=None):
+    """Tor of each of several matrices with every matrix's leaves split over the
+    ranks of `group` (strong scaling, paper Sec. 4): each rank evaluates its
+    aligned leaf range of every matrix in one launch (tor_eval_range_batch), so
+    one matrix's tail shares the GPU with the others' tasks; one gather of three
+    doubles per matrix and rank, then the fixed tree.  Every rank gets the merged
+    (hi, lo, abs) per matrix, equal bitwise to tor_eval of each matrix alone.
+    If any rank's evaluation fails, every rank raises after the gather."""
+    import torch.distributed as dist
+
+    from . import binding
+    world, rank = dist.get_world_size(group), dist.get_rank(group)
+    ranges = [shard_range(binding.tor_plan_leaves(ctx, m.shape[0] // 2), world, rank) for m in mats]
+
+    def evaluate():
+        res = binding.tor_eval_range_batch(ctx, mats, ranges, check=False)
+        for r in res:
+            if r.status != binding.TOR_OK:
+                raise binding.TorError(r.status, "tor_eval_range_batch")
+        return [(r.hi, r.lo, r.abs_sum) for r in res]
+    got = _gather_checked(evaluate, group)
+    return [tree_merge([g[i] for g in got]) for i in range(len(mats))]
+
+
 def distributed_tor(ctx, O, group=None):
     """Tor of one matrix with its leaves split over the ranks of `group`; every rank
     gets the merged (hi, lo, abs)."""

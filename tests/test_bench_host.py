@@ -29,6 +29,15 @@ def test_launches_per_step_counts_the_first_reduction_stage():
     assert bench.launches_per_step(PlanStub({30: 19, 8: 4}), [8, 30]) == 4
 
 
+def test_sharded_depths_keep_the_tasks_per_rank():
+    # two ranks keep the plan; 4 and 8 ranks deepen it by 1 and 2 levels, within p <= min(30, n - 1)
+    plan = PlanStub({30: 19, 34: 20, 12: 11})
+    assert bench.sharded_depths(plan, [30, 34], 2) == {30: 19, 34: 20}
+    assert bench.sharded_depths(plan, [34, 30, 34], 4) == {30: 20, 34: 21}
+    assert bench.sharded_depths(plan, [30, 34, 12], 8) == {12: 11, 30: 21, 34: 22}
+    assert bench.sharded_depths(PlanStub({40: 29}), [40], 16) == {40: 30}
+
+
 @pytest.mark.parametrize("n,count", [(10, 1), (10, 7), (12, 100), (20, 1000), (8, 1 << 8)])
 def test_spread_sample_covers_the_range(n, count):
     stride, k = bench.spread_sample(n, count)
@@ -47,8 +56,8 @@ def test_cpu_alg2_leg_runs_the_whole_small_sum():
 
 class LeafStub:
     """Stands in for the binding and a context on the CPU: a matrix with n modes has
-    2^(n-10) reduction leaves with fixed partial sums, and tor_eval_range returns
-    the binary-tree sum of its range's leaves, as the device does."""
+    2^(n-10) reduction leaves with fixed partial sums, and tor_eval_range_batch
+    returns the binary-tree sum of each range's leaves, as the device does."""
 
     class Res:
         def __init__(self, t):
@@ -63,10 +72,10 @@ class LeafStub:
     def tor_plan_leaves(self, ctx, n):
         return 1 << (n - 10)
 
-    def tor_eval_range(self, ctx, O, lo, cnt):
+    def tor_eval_range_batch(self, ctx, mats, ranges):
         from paper_2109_04528_gb300 import shard
-        self.calls.append((O, lo, cnt))
-        return self.Res(shard.tree_merge(self.leaves(O)[lo:lo + cnt]))
+        self.calls.append(list(zip(mats, ranges)))
+        return [self.Res(shard.tree_merge(self.leaves(O)[lo:lo + cnt])) for O, (lo, cnt) in zip(mats, ranges)]
 
     def last_times(self):
         return {"units_ms": 1.0}
@@ -83,7 +92,7 @@ def _sharded_rank_main(rank, world, port, out_dir):
     ns = [14, 16]
     res, units = bench.sharded_step(stub, stub, ns, ns, world, rank)  # "matrices" are their n here
     np.save(os.path.join(out_dir, f"s{rank}.npy"),
-            np.array([[r.hi, r.lo, r.abs_sum] for r in res] + [[units, len(stub.calls), stub.calls[1][1]]]))
+            np.array([[r.hi, r.lo, r.abs_sum] for r in res] + [[units, len(stub.calls), stub.calls[0][1][1][0]]]))
     dist.barrier()
     dist.destroy_process_group()
 
@@ -107,7 +116,7 @@ def test_sharded_step_two_ranks_equals_one_gpu(tmp_path):
     for rank in range(2):
         got = np.load(tmp_path / f"s{rank}.npy")
         assert [tuple(row) for row in got[:2]] == want
-        assert tuple(got[2]) == (2.0, 2, rank * (1 << 5))  # two ranges; n = 16's half starts at leaf 32
+        assert tuple(got[2]) == (1.0, 1, rank * (1 << 5))  # one launch; n = 16's half starts at leaf 32
 
 
 def test_product_closed_form_matches_the_oracle(oracle_mod):

@@ -10,17 +10,17 @@ import os
 import numpy as np
 import pytest
 
-from paper_2109_04528_gb300 import inputs, shard
+from paper_2109_04528_gb300 import binding, inputs, shard
 
 N, P = 9, 6  # 2^(P-5) = 2 leaves (warp tasks), each 32 units of 2^(N-P) subsets
 
 
-def task_partial(oracle_mod, O, t):
-    # lane l of task t takes unit u = t | (l << (P-5)); lanes merge by a binary tree over lane index
+def task_partial(oracle_mod, O, t, p=P):
+    # lane l of task t takes unit u = t | (l << (p-5)); lanes merge by a binary tree over lane index
     # (the shape of the device's lane tree, which leaves low parts unnormalised between levels)
     units = []
     for lane in range(32):
-        r = oracle_mod.tor_unit(O, P, t | (lane << (P - 5)), threads=1)
+        r = oracle_mod.tor_unit(O, p, t | (lane << (p - 5)), threads=1)
         units.append((r.hi, r.lo, r.abs_sum))
     return shard.tree_merge(units)
 
@@ -216,3 +216,72 @@ def test_failure_on_one_rank_raises_on_every_rank(tmp_path):
         got = np.load(tmp_path / f"f{rank}.npy")
         assert tuple(got[:2]) == (binding.TOR_ETIMEOUT, binding.TOR_ENOTPD)
         assert tuple(got[2:]) == (1.0, 0.0, 2.0)
+
+
+MANY = [(9, 6, 1234), (10, 7, 77)]  # (n, p, seed): 2 and 4 reduction leaves
+
+
+class _Res:
+    def __init__(self, t, status=0):
+        (self.hi, self.lo, self.abs_sum), self.status = t, status
+
+
+def _many_rank_main(rank, world, port, out_dir, fail_rank):
+    import torch.distributed as dist
+
+    import oracle
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    depth = {n: p for n, p, _ in MANY}
+    calls = []
+
+    def eval_range_batch(ctx, mats, ranges, check=True):  # the device's leaf sums, from the oracle
+        calls.append(list(ranges))
+        out = []
+        for O, (lo, cnt) in zip(mats, ranges):
+            p = depth[O.shape[0] // 2]
+            out.append(_Res(shard.tree_merge([task_partial(oracle, O, t, p) for t in range(lo, lo + cnt)]),
+                            binding.TOR_ENOTPD if rank == fail_rank else 0))
+        return out
+    binding.tor_plan_leaves = lambda ctx, n: 1 << (depth[n] - 5)
+    binding.tor_eval_range_batch = eval_range_batch
+    mats = [inputs.lossy_squeezed(n, seed, (0.5, 1.2), 0.4).O for n, _, seed in MANY]
+    try:
+        got = shard.distributed_tor_many(None, mats)
+        status = 0
+    except binding.TorError as e:
+        got, status = [(0.0, 0.0, 0.0)] * len(mats), e.status
+    np.save(os.path.join(out_dir, f"many{rank}.npy"),
+            np.array([list(g) for g in got] + [[status, len(calls), calls[0][1][0]]]))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("fail_rank", [-1, 1])
+def test_many_matrices_sharded_in_one_launch_per_rank(oracle_mod, tmp_path, fail_rank):
+    # distributed_tor_many on two gloo ranks: one range call per rank covering every
+    # matrix; the merged results equal the single-process tree of all leaves bitwise
+    # and the oracle's full sum; a failed result on one rank raises on both
+    import socket
+
+    import torch.multiprocessing as mp
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    port = s.getsockname()[1]
+    s.close()
+    mp.start_processes(_many_rank_main, args=(2, port, str(tmp_path), fail_rank), nprocs=2, join=True,
+                       start_method="spawn")
+    rows = [np.load(tmp_path / f"many{r}.npy") for r in range(2)]
+    for rank, got in enumerate(rows):
+        status, ncalls, lo1 = got[-1]
+        assert ncalls == 1 and lo1 == rank * 2  # the n = 10 matrix's 4 leaves: 2 per rank
+        if fail_rank >= 0:
+            assert status == binding.TOR_ENOTPD
+            continue
+        assert status == 0
+        for (n, p, seed), g in zip(MANY, got[:-1]):
+            O = inputs.lossy_squeezed(n, seed, (0.5, 1.2), 0.4).O
+            single = shard.tree_merge([task_partial(oracle_mod, O, t, p) for t in range(1 << (p - 5))])
+            assert tuple(g) == tuple(single)
+            full = oracle_mod.tor_brute(O)
+            assert abs((g[0] - full.hi) + (g[1] - full.lo)) <= 1e-25 * full.abs_sum
