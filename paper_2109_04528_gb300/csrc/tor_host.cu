@@ -842,12 +842,14 @@ static void complete(tor_ctx* ctx, std::vector<Request*>& reqs) {  // caller hol
 // Work of one request in subset terms (2^n).
 static double request_terms(const Request* r) { return std::ldexp(1.0, std::max(0, std::min(r->in.n, 64))); }
 
-// Serving slots: serve[0] is the large lane (one large request at a time, low
-// stream priority, k_units in time slices), the others are small lanes (FIFO
-// batches of small requests, high priority).  A slice boundary lets the
-// pending blocks of a high-priority small batch take the SMs; the large
-// request continues from its task ticket right after, so it is never
-// restarted and its result does not depend on the interruption.
+// Serving slots: serve[0 .. n_large_slots) are the large lanes (one large
+// request each, low stream priority, k_units as non-persistent one-task-per-warp
+// launches, so a high-priority small batch's blocks take SMs as the large
+// request's warps finish their tasks); the others are small lanes (FIFO batches
+// of small requests, high priority).  With large_slice_ns > 0 a large request
+// runs as persistent launches in time slices instead, continuing from its task
+// ticket after each, so it is never restarted and its result does not depend
+// on the interruptions.
 static void server_loop(tor_ctx* ctx) {
   cudaSetDevice(ctx->cfg.device);
   struct InFlight {
