@@ -36,12 +36,26 @@ def _deps():
     return files
 
 
+def _fresh(out: str) -> bool:
+    return os.path.exists(out) and os.path.getmtime(out) >= max(os.path.getmtime(f) for f in _deps())
+
+
 def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) -> str:
     out = library_path()
-    if (not force and not ptxas_info and os.path.exists(out)
-            and os.path.getmtime(out) >= max(os.path.getmtime(f) for f in _deps())):
+    if not force and not ptxas_info and _fresh(out):
         return out
     os.makedirs(BUILD, exist_ok=True)
+    # several processes (ranks of one job) may ask at once: one compiles, the others
+    # wait for its library instead of writing the same objects
+    import fcntl
+    with open(os.path.join(BUILD, ".build.lock"), "w") as lock:
+        fcntl.flock(lock, fcntl.LOCK_EX)
+        if not force and not ptxas_info and _fresh(out):
+            return out
+        return _compile(out, verbose, ptxas_info)
+
+
+def _compile(out: str, verbose: bool, ptxas_info: bool) -> str:
     cc = nvcc()
     common = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE]
     if ptxas_info:
