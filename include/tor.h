@@ -335,9 +335,11 @@ tor_status tor_autotune(tor_ctx* ctx, int n_lo, int n_hi, double budget_s, int* 
  * batch (n[i], O[i], ld[i] as for tor_eval_batch, in the context's input kind)
  * for the throughput of the whole batch, which may want other depths than
  * single matrices of those sizes (larger units cost less per term once many
- * matrices fill the GPU).  Coordinate descent, the sizes with the most subset
- * terms first; each trial times the whole batch (best of two after a warm-up),
- * and a depth moves while the batch gets faster by more than 0.5 %.  Spends
+ * matrices fill the GPU).  Coordinate descent in steps of one level over: the
+ * depths of all sizes together, then each size holding at least a tenth of
+ * the batch's subset terms, then the remaining sizes together; each trial
+ * times the whole batch (best of two after a warm-up), and a coordinate moves
+ * while the batch gets faster by more than 0.5 %.  Spends
  * about budget_s seconds (at least one trial).  chosen (may be NULL) receives
  * count depths, one per matrix.  The depths stay in the context's plan (save
  * them with tor_plan_save); results change in rounding with the depth.  The

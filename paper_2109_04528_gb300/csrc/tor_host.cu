@@ -2031,37 +2031,66 @@ static tor_status tor_autotune_batch_impl(tor_ctx* ctx, int count, const int* n,
     std::lock_guard<std::mutex> lk(ctx->run_mu);
     return plan_p(ctx, nn);
   };
+  // Coordinates of the descent, each a set of sizes whose depths move together by
+  // one level per step: all sizes at once (a batch often wants every unit larger
+  // or smaller, and one size alone moves the batch time less than the threshold),
+  // then each size that holds at least a tenth of the work, then the remaining
+  // sizes as one group.
+  double total = 0;
+  for (const auto& kv : work) total += kv.second;
+  std::vector<std::vector<int>> coords;
+  coords.push_back(sizes);
+  std::vector<int> rest;
+  for (int nn : sizes) {
+    if (work[nn] >= 0.1 * total) coords.push_back({nn});
+    else rest.push_back(nn);
+  }
+  if (!rest.empty() && rest.size() < sizes.size()) coords.push_back(rest);
+  auto valid = [&](int nn, int q) { return q >= 0 && q <= std::min(nn - 1, kMaxPrefixDepth) && nn - q <= 22; };
+  // moves every size of c by dir (sizes already at a limit stay); false if none moved
+  auto shift = [&](const std::vector<int>& c, int dir, std::vector<int>& old) {
+    bool any = false;
+    old.clear();
+    for (int nn : c) {
+      const int p = get_p(nn);
+      old.push_back(p);
+      if (valid(nn, p + dir)) {
+        set_p(nn, p + dir);
+        any = true;
+      }
+    }
+    return any;
+  };
+  auto restore = [&](const std::vector<int>& c, const std::vector<int>& old) {
+    for (size_t k = 0; k < c.size(); ++k) set_p(c[k], old[k]);
+  };
   const double t_end = now_s() + budget_s;
   double best;
   tor_status st = time_batch(&best);
   if (st != TOR_OK) return st;
+  std::vector<int> old;
   for (int pass = 0; pass < 3 && now_s() < t_end; ++pass) {
     bool moved = false;
-    for (int nn : sizes) {
+    for (const std::vector<int>& c : coords) {
       if (now_s() >= t_end) break;
-      const int p0 = get_p(nn);
+      bool improved = false;
       for (int dir : {-1, +1}) {
-        int p = p0;
-        for (;;) {
-          const int q = p + dir;
-          if (q < 0 || q > std::min(nn - 1, kMaxPrefixDepth) || nn - q > 22 || now_s() >= t_end) break;
-          set_p(nn, q);
+        while (now_s() < t_end && shift(c, dir, old)) {
           double t;
           st = time_batch(&t);
           if (st != TOR_OK) {
-            set_p(nn, p);
+            restore(c, old);
             return st;
           }
           if (t < best * 0.995) {
             best = t;
-            p = q;
-            moved = true;
+            improved = moved = true;
           } else {
-            set_p(nn, p);
+            restore(c, old);
             break;
           }
         }
-        if (p != p0) break;  // improved in this direction: the other one starts from worse
+        if (improved) break;  // improved in this direction: the other one starts from worse
       }
     }
     if (!moved) break;
