@@ -287,7 +287,11 @@ static tor_status cuda_fail(tor_ctx* ctx, cudaError_t e, const char* what) {
 // scaled by lw = floor(log2(resident warps)):
 //   small n: units over M = 4 modes (as much parallelism as the tree offers);
 //   then p = lw + 5, about one wave of 2^lw warp tasks;
-//   from n = lw + 16 on, p = lw + 8, about eight waves (room for the tail).
+//   from n = lw + 16 on, p = lw + 8, about eight waves (room for the tail);
+//   units of at most kMaxPlanM modes (2^20 subsets, already far more work per
+//   unit than its root build), so the lane stacks, which grow as M^3, stay
+//   bounded for n > 40 as well.
+constexpr int kMaxPlanM = 20;
 static int default_prefix_depth(int n, int nwarps) {
   int lw = 0;
   while ((2ll << lw) <= std::max(nwarps, 1)) ++lw;
@@ -297,6 +301,7 @@ static int default_prefix_depth(int n, int nwarps) {
   else if (n <= lw + 15) p = lw + 6;
   else if (n <= lw + 20) p = lw + 8;
   else p = lw + 9;
+  p = std::max(p, n - kMaxPlanM);
   return std::max(0, std::min(p, n - 1));
 }
 

@@ -158,3 +158,17 @@ def test_deep_prefix_leaf_at_40_modes_against_the_oracle(oracle_mod, flags):
             ref = shard.tree_merge(units)
             assert abs((r.hi - ref[0]) + (r.lo - ref[1])) <= 1e-10 * ref[2], t
             assert abs(r.abs_sum - ref[2]) <= 1e-12 * ref[2], t
+
+
+def test_built_in_plan_bounds_the_units():
+    # units of at most 20 modes up to n = 50 (then p = 30, the deepest), and the plan
+    # below 41 modes as before: p <= n - 1, leaves = 2^(p-5)
+    with binding.Context(device=0) as c:
+        for n in range(1, 65):
+            p = c.plan_prefix_depth(n)
+            assert 0 <= p <= min(n - 1, 30), n
+            assert n - p <= max(20, n - 30), n
+            if p >= 5:
+                assert binding.tor_plan_leaves(c, n) == 1 << (p - 5)
+        assert c.plan_prefix_depth(38) == c.plan_prefix_depth(34) == 20
+        assert c.plan_prefix_depth(44) == 24 and c.plan_prefix_depth(64) == 30
