@@ -164,7 +164,7 @@ struct Slot {
   // serving state
   cudaEvent_t units_done = nullptr;  // end of a time slice of k_units
   int phase = 0;                     // 0 idle, 1 k_units slice in flight, 2 reduce and copies in flight
-  bool large = false;                // runs one large request, time-sliced, low priority
+  bool large = false;                // a large lane: one large request at a time, low priority
   double t_start = 0;
 
   static constexpr int kBufs = 9;
@@ -283,8 +283,8 @@ static tor_status cuda_fail(tor_ctx* ctx, cudaError_t e, const char* what) {
     if (e_ != cudaSuccess) return cuda_fail(ctx, e_, what); \
   } while (0)
 
-// Built-in plan, the shape the autotuner finds on GB300 (1216 resident warps),
-// scaled by lw = floor(log2(resident warps)):
+// Built-in plan, the shape the autotuner finds on GB300 (2432 resident warps
+// of k_units, 1216 of k_units_ext), scaled by lw = floor(log2(resident warps)):
 //   small n: units over M = 4 modes (as much parallelism as the tree offers);
 //   then p = lw + 5, about one wave of 2^lw warp tasks;
 //   from n = lw + 16 on, p = lw + 8, about eight waves (room for the tail);
