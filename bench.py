@@ -863,6 +863,80 @@ def run_sweep_n(args, world, rank, local):
     return 0
 
 
+ACCURACY_S = (0.2, 0.35, 0.5, 0.75, 1.0, 1.5)
+ACCURACY_N = (12, 16, 20, 24, 28, 32)
+ACCURACY_ORACLE_MAX_N = 16
+
+
+def accuracy_row(n, S, r64, rx, oracle_ref=None, rx_rev=None):
+    """One cell of the error-against-squeezing table: kappa = sum|term| / |Tor| and
+    the relative error of the FP64 and double-double results against the binary128
+    oracle where it runs (n <= ACCURACY_ORACLE_MAX_N), else the FP64 error against
+    the double-double result and the double-double result's own error estimated
+    from a second evaluation on the mode-reversed matrix."""
+    if oracle_ref is not None:
+        ref_hi, ref_lo, ref_name = oracle_ref.hi, oracle_ref.lo, "binary128 oracle"
+    else:
+        ref_hi, ref_lo, ref_name = rx.hi, rx.lo, "double-double GPU path"
+    tref = ref_hi + ref_lo
+    row = {"n": n, "S": S, "ref": ref_name, "tor": tref, "abs_sum": r64.abs_sum,
+           "kappa": r64.abs_sum / abs(tref) if tref else None,
+           "fp64_rel_err": abs((r64.hi - ref_hi) + (r64.lo - ref_lo)) / abs(tref) if tref else None,
+           "fp64_rel_bound": r64.err_est / abs(tref) if tref else None,
+           "ext_rel_bound": rx.err_est / abs(tref) if tref else None}
+    if oracle_ref is not None:
+        row["ext_rel_err"] = abs((rx.hi - ref_hi) + (rx.lo - ref_lo)) / abs(tref) if tref else None
+    elif rx_rev is not None:
+        row["ext_rel_diff_reversed"] = abs((rx.hi - rx_rev.hi) + (rx.lo - rx_rev.lo)) / abs(tref) if tref else None
+    return row
+
+
+def run_accuracy(args, world, rank, local):
+    """The error of the FP64 and double-double paths against the squeezing S of the
+    state (the question of Sec. 5, Fig. 6): lossy squeezed states with r_j ~
+    U[0.8 S, 1.2 S], eta = 0.5 and a Haar unitary, one matrix per (n, S); the
+    binary128 oracle is the reference up to n = 16, the double-double path beyond
+    (its own error estimated by a second evaluation on the mode-reversed matrix)."""
+    if rank != 0:
+        return 0
+    import torch
+
+    import oracle
+    from paper_2109_04528_gb300 import binding, build
+    build.build()
+    oracle.build()
+    device = torch.device("cuda", local)
+    torch.cuda.set_device(device)
+    rows = []
+    with binding.Context(device=local, flags=binding.TOR_IN_DEVICE) as c64, \
+            binding.Context(device=local, flags=binding.TOR_IN_DEVICE | binding.TOR_EXTENDED) as cx:
+        for n in ACCURACY_N:
+            for k, S in enumerate(ACCURACY_S):
+                inst = inputs.lossy_squeezed(n, inputs.SEED_BASE + 5000 + 10 * n + k, (0.8 * S, 1.2 * S), 0.5)
+                d = torch.from_numpy(inst.O).to(device)
+                r64 = binding.tor_eval(c64, d)
+                rx = binding.tor_eval(cx, d)
+                ref = rev = None
+                if n <= ACCURACY_ORACLE_MAX_N:
+                    ref = oracle.tor_brute(inst.O)
+                else:
+                    dr = torch.from_numpy(inputs.permute_modes(inst.O, list(range(n))[::-1])).to(device)
+                    rev = binding.tor_eval(cx, dr)
+                row = accuracy_row(n, S, r64, rx, ref, rev)
+                rows.append(row)
+                print(json.dumps(row), file=sys.stderr, flush=True)
+    out = {"metric": "relative error of Tor", "unit": "|Tor - Tor_ref| / |Tor_ref|", "n_gpus": 1,
+           "higher_is_better": False, "dtype": "f64 and f64x2", "data": "synthetic",
+           "config": {"workload": "accuracy",
+                      "desc": "lossy squeezed, r_j ~ U[0.8 S, 1.2 S], eta = 0.5, Haar U; one matrix per (n, S)",
+                      "S": list(ACCURACY_S), "n": list(ACCURACY_N),
+                      "reference": f"binary128 brute force for n <= {ACCURACY_ORACLE_MAX_N}; the double-double "
+                                   "GPU path beyond, with its second evaluation on the mode-reversed matrix"},
+           "rows": rows}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -905,6 +979,8 @@ def main():
         return run_sample(args, world, rank, local)
     if args.workload == "sweep_n":
         return run_sweep_n(args, world, rank, local)
+    if args.workload == "accuracy":
+        return run_accuracy(args, world, rank, local)
 
     import torch
 

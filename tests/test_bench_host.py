@@ -149,3 +149,17 @@ def test_result_record_states_errors_against_the_reference():
                                                   "bound": rx.err_est})
     assert "abs_err" in rec2["fp64"] and "abs_err" not in rec2["extended"] and rec2["ref_err_bound"] == 1.0e-20
     assert bench.result_record("m", 20, r64)["ref"] is None
+
+
+def test_accuracy_row_states_both_paths_against_the_reference():
+    class R:
+        def __init__(self, hi, lo=0.0, abs_sum=1.0e6, err_est=1.0e-9):
+            self.hi, self.lo, self.abs_sum, self.err_est = hi, lo, abs_sum, err_est
+    r64, rx, ref = R(1.1e-3), R(1.0e-3, 2.0e-20, err_est=1e-21), R(1.0e-3, 1.0e-20)
+    row = bench.accuracy_row(12, 0.2, r64, rx, oracle_ref=ref)
+    assert row["ref"] == "binary128 oracle" and abs(row["kappa"] - 1.0e9) <= 1e-3
+    assert abs(row["fp64_rel_err"] - 0.1) <= 1e-12 and abs(row["ext_rel_err"] - 1e-17) <= 1e-22
+    assert abs(row["fp64_rel_bound"] - 1e-6) <= 1e-18
+    row = bench.accuracy_row(24, 0.2, r64, rx, rx_rev=R(1.0e-3, 5.0e-20))
+    assert row["ref"] == "double-double GPU path" and "ext_rel_err" not in row
+    assert abs(row["ext_rel_diff_reversed"] - 3e-17) <= 1e-22
