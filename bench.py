@@ -397,9 +397,13 @@ def large_extras(local, stream, ctx_dev, mats, dmats, res64, ns, peak_ops: float
     # n = 38: a lossy squeezed state and a product state with a closed form, one evaluation each
     lossy38 = inputs.config_single(38, seed=inputs.SEED_BASE + 1038)
     prod38 = inputs.product_state(38, inputs.SEED_BASE + 2038)
+    parts38 = None
     for name, inst in (("lossy n=38", lossy38), ("product state n=38", prod38)):
         d = torch.from_numpy(inst.O).to(device)
-        r = binding.tor_eval(ctx_dev, d)
+        if inst is lossy38:  # the same launch, with the unit partials copied back for the sampled check
+            r, p38, parts38 = binding.tor_eval_units(ctx_dev, d)
+        else:
+            r = binding.tor_eval(ctx_dev, d)
         ms = ctx_dev.last_times()["total_ms"]
         out["n38"].append({"matrix": name, "ms": ms, "terms_per_s": 2.0 ** 38 / (ms * 1e-3), "status": r.status,
                            "path": r.path, "prefix_depth": ctx_dev.plan_prefix_depth(38)})
@@ -438,6 +442,20 @@ def large_extras(local, stream, ctx_dev, mats, dmats, res64, ns, peak_ops: float
                            "oracle_s": time.perf_counter() - t0,
                            "what": "GPU unit partials (tor_eval_units, the timed launch plan) against the "
                                    "binary128 brute force of the same units"}
+    # the lossy n = 38 evaluation's own units: two with few prefix modes included (their subsets
+    # are small, so the oracle's 2^18 determinants per unit take seconds)
+    if parts38 is not None:
+        checks = []
+        t0 = time.perf_counter()
+        for u in (0, (1 << 3) | (1 << 17)):
+            q = oracle.tor_unit(lossy38.O, p38, u)
+            d = abs((parts38[u][0] - q.hi) + (parts38[u][1] - q.lo))
+            checks.append({"u": u, "abs_err": d, "err_over_abs_sum": d / q.abs_sum,
+                           "pass_1e-10": bool(d <= 1e-10 * q.abs_sum)})
+        out["units_parity_n38"] = {"n": 38, "p": p38, "subsets_per_unit": 1 << (38 - p38), "units": checks,
+                                   "oracle_s": time.perf_counter() - t0,
+                                   "what": "unit partials of the timed lossy n = 38 evaluation against the "
+                                           "binary128 brute force of the same units"}
     return out
 
 
