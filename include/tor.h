@@ -250,8 +250,10 @@ tor_status tor_submit_marginal(tor_ctx* ctx, tor_session* s, int j, int k, const
  *   max_dev   out (may be NULL): the largest |(t0 + t1) / sqrt(det Sigma_[j+1])
  *             - P(S on the first j modes)| / P(...) over samples and steps --
  *             the chain rule's consistency, a rounding-level number.
- * All samples' requests of one step go to the serving loop together (2 count
- * per step).  Each evaluation is exact and costs 2^|S|; patterns with more
+ * One step evaluates the distinct marginals of all samples (samples with the
+ * same clicks so far share theirs; at most 2 count per step) in batched
+ * blocking launches of the context, as tor_eval_batch would, so each t equals
+ * tor_eval_marginal's bitwise.  Each evaluation is exact and costs 2^|S|; patterns with more
  * than 64 clicks return TOR_ETOOBIG.  Under TOR_EXTENDED the t's carry ~106
  * bits, for weakly squeezed states whose Torontonians cancel (Sec. 5).
  * Returns TOR_EINVAL for bad arguments (n_modes > the session's modes, a

@@ -1837,54 +1837,81 @@ tor_status tor_submit_marginal(tor_ctx* ctx, tor_session* s, int j, int k, const
 
 // Threshold-detector sampling by the chain rule: for every sample, mode j is
 // decided from the two continuations of its clicks S so far on the first
-// j + 1 modes, t0 = Tor(O^(j+1)_S) and t1 = Tor(O^(j+1)_{S u {j}}).  All
-// samples' requests of one step go to the serving loop together.
+// j + 1 modes, t0 = Tor(O^(j+1)_S) and t1 = Tor(O^(j+1)_{S u {j}}).  One step
+// evaluates the distinct marginals of all samples (samples that share their
+// clicks so far share them) in batched blocking launches of the context.
+constexpr size_t kSampleBatch = 8192;  // marginals per launch
 static tor_status tor_sample_impl(tor_ctx* ctx, tor_session* s, int count, int n_modes, const double* uniforms,
                       unsigned char* patterns, double* prob, double* max_dev) {
   if (!ctx || !s || s->ctx != ctx || count < 0 || n_modes < 1 || n_modes > s->N) return TOR_EINVAL;
   if (count > 0 && (!uniforms || !patterns)) return TOR_EINVAL;
   for (long long i = 0; i < (long long)count * n_modes; ++i)
     if (!(uniforms[i] >= 0.0 && uniforms[i] < 1.0)) return TOR_EINVAL;
-  std::vector<std::vector<int>> S(count);
+  {
+    std::lock_guard<std::mutex> lq(ctx->q_mu);
+    if (s->closing) return TOR_EINVAL;
+    ++s->blocking;  // the session's matrices stay until the call returns
+  }
+  std::vector<std::vector<int>> S(count);       // clicks so far, ascending
   std::vector<long double> pprev(count, 1.0L);  // P(clicks S on the modes decided so far)
-  std::vector<uint64_t> t0(count), t1(count);
-  std::vector<char> sub0(count), sub1(count);
+  std::vector<int> id0(count), id1(count);
   long double dev = 0.0L;
   tor_status first = TOR_OK;
-  for (int j = 0; j < n_modes && first == TOR_OK; ++j) {
-    for (int i = 0; i < count; ++i) {
-      std::vector<int>& c = S[i];
-      tor_status st = tor_submit_marginal(ctx, s, j + 1, (int)c.size(), c.data(), &t0[i]);
-      sub0[i] = st == TOR_OK;
-      c.push_back(j);
-      tor_status st1 = st == TOR_OK ? tor_submit_marginal(ctx, s, j + 1, (int)c.size(), c.data(), &t1[i]) : st;
-      c.pop_back();
-      sub1[i] = st == TOR_OK && st1 == TOR_OK;
-      if (first == TOR_OK && st1 != TOR_OK) first = st1;
-      if (first != TOR_OK) {  // stop submitting; what was submitted is still collected below
-        for (int k = i + 1; k < count; ++k) sub0[k] = sub1[k] = 0;
-        break;
+  try {
+    for (int j = 0; j < n_modes && first == TOR_OK; ++j) {
+      // the step's distinct marginals: S and S u {j} of every sample
+      std::map<std::vector<int>, int> index;
+      std::vector<const std::vector<int>*> keys;
+      auto add = [&](const std::vector<int>& key) {
+        auto it = index.emplace(key, (int)keys.size()).first;
+        if (it->second == (int)keys.size()) keys.push_back(&it->first);
+        return it->second;
+      };
+      for (int i = 0; i < count; ++i) {
+        id0[i] = add(S[i]);
+        S[i].push_back(j);
+        id1[i] = add(S[i]);
+        S[i].pop_back();
+      }
+      const size_t U = keys.size();
+      std::vector<MatIn> ins(U);
+      std::vector<std::vector<int>> own(U);
+      for (size_t u = 0; u < U && first == TOR_OK; ++u) {
+        const tor_status st = marginal_in(s, j + 1, (int)keys[u]->size(), keys[u]->data(), ins[u], own[u]);
+        if (st != TOR_OK) first = st;
+        ins[u].modes = own[u].empty() ? nullptr : own[u].data();
+      }
+      std::vector<tor_result> res(U);
+      for (size_t b = 0; b < U && first == TOR_OK; b += kSampleBatch) {
+        const size_t e = std::min(U, b + kSampleBatch);
+        std::vector<MatIn> part(ins.begin() + b, ins.begin() + e);
+        std::lock_guard<std::mutex> lk(ctx->run_mu);
+        const tor_status st = run_blocking(ctx, part, res.data() + b, nullptr, 0);
+        if (st != TOR_OK) first = st;
+      }
+      if (first != TOR_OK) break;
+      const long double norm = expl(-0.5L * s->logdet_sigma[j + 1]);  // 1 / sqrt(det Sigma_[j+1])
+      for (int i = 0; i < count; ++i) {
+        const tor_result& r0 = res[id0[i]];
+        const tor_result& r1 = res[id1[i]];
+        const long double a = ((long double)r0.hi + (long double)r0.lo) * norm;
+        const long double b = ((long double)r1.hi + (long double)r1.lo) * norm;
+        if (pprev[i] > 0) dev = std::max(dev, fabsl(a + b - pprev[i]) / pprev[i]);
+        const long double p1 = b / (a + b);
+        const bool click = (long double)uniforms[(size_t)i * n_modes + j] < p1;
+        patterns[(size_t)i * n_modes + j] = click ? 1 : 0;
+        if (click) S[i].push_back(j);
+        pprev[i] = click ? b : a;
       }
     }
-    const long double norm = expl(-0.5L * s->logdet_sigma[j + 1]);  // 1 / sqrt(det Sigma_[j+1])
-    for (int i = 0; i < count; ++i) {
-      tor_result r0{}, r1{};
-      tor_status a0 = sub0[i] ? tor_poll(ctx, t0[i], &r0, -1.0) : TOR_EINVAL;
-      tor_status a1 = sub1[i] ? tor_poll(ctx, t1[i], &r1, -1.0) : TOR_EINVAL;
-      if (!sub0[i] || !sub1[i]) continue;
-      if (first == TOR_OK && a0 != TOR_OK) first = a0;
-      if (first == TOR_OK && a1 != TOR_OK) first = a1;
-      if (first != TOR_OK) continue;
-      const long double a = ((long double)r0.hi + (long double)r0.lo) * norm;
-      const long double b = ((long double)r1.hi + (long double)r1.lo) * norm;
-      if (pprev[i] > 0) dev = std::max(dev, fabsl(a + b - pprev[i]) / pprev[i]);
-      const long double p1 = b / (a + b);
-      const bool click = (long double)uniforms[(size_t)i * n_modes + j] < p1;
-      patterns[(size_t)i * n_modes + j] = click ? 1 : 0;
-      if (click) S[i].push_back(j);
-      pprev[i] = click ? b : a;
-    }
+  } catch (const std::bad_alloc&) {
+    first = TOR_ENOMEM;
   }
+  {
+    std::lock_guard<std::mutex> lq(ctx->q_mu);
+    --s->blocking;
+  }
+  ctx->done_cv.notify_all();
   if (first != TOR_OK) return first;
   if (prob)
     for (int i = 0; i < count; ++i) prob[i] = (double)pprev[i];

@@ -163,3 +163,12 @@ def test_accuracy_row_states_both_paths_against_the_reference():
     row = bench.accuracy_row(24, 0.2, r64, rx, rx_rev=R(1.0e-3, 5.0e-20))
     assert row["ref"] == "double-double GPU path" and "ext_rel_err" not in row
     assert abs(row["ext_rel_diff_reversed"] - 3e-17) <= 1e-22
+
+
+def test_sample_work_counts_each_distinct_marginal_once():
+    import numpy as np
+    pat = np.array([[1, 0, 1], [1, 0, 0], [0, 1, 1]], dtype=np.uint8)
+    terms, evals = bench.sample_work(pat)
+    # step 0: S = {} for all; step 1: {0}, {}; step 2: {0}, {0}, {1} -> {0}, {1}
+    assert evals == 2 * (1 + 2 + 2)
+    assert terms == 3.0 * (1 + (2 + 1) + (2 + 2))
