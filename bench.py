@@ -839,6 +839,30 @@ def run_sample(args, world, rank, local):
            "requested_terms_per_s": float((3.0 * np.exp2(before)).sum()) / el,
            "mean_clicks": float(k.mean()), "max_clicks": int(k.max()),
            "min_log10_prob": float(np.log10(prob.min())), "chain_rule_max_dev": dev}
+    # the plan tuned for the sampler's own batches: tor_autotune_batch on one step's batch (the
+    # distinct marginals of the last step of the patterns just drawn), then the same sampling
+    j = n - 1
+    Oj = sess.marginal_matrix(j + 1)
+    pmats = []
+    for S in sorted({tuple(np.flatnonzero(row[:j])) for row in pat}):
+        pmats += [inputs.submatrix(Oj, S), inputs.submatrix(Oj, S + (j,))]
+    before_plan = {m: ctx.plan_prefix_depth(m) for m in range(1, n + 1)}
+    t0 = time.perf_counter()
+    binding.tor_autotune_batch(ctx, pmats, 10.0)
+    tune_s = time.perf_counter() - t0
+    binding.tor_sample(ctx, sess, u[:16])
+    t0 = time.perf_counter()
+    pat2, prob2, dev2 = binding.tor_sample(ctx, sess, u)
+    el2 = time.perf_counter() - t0
+    out["autotuned"] = {"value": len(u) / el2, "unit": "samples/s", "seconds": el2, "tune_s": tune_s,
+                        "pilot_marginals": len(pmats), "same_patterns": bool(np.array_equal(pat, pat2)),
+                        "max_prob_rel_diff": float(np.max(np.abs(prob2 - prob) / prob)),
+                        "chain_rule_max_dev": dev2,
+                        "changed_depths": {str(m): [before_plan[m], ctx.plan_prefix_depth(m)]
+                                           for m in range(1, n + 1) if ctx.plan_prefix_depth(m) != before_plan[m]},
+                        "what": "tor_autotune_batch (10 s) on the batch of the last chain-rule step of the "
+                                "samples drawn above, then the same samples again"}
+    out["autotuned_over_builtin"] = out["autotuned"]["value"] / out["value"]
     ctx.close()
     sess.close()
     print(json.dumps(out), flush=True)
