@@ -1882,12 +1882,21 @@ static tor_status tor_sample_impl(tor_ctx* ctx, tor_session* s, int count, int n
         ins[u].modes = own[u].empty() ? nullptr : own[u].data();
       }
       std::vector<tor_result> res(U);
-      for (size_t b = 0; b < U && first == TOR_OK; b += kSampleBatch) {
-        const size_t e = std::min(U, b + kSampleBatch);
+      size_t chunk = kSampleBatch;  // halved while a chunk does not fit the memory budget
+      for (size_t b = 0; b < U && first == TOR_OK;) {
+        const size_t e = std::min(U, b + chunk);
         std::vector<MatIn> part(ins.begin() + b, ins.begin() + e);
-        std::lock_guard<std::mutex> lk(ctx->run_mu);
-        const tor_status st = run_blocking(ctx, part, res.data() + b, nullptr, 0);
+        tor_status st;
+        {
+          std::lock_guard<std::mutex> lk(ctx->run_mu);
+          st = run_blocking(ctx, part, res.data() + b, nullptr, 0);
+        }
+        if (st == TOR_ENOMEM && chunk > 1) {
+          chunk /= 2;
+          continue;
+        }
         if (st != TOR_OK) first = st;
+        b = e;
       }
       if (first != TOR_OK) break;
       const long double norm = expl(-0.5L * s->logdet_sigma[j + 1]);  // 1 / sqrt(det Sigma_[j+1])

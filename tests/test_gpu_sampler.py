@@ -133,3 +133,26 @@ def test_arguments(ctx):
         # of a squeezed state
         pat, prob, _ = binding.tor_sample(ctx, sess, np.zeros((1, 5)))
         assert pat.sum() == 5
+
+
+def test_chunks_shrink_under_a_memory_budget():
+    # a budget that holds the fixed scratch and a quarter of what a whole step's 2 x 3000
+    # marginals add to it: the steps are split into smaller launches, the draws are the same
+    inst = inputs.lossy_squeezed(14, 77, (0.5, 1.2), 0.5)
+    u = inputs.rng_for(9).uniform(0.0, 1.0, size=(3000, 14))
+    with binding.Context(device=0) as c, binding.Session(c, inst.sigma) as sess:
+        want = binding.tor_sample(c, sess, u)
+        full = c.memory()[0]
+    kmax = min(14, int(want[0].sum(axis=1).max()) + 1)  # the largest continuation S u {j} evaluated
+    with binding.Context(device=0) as probe, binding.Session(probe, inst.sigma) as sess:
+        # the scratch of the largest marginal and of the largest one-lane-per-unit size (p < 5)
+        for k in sorted({kmax, min(kmax, 8)}):
+            assert binding.tor_eval_marginal(probe, sess, 14, list(range(k))).status == 0
+        fixed = probe.memory()[0]
+    assert full > fixed + (4 << 20), (full, fixed)
+    budget = fixed + (full - fixed) // 4
+    with binding.Context(device=0, mem_budget=budget) as c, binding.Session(c, inst.sigma) as sess:
+        got = binding.tor_sample(c, sess, u)
+        assert c.memory()[0] <= budget
+    assert np.array_equal(got[0], want[0])
+    assert np.array_equal(got[1], want[1])
