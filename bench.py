@@ -459,6 +459,38 @@ def large_extras(local, stream, ctx_dev, mats, dmats, res64, ns, peak_ops: float
     return out
 
 
+def small_batch(local, stream, count: int = 65536, k: int = 8, steps: int = 5):
+    """Many small Torontonians (the small-n regime of the paper's benchmark, where
+    calls, not terms, bound the rate): count k-click patterns of the 100-mode
+    state of the batch workload, as one stacked device tensor with record results
+    (tor_eval_batch_arrays), beside the same matrices as a list of tensors."""
+    import torch
+
+    from paper_2109_04528_gb300 import binding
+    device = torch.device("cuda", local)
+    base = inputs.lossy_squeezed(100, inputs.SEED_BASE + 4, (0.5, 1.2), 0.4).O
+    rng = inputs.rng_for(inputs.SEED_BASE + 45)
+    idx = np.sort(np.argsort(rng.random((count, 100)), axis=1)[:, :k], axis=1)
+    rows = np.concatenate([idx, idx + 100], axis=1)  # block layout: a_j and a_j^dag of each mode
+    stack = torch.from_numpy(base[rows[:, :, None], rows[:, None, :]]).to(device)
+    out = {"count": count, "k": k, "terms_per_call": float(count) * 2.0 ** k,
+           "desc": f"{count} random {k}-mode submatrices of the 100-mode state (r~U[0.5,1.2], eta=0.4)"}
+    with binding.Context(device=local, stream=stream.cuda_stream, flags=binding.TOR_IN_DEVICE) as c:
+        for name, src, fn in (("stacked_records", stack, binding.tor_eval_batch_arrays),
+                              ("list_of_tensors", [stack[i] for i in range(count)], binding.tor_eval_batch)):
+            fn(c, src)
+            torch.cuda.synchronize()
+            ts = []
+            for _ in range(steps):
+                t0 = time.perf_counter()
+                fn(c, src)
+                ts.append(time.perf_counter() - t0)
+            wall = statistics.median(ts)
+            out[name] = {"wall_ms": 1e3 * wall, "tor_per_s": count / wall, "device_ms": c.last_times()["total_ms"]}
+    out["what"] = "host wall time of the call (marshalling, launches, device, results), median of 5"
+    return out
+
+
 def batch_compare(local, stream, steps: int, tune_s: float = 15.0):
     """The 4096-matrix batch (k ~ U{4..24} click patterns of a 100-mode state):
     one batched launch, its CUDA-graph replay, and the plain path (one tor_eval
@@ -1234,6 +1266,7 @@ def main():
         res64 = list(binding.tor_eval_batch(ctx_dev, dmats))  # the timed step's own results
         nested(None, lambda: large_extras(local, stream, ctx_dev, mats, dmats, res64, ns, peak_ops))
         nested("batch4096", lambda: batch_compare(local, stream, steps=5))
+        nested("small_batch", lambda: small_batch(local, stream))
         nested("serve", lambda: serve_summary(local, args.serve_high_window, args.serve_sustain_rate))
     elif last_res:
         line["results"] = [result_record(f"n={n}", n, r, None,

@@ -52,7 +52,7 @@ class tor_result(ctypes.Structure):
                 ("path", ctypes.c_int), ("reserved", ctypes.c_int)]
 
 
-@dataclass
+@dataclass(slots=True)
 class TorResult:
     hi: float
     lo: float
@@ -152,6 +152,8 @@ def _device_matrix(O):
     """torch.cdouble CUDA tensor with unit column stride -> (tensor, n, ld, pointer)."""
     if O.dim() != 2 or O.shape[0] != O.shape[1] or O.shape[0] % 2:
         raise TorError(TOR_EINVAL, "O must be a square 2n x 2n matrix")
+    if not O.is_cuda or str(O.dtype) != "torch.complex128":
+        raise TorError(TOR_EINVAL, "TOR_IN_DEVICE inputs are complex128 CUDA tensors")
     if O.stride(1) != 1:
         O = O.contiguous()
     return O, O.shape[0] // 2, max(O.stride(0), 1), O.data_ptr()
@@ -281,58 +283,126 @@ def tor_eval(ctx: Context, O, check: bool = True) -> TorResult:
     return TorResult.of(res)
 
 
-def tor_eval_batch(ctx: Context, mats, check: bool = True):
-    """Tor of several matrices of mixed sizes in one launch; returns a list of TorResult."""
+# tor_result as a numpy record (the same 48 bytes)
+RESULT_DTYPE = np.dtype([("hi", "<f8"), ("lo", "<f8"), ("abs_sum", "<f8"), ("err_est", "<f8"),
+                         ("n", "<i4"), ("status", "<i4"), ("path", "<i4"), ("reserved", "<i4")])
+_C128 = np.dtype(np.complex128)
+
+
+def _batch_args(ctx: Context, mats):
+    """Marshals a batch for the C ABI: (objects to keep alive, n[], ld[], pointers[]) as
+    int32 / int32 / uint64 numpy arrays.  mats is a list of 2n x 2n matrices, or one
+    stacked (count, 2n, 2n) array (CUDA tensor with TOR_IN_DEVICE) of equal sizes,
+    whose pointers are arithmetic: no Python work per matrix."""
+    dev = bool(ctx.flags & TOR_IN_DEVICE)
+    stacked = (hasattr(mats, "dim") and mats.dim() == 3) if dev else (isinstance(mats, np.ndarray) and mats.ndim == 3)
+    if stacked:
+        if dev:
+            if not mats.is_cuda or str(mats.dtype) != "torch.complex128":
+                raise TorError(TOR_EINVAL, "TOR_IN_DEVICE inputs are complex128 CUDA tensors")
+            t = mats if mats.stride(2) == 1 and mats.stride(1) == mats.shape[2] else mats.contiguous()
+            count, m, m2 = t.shape
+            base, step = t.data_ptr(), t.stride(0) * 16
+            keep = t
+        else:
+            keep = np.ascontiguousarray(mats, dtype=np.complex128)
+            count, m, m2 = keep.shape
+            base, step = keep.ctypes.data, m * m2 * 16
+        if m != m2 or m % 2:
+            raise TorError(TOR_EINVAL, "O must be a stack of square 2n x 2n matrices")
+        ptrs = np.uint64(base) + np.arange(count, dtype=np.uint64) * np.uint64(step)
+        return keep, np.full(count, m // 2, np.int32), np.full(count, max(m, 1), np.int32), ptrs
     k = len(mats)
-    if k == 0:
-        return []
+    try:  # a list of plain arrays / tensors: one pass per attribute, no per-matrix calls into the binding
+        if dev:
+            ok = all(O.dim() == 2 and O.is_cuda and str(O.dtype) == "torch.complex128" and O.stride(1) == 1
+                     for O in mats)
+        else:
+            ok = all(type(O) is np.ndarray and O.ndim == 2 and O.dtype is _C128 and O.flags.c_contiguous
+                     for O in mats)
+    except AttributeError:
+        ok = False
+    if ok:
+        r = np.fromiter((O.shape[0] for O in mats), np.int64, k)
+        c = np.fromiter((O.shape[1] for O in mats), np.int64, k)
+        if (r != c).any() or (r % 2 != 0).any():
+            raise TorError(TOR_EINVAL, "O must be a square 2n x 2n matrix")
+        if dev:
+            ld = np.fromiter((O.stride(0) for O in mats), np.int64, k)
+            ptrs = np.fromiter((O.data_ptr() for O in mats), np.uint64, k)
+        else:
+            ld = r
+            ptrs = np.fromiter((O.ctypes.data for O in mats), np.uint64, k)
+        return mats, (r // 2).astype(np.int32), np.maximum(ld, 1).astype(np.int32), ptrs
     args = [_matrix_args(ctx, O) for O in mats]
-    ns = (ctypes.c_int * k)(*[a[1] for a in args])
-    lds = (ctypes.c_int * k)(*[a[2] for a in args])
-    ptrs = (ctypes.c_void_p * k)(*[a[3] for a in args])
-    res = (tor_result * k)()
-    st = ctx._lib.tor_eval_batch(ctx.handle, k, ns, ptrs, lds, res)
+    return (args, np.array([a[1] for a in args], np.int32), np.array([a[2] for a in args], np.int32),
+            np.array([a[3] for a in args], np.uint64))
+
+
+def _ptr(a, t):
+    return a.ctypes.data_as(ctypes.POINTER(t))
+
+
+def tor_eval_batch_arrays(ctx: Context, mats, check: bool = True) -> np.ndarray:
+    """Tor of several matrices in one launch (as tor_eval_batch); the results as one
+    numpy record array of RESULT_DTYPE (fields hi, lo, abs_sum, err_est, n, status,
+    path), without a Python object per matrix."""
+    keep, ns, lds, ptrs = _batch_args(ctx, mats)
+    k = len(ns)
+    res = np.zeros(k, dtype=RESULT_DTYPE)
+    if k == 0:
+        return res
+    st = ctx._lib.tor_eval_batch(ctx.handle, k, _ptr(ns, ctypes.c_int), _ptr(ptrs, ctypes.c_void_p),
+                                 _ptr(lds, ctypes.c_int), _ptr(res, tor_result))
     if check and st != TOR_OK:
         raise TorError(st, ctx.last_error() or "tor_eval_batch")
-    del args
-    return [TorResult.of(r) for r in res]
+    del keep
+    return res
+
+
+def _results(res: np.ndarray):
+    return [TorResult(hi, lo, a, e, n, st, path) for hi, lo, a, e, n, st, path, _ in res.tolist()]
+
+
+def tor_eval_batch(ctx: Context, mats, check: bool = True):
+    """Tor of several matrices of mixed sizes in one launch; returns a list of TorResult.
+    mats: a list of matrices, or one stacked (count, 2n, 2n) array / CUDA tensor."""
+    if len(mats) == 0:
+        return []
+    return _results(tor_eval_batch_arrays(ctx, mats, check))
 
 
 def tor_eval_seq(ctx: Context, mats, check: bool = True):
     """The plain path looped in C: one tor_eval per matrix, no Python between
     the calls.  Returns (list of TorResult, array of per-matrix wall ms)."""
-    k = len(mats)
-    if k == 0:
+    if len(mats) == 0:
         return [], np.zeros(0)
-    args = [_matrix_args(ctx, O) for O in mats]
-    ns = (ctypes.c_int * k)(*[a[1] for a in args])
-    lds = (ctypes.c_int * k)(*[a[2] for a in args])
-    ptrs = (ctypes.c_void_p * k)(*[a[3] for a in args])
-    res = (tor_result * k)()
+    keep, ns, lds, ptrs = _batch_args(ctx, mats)
+    k = len(ns)
+    res = np.zeros(k, dtype=RESULT_DTYPE)
     ms = np.zeros(k, dtype=np.float64)
-    st = ctx._lib.tor_eval_seq(ctx.handle, k, ns, ptrs, lds, res, ms.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+    st = ctx._lib.tor_eval_seq(ctx.handle, k, _ptr(ns, ctypes.c_int), _ptr(ptrs, ctypes.c_void_p),
+                               _ptr(lds, ctypes.c_int), _ptr(res, tor_result), _ptr(ms, ctypes.c_double))
     if check and st != TOR_OK:
         raise TorError(st, ctx.last_error() or "tor_eval_seq")
-    del args
-    return [TorResult.of(r) for r in res], ms
+    del keep
+    return _results(res), ms
 
 
 def tor_autotune_batch(ctx: Context, mats, budget_s: float = 10.0):
     """Tune the prefix depths of the batch's sizes for the throughput of the whole
     batch (tor_autotune_batch); returns {n: p}.  The depths stay in ctx's plan."""
-    k = len(mats)
-    if k == 0:
+    if len(mats) == 0:
         return {}
-    args = [_matrix_args(ctx, O) for O in mats]
-    ns = (ctypes.c_int * k)(*[a[1] for a in args])
-    lds = (ctypes.c_int * k)(*[a[2] for a in args])
-    ptrs = (ctypes.c_void_p * k)(*[a[3] for a in args])
-    chosen = (ctypes.c_int * k)()
-    st = ctx._lib.tor_autotune_batch(ctx.handle, k, ns, ptrs, lds, budget_s, chosen)
+    keep, ns, lds, ptrs = _batch_args(ctx, mats)
+    k = len(ns)
+    chosen = np.zeros(k, dtype=np.int32)
+    st = ctx._lib.tor_autotune_batch(ctx.handle, k, _ptr(ns, ctypes.c_int), _ptr(ptrs, ctypes.c_void_p),
+                                     _ptr(lds, ctypes.c_int), budget_s, _ptr(chosen, ctypes.c_int))
     if st != TOR_OK:
         raise TorError(st, ctx.last_error() or "tor_autotune_batch")
-    del args
-    return {int(ns[i]): int(chosen[i]) for i in range(k)}
+    del keep
+    return {int(n): int(p) for n, p in zip(ns, chosen)}
 
 
 def tor_eval_units(ctx: Context, O):
@@ -368,23 +438,22 @@ def tor_eval_range(ctx: Context, O, leaf_lo: int, leaf_count: int) -> TorResult:
 def tor_eval_range_batch(ctx: Context, mats, ranges, check: bool = True):
     """One launch over a leaf range of each matrix: ranges[i] = (leaf_lo, leaf_count),
     or None for the whole matrix.  Returns a list of TorResult."""
-    k = len(mats)
-    if k != len(ranges):
+    if len(mats) != len(ranges):
         raise ValueError("one range per matrix")
-    if k == 0:
+    if len(mats) == 0:
         return []
-    args = [_matrix_args(ctx, O) for O in mats]
-    ns = (ctypes.c_int * k)(*[a[1] for a in args])
-    lds = (ctypes.c_int * k)(*[a[2] for a in args])
-    ptrs = (ctypes.c_void_p * k)(*[a[3] for a in args])
-    los = (ctypes.c_longlong * k)(*[0 if r is None else int(r[0]) for r in ranges])
-    cnts = (ctypes.c_longlong * k)(*[-1 if r is None else int(r[1]) for r in ranges])
-    res = (tor_result * k)()
-    st = ctx._lib.tor_eval_range_batch(ctx.handle, k, ns, ptrs, lds, los, cnts, res)
+    keep, ns, lds, ptrs = _batch_args(ctx, mats)
+    k = len(ns)
+    los = np.array([0 if r is None else int(r[0]) for r in ranges], dtype=np.int64)
+    cnts = np.array([-1 if r is None else int(r[1]) for r in ranges], dtype=np.int64)
+    res = np.zeros(k, dtype=RESULT_DTYPE)
+    st = ctx._lib.tor_eval_range_batch(ctx.handle, k, _ptr(ns, ctypes.c_int), _ptr(ptrs, ctypes.c_void_p),
+                                       _ptr(lds, ctypes.c_int), _ptr(los, ctypes.c_longlong),
+                                       _ptr(cnts, ctypes.c_longlong), _ptr(res, tor_result))
     if check and st != TOR_OK:
         raise TorError(st, ctx.last_error() or "tor_eval_range_batch")
-    del args
-    return [TorResult.of(r) for r in res]
+    del keep
+    return _results(res)
 
 
 def tor_submit(ctx: Context, O) -> int:

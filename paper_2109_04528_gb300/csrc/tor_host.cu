@@ -423,6 +423,39 @@ static bool over_budget(tor_ctx* ctx, const Slot& S, const Needs& N) {
   return (size_t)std::max(0ll, held) + slot_growth(S, N) > ctx->cfg.mem_budget;
 }
 
+// Copies host matrices into the pinned staging buffer: one copy per matrix when
+// its rows are contiguous, row by row otherwise; a job staging more than 32 MB
+// is split over up to 8 threads by matrix (memory bandwidth, not the copy
+// loop, then limits it).
+template <class Copy>
+static void stage_host_matrices(const std::vector<Copy>& copies, size_t bytes) {
+  auto run = [&](size_t a, size_t b) {
+    for (size_t i = a; i < b; ++i) {
+      const Copy& c = copies[i];
+      if (c.ld == c.m) {
+        memcpy(c.dst, c.src, sizeof(tor_c128) * (size_t)c.m * c.m);
+      } else {
+        for (int r = 0; r < c.m; ++r)
+          memcpy(c.dst + (size_t)r * c.m, c.src + (size_t)r * c.ld, sizeof(tor_c128) * c.m);
+      }
+    }
+  };
+  const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
+  const size_t T = bytes >= ((size_t)32 << 20) ? std::min<size_t>({8, hw, copies.size()}) : 1;
+  if (T <= 1) {
+    run(0, copies.size());
+    return;
+  }
+  std::vector<std::thread> th;
+  const size_t per = (copies.size() + T - 1) / T;
+  for (size_t t = 1; t < T; ++t) {
+    const size_t a = std::min(copies.size(), t * per), b = std::min(copies.size(), a + per);
+    if (a < b) th.emplace_back(run, a, b);
+  }
+  run(0, std::min(copies.size(), per));
+  for (std::thread& x : th) x.join();
+}
+
 // Validates the inputs, fills trivial results, plans the job and fills the
 // slot's pinned staging buffers.  Returns the first error; *any = job has work.
 static tor_status slot_prepare(tor_ctx* ctx, Slot& S, const std::vector<MatIn>& ins, tor_result* out,
@@ -589,6 +622,12 @@ static tor_status slot_prepare(tor_ctx* ctx, Slot& S, const std::vector<MatIn>& 
   double2* dB = (double2*)S.d_B.p;
   tor_c128* hO = (tor_c128*)S.h_O.p;
   int* hm = (int*)S.h_modes.p;
+  struct HostCopy {
+    const tor_c128* src;
+    tor_c128* dst;
+    int m, ld;  // m x m entries from rows ld apart
+  };
+  std::vector<HostCopy> copies;
   for (int j = 0; j < J; ++j) {
     const MatIn& m = ins[S.act[j]];
     MatDesc& D = S.mats[j];
@@ -604,8 +643,7 @@ static tor_status slot_prepare(tor_ctx* ctx, Slot& S, const std::vector<MatIn>& 
       D.ld = m.ld;
       D.modes = nullptr;
     } else {
-      for (int r = 0; r < mm; ++r)
-        memcpy(hO + oo + (long long)r * mm, m.O + (long long)r * m.ld, sizeof(tor_c128) * mm);
+      copies.push_back({m.O, hO + oo, mm, m.ld});
       D.O = dO + oo;
       D.ld = mm;
       D.modes = nullptr;
@@ -614,6 +652,7 @@ static tor_status slot_prepare(tor_ctx* ctx, Slot& S, const std::vector<MatIn>& 
     D.B = dB + bo;
     bo += tri(m.n) * (long long)(eb / sizeof(double2));
   }
+  stage_host_matrices(copies, (size_t)oo * sizeof(tor_c128));
   memset(S.h_front.p, 0, 64);  // the control words
   memcpy((char*)S.h_front.p + S.off_mats, S.mats.data(), J * sizeof(MatDesc));
   if (S.tasks_staged_gen != S.gen) {  // not already in the pinned staging buffer

@@ -299,3 +299,23 @@ def test_mixed_batch_structured_and_general(ctx, oracle_mod):
     for O, b in list(zip(mats, batch))[:8]:
         ref = oracle_mod.tor_brute(O)
         assert gpu_err(b, ref) <= TOL * ref.abs_sum
+
+
+def test_stacked_batches_and_record_results(ctx):
+    # one (count, 2n, 2n) array (host) or CUDA tensor (device) gives the bits of the
+    # same matrices as a list, and tor_eval_batch_arrays the same numbers as records
+    torch = pytest.importorskip("torch")
+    base = inputs.lossy_squeezed(40, 8, (0.5, 1.2), 0.4).O
+    rng = np.random.default_rng(12)
+    mats = [inputs.submatrix(base, sorted(rng.choice(40, size=9, replace=False).tolist())) for _ in range(300)]
+    want = binding.tor_eval_batch(ctx, mats)
+    rec = binding.tor_eval_batch_arrays(ctx, np.stack(mats))
+    assert [(r.hi, r.lo, r.abs_sum, r.status) for r in want] == \
+        [(float(a), float(b), float(c), int(d)) for a, b, c, d in zip(rec["hi"], rec["lo"], rec["abs_sum"], rec["status"])]
+    flags = binding.TOR_IN_DEVICE | (binding.TOR_COMPLEX_PATH if ctx.kind == "complex" else 0)
+    with binding.Context(device=0, flags=flags) as cd:
+        dev = torch.from_numpy(np.stack(mats)).cuda()
+        got = binding.tor_eval_batch(cd, dev)
+        got_list = binding.tor_eval_batch(cd, [dev[i] for i in range(len(mats))])
+    for a, b, c in zip(want, got, got_list):
+        assert (a.hi, a.lo, a.abs_sum) == (b.hi, b.lo, b.abs_sum) == (c.hi, c.lo, c.abs_sum)
