@@ -487,6 +487,19 @@ def small_batch(local, stream, count: int = 65536, k: int = 8, steps: int = 5):
                 ts.append(time.perf_counter() - t0)
             wall = statistics.median(ts)
             out[name] = {"wall_ms": 1e3 * wall, "tor_per_s": count / wall, "device_ms": c.last_times()["total_ms"]}
+        # the plan tuned for this batch (small matrices alone fill the GPU with larger units)
+        p0 = c.plan_prefix_depth(k)
+        binding.tor_autotune_batch(c, stack, 3.0)
+        binding.tor_eval_batch_arrays(c, stack)
+        ts = []
+        for _ in range(steps):
+            t0 = time.perf_counter()
+            binding.tor_eval_batch_arrays(c, stack)
+            ts.append(time.perf_counter() - t0)
+        wall = statistics.median(ts)
+        out["stacked_records_autotuned"] = {"wall_ms": 1e3 * wall, "tor_per_s": count / wall,
+                                            "device_ms": c.last_times()["total_ms"],
+                                            "prefix_depth": [p0, c.plan_prefix_depth(k)]}
     out["what"] = "host wall time of the call (marshalling, launches, device, results), median of 5"
     return out
 

@@ -366,7 +366,7 @@ struct Needs {
 
 static Needs job_needs(tor_ctx* ctx, const std::vector<MatIn>& ins, size_t count) {
   long long o = 0, bt = 0, parts = 0, reds = 0, md = 0, lane_e = 0, warp_e = 0, ntask = 0;
-  std::map<int, long long> small_units;  // n -> units of the matrices with p < 5 (one lane each)
+  long long small_units[65] = {};  // n -> units of the matrices with p < 5 (one lane each)
   long long J = 0;
   for (size_t i = 0; i < count; ++i) {
     const MatIn& m = ins[i];
@@ -390,7 +390,7 @@ static Needs job_needs(tor_ctx* ctx, const std::vector<MatIn>& ins, size_t count
     lane_e = std::max(lane_e, lane_elems_for(m.n, p));
     warp_e = std::max(warp_e, warp_elems_for(m.n, p));
   }
-  for (const auto& kv : small_units) ntask += (kv.second + 31) / 32;
+  for (long long u : small_units) ntask += (u + 31) / 32;
   const size_t eb = entry_bytes(ctx);
   const size_t off_tasks = (256 + (size_t)J * sizeof(MatDesc) + 255) / 256 * 256;
   Needs N;
@@ -490,7 +490,8 @@ static tor_status slot_prepare(tor_ctx* ctx, Slot& S, const std::vector<MatIn>& 
   }
   if (S.act.empty()) return first;
   // job order: by n descending so equal sizes are adjacent (stable: same n keeps caller order)
-  std::stable_sort(S.act.begin(), S.act.end(), [&](int a, int b) { return ins[a].n > ins[b].n; });
+  auto by_n = [&](int a, int b) { return ins[a].n > ins[b].n; };
+  if (!std::is_sorted(S.act.begin(), S.act.end(), by_n)) std::stable_sort(S.act.begin(), S.act.end(), by_n);
   const int J = (int)S.act.size();
   S.mats.assign(J, MatDesc{});
   S.o_elems = S.b_elems = S.parts = S.reds = S.red_chunks = S.mode_elems = S.lane_e = S.warp_e = 0;
