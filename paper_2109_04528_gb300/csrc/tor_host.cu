@@ -857,7 +857,7 @@ static tor_status slot_finish(Slot& S, tor_result* out, double* unit_partials, d
 
 // Blocking evaluation on the main slot (caller holds run_mu).
 static tor_status run_blocking(tor_ctx* ctx, const std::vector<MatIn>& ins, tor_result* out, double* unit_partials,
-                               size_t unit_len) {
+                               size_t unit_len, bool allow_graphs = true) {
   CK(cudaSetDevice(ctx->cfg.device), "cudaSetDevice");
   for (int i = 0; i < 4; ++i) ctx->last_times[i] = 0;
   Slot& S = ctx->main;
@@ -865,7 +865,7 @@ static tor_status run_blocking(tor_ctx* ctx, const std::vector<MatIn>& ins, tor_
   tor_status first = slot_prepare(ctx, S, ins, out, unit_partials != nullptr, &any);
   if (!any) return first;
   if (unit_partials && (S.J != 1 || unit_len < 3ull * (1ull << S.mats[0].p))) return TOR_EINVAL;
-  tor_status st = slot_launch(ctx, S, (ctx->cfg.flags & TOR_GRAPHS) != 0);
+  tor_status st = slot_launch(ctx, S, allow_graphs && (ctx->cfg.flags & TOR_GRAPHS) != 0);
   if (st != TOR_OK) return st;
   CK(cudaStreamSynchronize(S.stream), "kernel execution");
   tor_status fin = slot_finish(S, out, unit_partials, ctx->last_times);
@@ -1929,7 +1929,7 @@ static tor_status tor_sample_impl(tor_ctx* ctx, tor_session* s, int count, int n
         tor_status st;
         {
           std::lock_guard<std::mutex> lk(ctx->run_mu);
-          st = run_blocking(ctx, part, res.data() + b, nullptr, 0);
+          st = run_blocking(ctx, part, res.data() + b, nullptr, 0, false);  // every step has a new shape: no graphs
         }
         if (st == TOR_ENOMEM && chunk > 1) {
           chunk /= 2;

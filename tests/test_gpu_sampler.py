@@ -156,3 +156,15 @@ def test_chunks_shrink_under_a_memory_budget():
         assert c.memory()[0] <= budget
     assert np.array_equal(got[0], want[0])
     assert np.array_equal(got[1], want[1])
+
+
+def test_graph_context_draws_the_same():
+    # a context with TOR_GRAPHS draws the same patterns (its sampling steps run uncaptured:
+    # each has a new shape) and keeps its graph cache for the calls that repeat
+    inst = inputs.lossy_squeezed(12, 61, (0.5, 1.2), 0.5)
+    u = inputs.rng_for(13).uniform(0.0, 1.0, size=(200, 12))
+    with binding.Context(device=0) as c, binding.Session(c, inst.sigma) as sess:
+        want = binding.tor_sample(c, sess, u)
+    with binding.Context(device=0, flags=binding.TOR_GRAPHS) as c, binding.Session(c, inst.sigma) as sess:
+        got = binding.tor_sample(c, sess, u)
+    assert np.array_equal(got[0], want[0]) and np.array_equal(got[1], want[1])
